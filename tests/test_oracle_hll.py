@@ -1,0 +1,137 @@
+"""Pins for the oracle's HyperLogLog pieces (Sec. 2.3, Sec. 3.3, Alg. 1).
+
+- SplitMix64 against its published reference outputs (tests/golden/splitmix64.txt).
+- The hand-written 128-bit -> double rounding against Python's correctly
+  rounded int -> float conversion.
+- alpha_m against Flajolet et al.'s constants (tests/golden/hll_alpha.txt).
+- The estimator against closed forms: an empty counter gives 0, a counter
+  holding one element gives m ln(m/(m-1)) (linear counting), a counter whose
+  registers all equal r >= 1 gives alpha_m m 2^r (raw estimate, V = 0).
+- Its accuracy against exact counts: the relative error's RMS over many
+  counters stays within the standard error 1.04/sqrt(m) quoted in Sec. 2.3
+  (with a 1.5x margin), and its mean shows no bias beyond that.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            yield line.split()
+
+
+@pytest.mark.parametrize("x,h", [(int(a, 16), int(b, 16)) for a, b in _rows("splitmix64.txt")])
+def test_splitmix64_published_outputs(x, h):
+    assert oracle.splitmix64(x) == h
+
+
+@pytest.mark.parametrize("p,alpha", [(int(a), float(b)) for a, b in _rows("hll_alpha.txt")])
+def test_alpha_constants(p, alpha):
+    assert oracle.hll_alpha(p) == pytest.approx(alpha, abs=5e-7)
+
+
+def test_hash_index_and_rho_ranges():
+    for p in (4, 8, 10, 12, 16):
+        js, rhos = [], []
+        for v in range(3000):
+            j, rho = oracle.hll_hash(v, 0, p)
+            assert 0 <= j < (1 << p)
+            assert 1 <= rho <= 65 - p
+            js.append(j)
+            rhos.append(rho)
+        rhos = np.array(rhos)
+        # rho is geometric(1/2): P(rho = 1) = 1/2, P(rho = 2) = 1/4
+        assert abs((rhos == 1).mean() - 0.5) < 0.04
+        assert abs((rhos == 2).mean() - 0.25) < 0.04
+        # index is uniform over the m registers
+        if p == 4:
+            counts = np.bincount(js, minlength=16)
+            sigma = math.sqrt(3000 / 16 * (1 - 1 / 16))
+            assert np.abs(counts - 3000 / 16).max() < 5 * sigma
+
+
+def test_hash_matches_definition_for_known_input():
+    # id 0, seed 0: hash = 0xe220a8397b1dcdaf (first SplitMix64 output).
+    h = 0xE220A8397B1DCDAF
+    for p in (4, 10, 16):
+        j, rho = oracle.hll_hash(0, 0, p)
+        assert j == h >> (64 - p)
+        w = (h << p) & ((1 << 64) - 1)
+        assert rho == 64 - w.bit_length() + 1
+    # seed enters as id XOR seed
+    assert oracle.hll_hash(5, 3, 10) == oracle.hll_hash(6, 0, 10)
+
+
+@pytest.mark.parametrize("x", [0, 1, 2**53 - 1, 2**53, 2**53 + 1, 2**53 + 2, 2**53 + 3, 2**54 + 2, 2**54 + 6,
+                               2**64 - 1, 2**64, 2**64 + 1, 2**65, 2**65 + 2**12, 2**65 + 2**13 - 1,
+                               2**127 + 2**74, (2**128 - 1)])
+def test_u128_to_double_edge_values(x):
+    assert oracle.u128_to_double(x) == float(x)
+
+
+def test_u128_to_double_random():
+    rng = np.random.default_rng(1)
+    for _ in range(3000):
+        bits = int(rng.integers(1, 128))
+        x = int(rng.integers(0, 2**62)) << max(0, bits - 62) | int(rng.integers(0, 2**20))
+        x &= (1 << 128) - 1
+        assert oracle.u128_to_double(x) == float(x)
+
+
+@pytest.mark.parametrize("p", [4, 6, 8, 10, 12, 14, 16])
+def test_estimator_closed_forms(p):
+    m = 1 << p
+    reg = np.zeros(m, np.uint8)
+    assert oracle.hll_estimate(reg, p) == 0.0                       # empty set
+    reg[3 % m] = 2
+    assert oracle.hll_estimate(reg, p) == pytest.approx(m * math.log(m / (m - 1)), rel=1e-15)
+    for r in (1, 3, 7):
+        reg[:] = r
+        assert oracle.hll_estimate(reg, p) == pytest.approx(oracle.hll_alpha(p) * m * 2**r, rel=1e-15)
+
+
+@pytest.mark.parametrize("p", [8, 10, 12])
+def test_estimator_standard_error(p):
+    m = 1 << p
+    rng = np.random.default_rng(p)
+    errs = []
+    for trial in range(40):
+        n = int(rng.integers(5 * m, 50 * m))
+        base = int(rng.integers(0, 2**40))
+        reg = np.zeros(m, np.uint8)
+        for v in range(base, base + n):
+            j, rho = oracle.hll_hash(v, 0, p)
+            if rho > reg[j]:
+                reg[j] = rho
+        errs.append(oracle.hll_estimate(reg, p) / n - 1.0)
+    errs = np.array(errs)
+    se = 1.04 / math.sqrt(m)
+    assert math.sqrt(np.mean(errs ** 2)) < 1.5 * se
+    assert abs(errs.mean()) < 3 * se / math.sqrt(len(errs)) + 0.5 * se
+
+
+def test_init_inserts_each_node_in_its_own_counter():
+    n, p = 300, 8
+    regs = oracle.hll_init(n, p, seed=77)
+    for v in range(n):
+        j, rho = oracle.hll_hash(v, 77, p)
+        assert regs[v, j] == rho
+        assert np.count_nonzero(regs[v]) == 1
+        assert oracle.hll_estimate(regs[v], p) == pytest.approx((1 << p) * math.log((1 << p) / ((1 << p) - 1)))
+
+
+def test_accumulate_rounds_each_step():
+    # sum_d + t * (c_t - c_prev), evaluated as three correctly rounded steps
+    assert oracle.accumulate(0.0, 1, 10.0, 1.0) == 9.0
+    assert oracle.accumulate(9.0, 2, 30.0, 10.0) == 49.0
+    a, t, c1, c0 = 0.1, 3, 0.7, 0.3
+    assert oracle.accumulate(a, t, c1, c0) == a + t * (c1 - c0)
