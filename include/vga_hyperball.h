@@ -1,0 +1,229 @@
+/*
+ * vga_hyperball.h -- C ABI of the GB300 HyperBall library for visibility
+ * graph analysis.
+ *
+ * Paper: "City-Scale Visibility Graph Analysis via GPU-Accelerated HyperBall"
+ * (arXiv 2604.08374).  The library keeps a visibility graph resident in device
+ * memory as the paper's delta-compressed LEB128 CSR (Sec. 3.2) and runs the
+ * HyperBall iteration of Algorithm 1 (Sec. 3.3) on it with sm_103a kernels:
+ * HyperLogLog counters of m = 2^p uint8 registers, the register-wise union of
+ * Eq. hll-union, the HLL estimator, the distance accumulation of Eq. sumD, and
+ * Visual Mean Depth MD(v) = sum_d[v] / (N_v - 1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: VGA_OK (0) or a negative vga_status.  On failure
+ *    vga_last_error() gives a message for the calling thread; outputs are
+ *    unspecified.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *    Output buffers are caller-owned and must hold the stated element counts.
+ *  - "host" pointers are ordinary CPU memory (pinned or pageable); "device"
+ *    pointers are CUDA global memory of the current device.
+ *  - Node ids are uint32, numbered 0..N-1.  Edges are directed: a visibility
+ *    edge u-v appears in both lists, and E = sum of degrees (the paper's edge
+ *    counts, Sec. 4.3 edge-density table, count both directions).
+ *  - A vga_graph lives on the device that was current when it was loaded; run
+ *    it with that device current.
+ */
+#ifndef VGA_HYPERBALL_H
+#define VGA_HYPERBALL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vga_status {
+    VGA_OK = 0,
+    VGA_EINVAL = -1,    /* bad argument (size, precision, null pointer)        */
+    VGA_ENOMEM = -2,    /* device or host allocation failed                    */
+    VGA_ECORRUPT = -3,  /* malformed CSR or file                               */
+    VGA_ECUDA = -4,     /* a CUDA call failed                                  */
+    VGA_ETIMEOUT = -5,  /* a bounded device wait ran out                       */
+    VGA_EBUSY = -6,     /* resource budget exhausted, try later                */
+    VGA_EIO = -7        /* file could not be read or written                   */
+} vga_status;
+
+/* Opaque graph: owns the device-resident compressed CSR. */
+typedef struct vga_graph vga_graph;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *vga_last_error(void);
+
+/* Library version string. */
+const char *vga_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* Compressed CSR (Sec. 3.2)                                               */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * vga_csr_encode -- delta + LEB128 encoding of sorted neighbour lists
+ * (Sec. 3.2, "Encoding"): each list's first id is an absolute unsigned
+ * LEB128 varint (7-bit groups, least significant first, 0x80 = more bytes
+ * follow), every later id the delta (>= 1) from its predecessor.
+ *   n        number of nodes.
+ *   row_ptr  host, n+1 entries: list of node v is col[row_ptr[v] .. row_ptr[v+1]).
+ *   col      host, row_ptr[n] ids, strictly increasing within each list.
+ *   offsets  host out, n+1 entries: byte range of node v's list.
+ *   bytes    host out or NULL.  With NULL only offsets and *n_bytes are filled
+ *            (size query); otherwise it must hold *n_bytes bytes from a size
+ *            query.
+ *   n_bytes  out: total encoded bytes.
+ * Errors: VGA_EINVAL for null pointers or a list that is not strictly
+ * increasing.
+ */
+int vga_csr_encode(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, uint64_t *offsets,
+                   uint8_t *bytes, uint64_t *n_bytes);
+
+/* ---------------------------------------------------------------------- */
+/* Graph residency (Sec. 3.2, Sec. 3.4)                                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * vga_graph_load -- copy a compressed CSR to the current device and keep it
+ * there (the paper's D1 CompressedCsr: u64 byte offsets, derived u32 degrees,
+ * the byte stream).
+ *   n_nodes    N >= 0.
+ *   offsets    host, N+1 entries, offsets[0] = 0, non-decreasing,
+ *              offsets[N] = n_bytes.
+ *   bytes      host, n_bytes bytes (may be NULL when n_bytes = 0).
+ *   comp_size  host, N entries or NULL: exact component size N_v of each node
+ *              (Sec. 3.3); NULL means every node belongs to one component of
+ *              size N.
+ *   out        receives the graph handle.
+ * The byte stream is validated on the device right after the copy: every
+ * varint at most 5 bytes and ending inside its node's range, every id < N and
+ * different from the node itself, ids strictly increasing.  A malformed graph
+ * returns VGA_ECORRUPT (nothing is kept).  Degrees and E are derived here.
+ */
+int vga_graph_load(uint32_t n_nodes, const uint64_t *offsets, const uint8_t *bytes, uint64_t n_bytes,
+                   const uint32_t *comp_size, vga_graph **out);
+
+/* As vga_graph_load, but the offsets and bytes are already in device memory
+ * (copied device to device on `stream`, a cudaStream_t or NULL). */
+int vga_graph_load_device(uint32_t n_nodes, const uint64_t *offsets_dev, const uint8_t *bytes_dev,
+                          uint64_t n_bytes, const uint32_t *comp_size_host, void *stream, vga_graph **out);
+
+/*
+ * vga_graph_load_file / vga_graph_save_file -- this library's own binary
+ * format (".vgacsr"; the paper's VGACSR03 layout is not published, so this is
+ * not byte-compatible with it).  Little-endian: 8-byte magic "VGAHB\0\0\1",
+ * u64 N, u64 n_bytes, u64 flags (bit 0: component sizes present), then
+ * offsets (N+1 u64), bytes, and N u32 component sizes if flagged.
+ * Errors: VGA_EIO (open/read/write), VGA_ECORRUPT (bad header or contents).
+ */
+int vga_graph_load_file(const char *path, vga_graph **out);
+int vga_graph_save_file(const vga_graph *g, const char *path);
+
+/* Release the graph's device memory.  NULL is ignored. */
+void vga_graph_free(vga_graph *g);
+
+/* Sizes of a loaded graph: nodes, directed edges, compressed bytes. */
+int vga_graph_info(const vga_graph *g, uint32_t *n_nodes, uint64_t *n_edges, uint64_t *n_bytes);
+
+/* Copy the CSR back to host memory: offsets (N+1), bytes (n_bytes), degrees
+ * (N).  Any output may be NULL. */
+int vga_graph_copy_csr(const vga_graph *g, uint64_t *offsets, uint8_t *bytes, uint32_t *degrees);
+
+/* ---------------------------------------------------------------------- */
+/* Visibility graph builder (Sec. 3.1)                                     */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * vga_visibility_build -- build the visibility graph of an obstacle grid on
+ * the device and load it (Sec. 3.1, "Visibility Graph Construction").
+ * Rule: two free cells see each other iff the closed segment between their
+ * centres meets no obstacle cell's closed square.  Nodes are the cells of the
+ * largest 4-connected free component (ties: the component holding the lowest
+ * raster index), numbered in row-major raster order (Sec. 3.2).  Only the main
+ * component is kept, so N_v = N for every node.
+ *   W, H        grid size, 1 <= W, H <= 16384.
+ *   obst        host, H*W bytes, row-major (row = y), nonzero = obstacle.
+ *   cell_of_node host out or NULL: N entries, raster index y*W+x of each node
+ *               (size it W*H to be safe, or query N first with
+ *               vga_visibility_count).
+ *   out         receives the graph handle.
+ * Device scratch: an N x ceil(N/32) bit matrix (N = 236k needs 7 GB).
+ */
+int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_node, vga_graph **out);
+
+/* Number of nodes (main-component cells) the builder would produce. */
+int vga_visibility_count(int W, int H, const uint8_t *obst, uint32_t *n_nodes);
+
+/* ---------------------------------------------------------------------- */
+/* HyperBall (Sec. 3.3, Algorithm 1, Sec. 3.4)                             */
+/* ---------------------------------------------------------------------- */
+
+/* Tuning knobs (all 0 = choose automatically). */
+typedef struct vga_tuning {
+    int slice_bytes;     /* registers per union slice: power of two in [16, min(m, 1024)] */
+    int warps_per_cta;   /* union kernel CTA size in warps: 1..32                         */
+    int l2_budget_mb;    /* L2 share the auto slice width aims at (default: 60 % of L2)   */
+    int reserved[5];
+} vga_tuning;
+
+/*
+ * hyperball_run -- Algorithm 1 end to end, host outputs.
+ *   g           loaded graph.
+ *   p           HLL precision, 4 <= p <= 16; m = 2^p uint8 registers per node.
+ *   d           depth limit: run at most d union passes; d <= 0 = unlimited.
+ *   seed        hash seed: node v is inserted as splitmix64(v XOR seed); the
+ *               top p bits pick the register, rho = leading zeros of the
+ *               other 64-p bits + 1 (Sec. 3.3 "Initialisation").
+ *   mean_depth  host out, N doubles: MD(v) = sum_d[v] / (N_v - 1), NaN when
+ *               N_v <= 1 (Sec. 3.3 "Distance accumulation").
+ *   ball_size   host out, N doubles: the estimate c_t[v] of |B(v,t)| after the
+ *               last pass run.
+ *   iterations  host out or NULL: union passes run.
+ * Stopping: after pass t the run ends if t = d or if the pass changed no
+ * register anywhere (then every later pass would change nothing and add 0 to
+ * sum_d).  The paper's rule max_v(c_t - c_{t-1}) <= 0.5 is available as
+ * conv_mode 1 in hyperball_run_dev.
+ */
+int hyperball_run(const vga_graph *g, int p, int d, uint64_t seed, double *mean_depth, double *ball_size,
+                  int *iterations);
+
+/* Bytes of device workspace hyperball_run_dev needs for this graph and p. */
+int hyperball_workspace_bytes(const vga_graph *g, int p, uint64_t *bytes);
+
+/*
+ * hyperball_run_dev -- as hyperball_run, with device outputs and explicit
+ * stream, workspace and tuning.
+ *   conv_mode       0: stop at the first pass that changes no register;
+ *                   1: the paper's rule (Algorithm 1), stop when
+ *                   max_v(c_t - c_{t-1}) <= 0.5.  Both also stop at t = d.
+ *   mean_depth_dev  device out, N doubles (may be NULL).
+ *   ball_size_dev   device out, N doubles (may be NULL).
+ *   iterations      host out or NULL.
+ *   workspace_dev   device scratch of at least hyperball_workspace_bytes(),
+ *                   256-byte aligned, or NULL to let the library allocate and
+ *                   free its own.
+ *   stream          cudaStream_t to run on (NULL = legacy default stream).  The
+ *                   call returns after the last pass; it synchronises on the
+ *                   stream once per pass to read the stop flag.
+ *   tuning          NULL or knobs.
+ */
+int hyperball_run_dev(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth_dev,
+                      double *ball_size_dev, int *iterations, void *workspace_dev, uint64_t workspace_bytes,
+                      void *stream, const vga_tuning *tuning);
+
+/*
+ * hyperball_run_trace -- debug hook for bit-exact checks: as hyperball_run_dev
+ * with host outputs, and additionally copies the registers and estimates after
+ * every pass.
+ *   regs_host   host out or NULL: (max_trace+1) x N x m bytes, node-major
+ *               (node v's m registers contiguous); slot 0 holds the initial
+ *               counters, slot t the counters after pass t (t <= max_trace).
+ *   c_host      host out or NULL: (max_trace+1) x N doubles, c_t likewise.
+ */
+int hyperball_run_trace(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth,
+                        double *ball_size, int *iterations, uint8_t *regs_host, double *c_host, int max_trace,
+                        const vga_tuning *tuning);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VGA_HYPERBALL_H */

@@ -1,0 +1,283 @@
+"""GB300 HyperBall for visibility graph analysis -- Python binding.
+
+Thin ctypes marshalling over the C ABI declared in ``include/vga_hyperball.h``
+(same names).  Every step of the computation runs in the CUDA library
+``libvga_hyperball.so`` built from ``csrc/`` for sm_103a; this module only
+converts numpy arrays and torch tensors to pointers.  There is no CPU
+fallback: if the library is missing, importing the binding's functions raises.
+
+Paper: "City-Scale Visibility Graph Analysis via GPU-Accelerated HyperBall"
+(arXiv 2604.08374): delta-compressed LEB128 CSR (Sec. 3.2), HyperBall
+(Sec. 3.3, Algorithm 1), GPU pipeline (Sec. 3.4).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvga_hyperball.so")
+
+VGA_OK, VGA_EINVAL, VGA_ENOMEM, VGA_ECORRUPT, VGA_ECUDA, VGA_ETIMEOUT, VGA_EBUSY, VGA_EIO = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "VGA_OK", -1: "VGA_EINVAL", -2: "VGA_ENOMEM", -3: "VGA_ECORRUPT", -4: "VGA_ECUDA",
+                -5: "VGA_ETIMEOUT", -6: "VGA_EBUSY", -7: "VGA_EIO"}
+
+# Every entry point the header declares, with its ctypes signature.
+vp, i32, u32, u64, i64, f64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_int64, C.c_double
+
+
+class VgaTuning(C.Structure):
+    _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
+                ("reserved", C.c_int * 5)]
+
+
+SIGNATURES = {
+    "vga_last_error": ([], C.c_char_p),
+    "vga_version": ([], C.c_char_p),
+    "vga_csr_encode": ([u32, vp, vp, vp, vp, C.POINTER(u64)], i32),
+    "vga_graph_load": ([u32, vp, vp, u64, vp, C.POINTER(vp)], i32),
+    "vga_graph_load_device": ([u32, vp, vp, u64, vp, vp, C.POINTER(vp)], i32),
+    "vga_graph_load_file": ([C.c_char_p, C.POINTER(vp)], i32),
+    "vga_graph_save_file": ([vp, C.c_char_p], i32),
+    "vga_graph_free": ([vp], None),
+    "vga_graph_info": ([vp, C.POINTER(u32), C.POINTER(u64), C.POINTER(u64)], i32),
+    "vga_graph_copy_csr": ([vp, vp, vp, vp], i32),
+    "vga_visibility_build": ([i32, i32, vp, vp, C.POINTER(vp)], i32),
+    "vga_visibility_count": ([i32, i32, vp, C.POINTER(u32)], i32),
+    "hyperball_run": ([vp, i32, i32, u64, vp, vp, C.POINTER(i32)], i32),
+    "hyperball_workspace_bytes": ([vp, i32, C.POINTER(u64)], i32),
+    "hyperball_run_dev": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, u64, vp, C.POINTER(VgaTuning)], i32),
+    "hyperball_run_trace": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, vp, i32, C.POINTER(VgaTuning)],
+                            i32),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VgaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib():
+    """Load libvga_hyperball.so (build it first with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: run paper_2604_08374_gb300.build.build() "
+                                  "(the library has no CPU fallback)")
+            L = C.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != VGA_OK:
+        raise VgaError(status, lib().vga_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> int | None:
+    """Data pointer of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data if a.size else None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr() or None
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0):
+    if not (slice_bytes or warps_per_cta or l2_budget_mb):
+        return None
+    t = VgaTuning()
+    t.slice_bytes, t.warps_per_cta, t.l2_budget_mb = slice_bytes, warps_per_cta, l2_budget_mb
+    return C.pointer(t)
+
+
+def version() -> str:
+    return lib().vga_version().decode()
+
+
+# --------------------------------------------------------------------------
+# Compressed CSR (Sec. 3.2)
+# --------------------------------------------------------------------------
+
+def vga_csr_encode(row_ptr: np.ndarray, col: np.ndarray):
+    """Delta + LEB128 encode sorted neighbour lists -> (offsets u64[n+1], bytes u8)."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.uint64)
+    col = np.ascontiguousarray(col, np.uint32)
+    n = len(row_ptr) - 1
+    offsets = np.zeros(n + 1, np.uint64)
+    nb = C.c_uint64()
+    _check(lib().vga_csr_encode(n, _ptr(row_ptr), _ptr(col), _ptr(offsets), None, C.byref(nb)))
+    out = np.zeros(max(nb.value, 1), np.uint8)
+    _check(lib().vga_csr_encode(n, _ptr(row_ptr), _ptr(col), _ptr(offsets), _ptr(out), C.byref(nb)))
+    return offsets, out[: nb.value]
+
+
+class Graph:
+    """A device-resident compressed visibility graph (owns a vga_graph*)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+        n, e, b = C.c_uint32(), C.c_uint64(), C.c_uint64()
+        _check(lib().vga_graph_info(self._h, C.byref(n), C.byref(e), C.byref(b)))
+        self.n_nodes, self.n_edges, self.n_bytes = n.value, e.value, b.value
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise ValueError("graph has been freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().vga_graph_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def copy_csr(self):
+        """(offsets, bytes, degrees) copied back to host memory."""
+        offsets = np.zeros(self.n_nodes + 1, np.uint64)
+        bytes_ = np.zeros(max(self.n_bytes, 1), np.uint8)
+        deg = np.zeros(max(self.n_nodes, 1), np.uint32)
+        _check(lib().vga_graph_copy_csr(self.handle, _ptr(offsets), _ptr(bytes_), _ptr(deg)))
+        return offsets, bytes_[: self.n_bytes], deg[: self.n_nodes]
+
+    def save(self, path: str):
+        _check(lib().vga_graph_save_file(self.handle, path.encode()))
+
+
+def vga_graph_load(offsets: np.ndarray, bytes_: np.ndarray, comp_size=None) -> Graph:
+    """Copy a compressed CSR (host arrays) to the device; validated there."""
+    offsets = np.ascontiguousarray(offsets, np.uint64)
+    bytes_ = np.ascontiguousarray(bytes_, np.uint8)
+    n = len(offsets) - 1
+    cs = None if comp_size is None else np.ascontiguousarray(comp_size, np.uint32)
+    h = C.c_void_p()
+    _check(lib().vga_graph_load(n, _ptr(offsets), _ptr(bytes_), len(bytes_), _ptr(cs), C.byref(h)))
+    return Graph(h.value)
+
+
+def vga_graph_load_device(offsets_dev, bytes_dev, n_bytes: int, comp_size=None, stream=None) -> Graph:
+    """Load from device buffers (torch tensors): offsets u64 (n+1), bytes u8."""
+    n = offsets_dev.numel() - 1
+    cs = None if comp_size is None else np.ascontiguousarray(comp_size, np.uint32)
+    h = C.c_void_p()
+    _check(lib().vga_graph_load_device(n, _ptr(offsets_dev), _ptr(bytes_dev), n_bytes, _ptr(cs),
+                                       _stream_ptr(stream), C.byref(h)))
+    return Graph(h.value)
+
+
+def vga_graph_load_file(path: str) -> Graph:
+    h = C.c_void_p()
+    _check(lib().vga_graph_load_file(path.encode(), C.byref(h)))
+    return Graph(h.value)
+
+
+# --------------------------------------------------------------------------
+# Visibility builder (Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def vga_visibility_count(obst: np.ndarray) -> int:
+    obst = np.ascontiguousarray(obst, np.uint8)
+    H, W = obst.shape
+    n = C.c_uint32()
+    _check(lib().vga_visibility_count(W, H, _ptr(obst), C.byref(n)))
+    return n.value
+
+
+def vga_visibility_build(obst: np.ndarray, return_cells: bool = False):
+    """Build the supercover visibility graph of an obstacle grid on the GPU."""
+    obst = np.ascontiguousarray(obst, np.uint8)
+    H, W = obst.shape
+    cells = np.zeros(max(H * W, 1), np.uint64)
+    h = C.c_void_p()
+    _check(lib().vga_visibility_build(W, H, _ptr(obst), _ptr(cells), C.byref(h)))
+    g = Graph(h.value)
+    if return_cells:
+        return g, cells[: g.n_nodes]
+    return g
+
+
+# --------------------------------------------------------------------------
+# HyperBall (Sec. 3.3, Algorithm 1)
+# --------------------------------------------------------------------------
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+def hyperball_run(g: Graph, p: int = 10, d: int = 0, seed: int = 0):
+    """Algorithm 1 with host outputs -> (mean_depth, ball_size, iterations)."""
+    md = np.zeros(max(g.n_nodes, 1), np.float64)
+    ball = np.zeros(max(g.n_nodes, 1), np.float64)
+    it = C.c_int()
+    _check(lib().hyperball_run(g.handle, p, d, seed, _ptr(md), _ptr(ball), C.byref(it)))
+    return md[: g.n_nodes], ball[: g.n_nodes], it.value
+
+
+def hyperball_workspace_bytes(g: Graph, p: int) -> int:
+    b = C.c_uint64()
+    _check(lib().hyperball_workspace_bytes(g.handle, p, C.byref(b)))
+    return b.value
+
+
+def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
+                      workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
+                      l2_budget_mb: int = 0) -> int:
+    """Algorithm 1 into device tensors (float64, N each); returns passes run."""
+    it = C.c_int()
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
+                                   C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
+                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb)))
+    return it.value
+
+
+def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0, max_trace: int = 8,
+                        slice_bytes: int = 0, warps_per_cta: int = 0):
+    """Run with per-pass register and estimate dumps (bit-exact checks).
+
+    Returns dict(mean_depth, ball, iterations, regs[(max_trace+1), N, m], c[(max_trace+1), N])."""
+    n, m = g.n_nodes, 1 << p
+    md = np.zeros(max(n, 1), np.float64)
+    ball = np.zeros(max(n, 1), np.float64)
+    regs = np.zeros(max((max_trace + 1) * n * m, 1), np.uint8)
+    cc = np.zeros(max((max_trace + 1) * n, 1), np.float64)
+    it = C.c_int()
+    _check(lib().hyperball_run_trace(g.handle, p, d, seed, conv_mode, _ptr(md), _ptr(ball), C.byref(it),
+                                     _ptr(regs), _ptr(cc), max_trace, _tuning(slice_bytes, warps_per_cta)))
+    return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
+            "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
+            "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}

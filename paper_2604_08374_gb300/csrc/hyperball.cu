@@ -1,0 +1,487 @@
+// hyperball.cu -- HyperBall (Algorithm 1, Sec. 3.3) on the device-resident
+// compressed CSR: counter initialisation, the register-wise union of
+// Eq. hll-union with on-the-fly LEB128 decoding, the HLL estimator, the
+// distance accumulation of Eq. sumD and Visual Mean Depth.
+//
+// Register layout: the N x m uint8 registers are stored slice-major,
+// [m/S][N][S] for a slice width of S bytes, so that one union launch touches
+// only N*S bytes of counters (sized to stay resident in L2) and every
+// neighbour gather is S contiguous, 16-byte aligned bytes.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "vga_common.cuh"
+
+namespace vga {
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood 2014): one golden-ratio state step, then the
+// output mix.  Sec. 3.3 inserts node v into its own counter with this hash.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Alg. 1 initialisation: node v's counter gets rho in register j, where j is
+// the top p bits of the hash and rho the position of the first set bit of the
+// remaining 64-p bits (65-p if none).  The registers were zeroed beforehand.
+__global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed) {
+    const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint64_t h = splitmix64(v ^ seed);
+    const uint32_t j = (uint32_t)(h >> (64 - p));
+    const uint64_t w = h << p;
+    const uint32_t rho = w ? (uint32_t)__clzll((long long)w) + 1u : (uint32_t)(65 - p);
+    const uint32_t s = j / (uint32_t)S, o = j % (uint32_t)S;
+    regs[((uint64_t)s * n + v) * (uint64_t)S + o] = (uint8_t)rho;
+}
+
+// Eq. hll-union for one register slice: next[v] = max(cur[v], max_{w in N(v)}
+// cur[w]) bytewise.  One warp per node: the warp decodes the node's LEB128
+// list 32 bytes at a time, then gathers each neighbour's S-byte slice with
+// 16-byte loads (G lanes per neighbour, P = 32/G neighbours in flight per
+// load instruction, U loads per lane in flight) and folds it in with
+// __vmaxu4.  Sets flags[0] if any register of the slice changed.
+template <int S>
+__global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restrict__ off,
+                                                       const uint8_t *__restrict__ bytes,
+                                                       const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
+                                                       uint32_t n, uint32_t *__restrict__ flags) {
+    constexpr int CH = (S > 512) ? S / 32 : 16;  // bytes per lane per neighbour
+    constexpr int G = S / CH;                     // lanes per neighbour
+    constexpr int P = 32 / G;                     // neighbours per warp-wide load
+    constexpr int V4 = CH / 16;                   // uint4 per lane per neighbour
+    constexpr int U = (V4 == 1) ? 4 : 2;          // loads per lane in flight
+    extern __shared__ uint32_t s_ids[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *ids = s_ids + wib * 32;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= n) return;
+    const uint32_t v = (uint32_t)warp;
+    const int g = lane / G, sub = lane % G;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    uint4 acc[V4];
+#pragma unroll
+    for (int q = 0; q < V4; q++) acc[q] = make_uint4(0, 0, 0, 0);
+
+    uint64_t pos = off[v];
+    const uint64_t end = off[v + 1];
+    uint32_t base = 0;
+    while (pos < end) {
+        const WindowDecode<uint32_t> r = decode_window<uint32_t>(bytes, pos, end, base, lane);
+        const uint32_t T = r.term_mask;
+        if (T == 0) break;  // cannot happen on a validated graph; guarantees progress
+        if ((T >> lane) & 1u) ids[__popc(T & lt_mask)] = r.id;
+        __syncwarp();
+        const int cnt = __popc(T);
+        for (int k0 = 0; k0 < cnt; k0 += P * U) {
+            uint4 x[U][V4];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int k = k0 + u * P + g;
+                if (k < cnt) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(cur + (uint64_t)ids[k] * S + sub * CH);
+#pragma unroll
+                    for (int q = 0; q < V4; q++) x[u][q] = __ldg(src + q);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int q = 0; q < V4; q++) acc[q] = vmax4(acc[q], x[u][q]);
+        }
+        __syncwarp();
+        base = r.next_base;
+        pos += (uint64_t)r.advance;
+    }
+    // fold the P lane groups together
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < V4; q++) {
+            uint4 y;
+            y.x = __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+            y.y = __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+            y.z = __shfl_xor_sync(0xffffffffu, acc[q].z, o);
+            y.w = __shfl_xor_sync(0xffffffffu, acc[q].w, o);
+            acc[q] = vmax4(acc[q], y);
+        }
+    bool changed = false;
+    if (g == 0) {
+        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * CH);
+        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * CH);
+#pragma unroll
+        for (int q = 0; q < V4; q++) {
+            const uint4 o4 = __ldg(own + q);
+            const uint4 res = vmax4(acc[q], o4);
+            dst[q] = res;
+            changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
+        }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) {
+        if (*reinterpret_cast<volatile uint32_t *>(flags) == 0u) atomicOr(flags, 1u);
+    }
+}
+
+// Correctly rounded (to nearest, ties to even) conversion of hi*2^64 + lo to
+// double: shift the value into 64 bits keeping a sticky bit for everything
+// shifted out, let the hardware round the 64-bit integer, scale back exactly.
+__device__ __forceinline__ double u128_to_double(uint64_t hi, uint64_t lo) {
+    if (hi == 0) return __ull2double_rn(lo);
+    const int k = 64 - __clzll((long long)hi);  // significant bits in hi, 1..64
+    uint64_t y, sticky;
+    if (k == 64) {
+        y = hi;
+        sticky = lo != 0;
+    } else {
+        y = (hi << (64 - k)) | (lo >> k);
+        sticky = (lo & ((1ull << k) - 1ull)) != 0;
+    }
+    const double scale = __longlong_as_double((long long)(1023 + k) << 52);  // 2^k
+    return __dmul_rn(__ull2double_rn(y | sticky), scale);
+}
+
+// HLL estimator (Sec. 2.3, Sec. 3.3) for every node, then Eq. sumD.
+// The harmonic sum Z = sum_j 2^-M[j] is formed exactly as the integer
+// Z * 2^(65-p) (zero registers V * 2^(65-p) plus 2^(65-p-M) for M >= 1) and
+// rounded once, so the result does not depend on summation order.
+// E = alpha_m m^2 / Z; c = lc[V] = m ln(m/V) if E <= 2.5m and V > 0, else E.
+// For t >= 1: sum_d += t * (c - c_prev), and flags[1] records
+// max_v(c - c_prev) > 0.5 (the paper's convergence test).
+__global__ void hb_estimate_kernel(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, int t,
+                                   double alpha_mm, const double *__restrict__ lc, const double *__restrict__ c_prev,
+                                   double *__restrict__ c_cur, double *__restrict__ sum_d,
+                                   uint32_t *__restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= n) return;
+    const uint32_t v = (uint32_t)warp;
+    const uint32_t m = 1u << p;
+    const int K = 65 - p;
+    uint64_t lo = 0, hi = 0;
+    uint32_t zeros = 0;
+    for (uint32_t q = lane; q * 16u < m; q += 32) {
+        const uint32_t r0 = q * 16u;
+        const uint32_t s = r0 / (uint32_t)S, o = r0 % (uint32_t)S;
+        const uint4 x = *reinterpret_cast<const uint4 *>(regs + ((uint64_t)s * n + v) * (uint64_t)S + o);
+        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const uint32_t M = (wv[i] >> (8 * b)) & 0xFFu;
+                if (M == 0) {
+                    zeros++;
+                } else {
+                    const uint64_t term = 1ull << (K - (int)M);
+                    lo += term;
+                    hi += (lo < term);
+                }
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+        const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo += olo;
+        hi += ohi + (lo < olo);
+    }
+    if (lane != 0) return;
+    // add V * 2^K (V <= 2^16, K <= 61: fits in 128 bits)
+    const uint64_t zlo = (uint64_t)zeros << K;
+    const uint64_t zhi = (uint64_t)zeros >> (64 - K);
+    lo += zlo;
+    hi += zhi + (lo < zlo);
+    const double inv_scale = __longlong_as_double((long long)(1023 - K) << 52);  // 2^-K
+    const double Z = __dmul_rn(u128_to_double(hi, lo), inv_scale);
+    const double E = __ddiv_rn(alpha_mm, Z);
+    const double c = (E <= 2.5 * (double)m && zeros > 0) ? lc[zeros] : E;
+    if (t > 0) {
+        const double diff = __dsub_rn(c, c_prev[v]);
+        sum_d[v] = __dadd_rn(sum_d[v], __dmul_rn((double)t, diff));
+        if (diff > 0.5 && *reinterpret_cast<volatile uint32_t *>(flags + 1) == 0u) atomicOr(flags + 1, 1u);
+    }
+    c_cur[v] = c;
+}
+
+// MD(v) = sum_d[v] / (N_v - 1) (Sec. 3.3), NaN when N_v <= 1; ball = c_t.
+__global__ void hb_finalize_kernel(uint32_t n, const uint32_t *__restrict__ comp, const double *__restrict__ sum_d,
+                                   const double *__restrict__ c, double *__restrict__ md, double *__restrict__ ball) {
+    const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const double nv = comp ? (double)comp[v] : (double)n;
+    if (md) md[v] = (nv <= 1.0) ? __longlong_as_double(0x7FF8000000000000ll) : __ddiv_rn(sum_d[v], __dsub_rn(nv, 1.0));
+    if (ball) ball[v] = c[v];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct Plan {
+    int p = 10;
+    uint32_t m = 1024;
+    int S = 1024;          // slice bytes
+    int slices = 1;
+    int warps = 8;         // union kernel warps per CTA
+    uint64_t n = 0;
+    // workspace layout (byte offsets, 256-aligned)
+    uint64_t off_cur = 0, off_next = 0, off_c0 = 0, off_c1 = 0, off_sum = 0, off_lc = 0, off_flags = 0, total = 0;
+};
+
+static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P) {
+    if (p < 4 || p > 16) {
+        set_error("precision p = %d is outside 4..16", p);
+        return VGA_EINVAL;
+    }
+    P->p = p;
+    P->m = 1u << p;
+    P->n = g->n;
+    int S = tune ? tune->slice_bytes : 0;
+    if (S != 0) {
+        if (S < 16 || S > 1024 || (S & (S - 1)) || (uint32_t)S > P->m) {
+            set_error("slice_bytes = %d must be a power of two in [16, min(2^p, 1024)]", S);
+            return VGA_EINVAL;
+        }
+    } else {
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device);
+        uint64_t budget = (tune && tune->l2_budget_mb > 0) ? (uint64_t)tune->l2_budget_mb << 20
+                                                           : (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
+        S = (int)std::min<uint32_t>(P->m, 1024u);
+        while (S > 16 && (uint64_t)S * P->n > budget) S >>= 1;
+    }
+    P->S = S;
+    P->slices = (int)(P->m / (uint32_t)S);
+    P->warps = (tune && tune->warps_per_cta > 0) ? tune->warps_per_cta : 8;
+    if (P->warps > 16) {
+        set_error("warps_per_cta = %d exceeds 16", P->warps);
+        return VGA_EINVAL;
+    }
+    const uint64_t regs = (uint64_t)P->n * P->m;
+    uint64_t o = 0;
+    P->off_cur = o;   o = align256(o + regs);
+    P->off_next = o;  o = align256(o + regs);
+    P->off_c0 = o;    o = align256(o + 8 * P->n);
+    P->off_c1 = o;    o = align256(o + 8 * P->n);
+    P->off_sum = o;   o = align256(o + 8 * P->n);
+    P->off_lc = o;    o = align256(o + 8 * ((uint64_t)P->m + 1));
+    P->off_flags = o; o = align256(o + 64);
+    P->total = o;
+    return VGA_OK;
+}
+
+static double hll_alpha(int p) {
+    const double m = (double)(1u << p);
+    if (p == 4) return 0.673;
+    if (p == 5) return 0.697;
+    if (p == 6) return 0.709;
+    return 0.7213 / (1.0 + 1.079 / m);
+}
+
+// Linear-counting table m ln(m / V), V = 1..m, computed once per p on the host
+// so that the device and any host consumer see the same doubles.
+static const std::vector<double> &lc_table(int p) {
+    static std::vector<double> tables[17];
+    static bool ready[17] = {false};
+    if (!ready[p]) {
+        const uint32_t m = 1u << p;
+        std::vector<double> t(m + 1, 0.0);
+        for (uint32_t V = 1; V <= m; V++) t[V] = (double)m * std::log((double)m / (double)V);
+        tables[p].swap(t);
+        ready[p] = true;
+    }
+    return tables[p];
+}
+
+static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, uint8_t *nxt, uint32_t *flags,
+                        cudaStream_t stream) {
+    const unsigned blocks = (unsigned)((P.n + P.warps - 1) / P.warps);
+    const size_t smem = (size_t)P.warps * 32 * sizeof(uint32_t);
+    const uint64_t slice_bytes = (uint64_t)P.n * P.S;
+    for (int s = 0; s < P.slices; s++) {
+        const uint8_t *c = cur + (uint64_t)s * slice_bytes;
+        uint8_t *x = nxt + (uint64_t)s * slice_bytes;
+        switch (P.S) {
+#define VGA_CASE(SS)                                                                                            \
+    case SS:                                                                                                    \
+        hb_union_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n, \
+                                                                    flags);                                     \
+        break;
+            VGA_CASE(16)
+            VGA_CASE(32)
+            VGA_CASE(64)
+            VGA_CASE(128)
+            VGA_CASE(256)
+            VGA_CASE(512)
+            VGA_CASE(1024)
+#undef VGA_CASE
+            default:
+                set_error("internal: slice width %d", P.S);
+                return VGA_EINVAL;
+        }
+    }
+    VGA_CHECK_CUDA(cudaGetLastError());
+    return VGA_OK;
+}
+
+static int launch_estimate(const Plan &P, const uint8_t *regs, int t, const double *lc, const double *c_prev,
+                           double *c_cur, double *sum_d, uint32_t *flags, cudaStream_t stream) {
+    const int warps = 8;
+    const unsigned blocks = (unsigned)((P.n + warps - 1) / warps);
+    const double alpha_mm = hll_alpha(P.p) * (double)P.m * (double)P.m;
+    hb_estimate_kernel<<<blocks, warps * 32, 0, stream>>>(regs, (uint32_t)P.n, P.p, P.S, t, alpha_mm, lc, c_prev,
+                                                          c_cur, sum_d, flags);
+    VGA_CHECK_CUDA(cudaGetLastError());
+    return VGA_OK;
+}
+
+static int copy_trace(const Plan &P, const uint8_t *regs, const double *c, int slot, uint8_t *trace_regs,
+                      double *trace_c, cudaStream_t stream) {
+    if (trace_regs) {
+        uint8_t *dst = trace_regs + (uint64_t)slot * P.n * P.m;
+        for (int s = 0; s < P.slices; s++)
+            VGA_CHECK_CUDA(cudaMemcpy2DAsync(dst + (uint64_t)s * P.S, P.m, regs + (uint64_t)s * P.n * P.S, P.S, P.S,
+                                             P.n, cudaMemcpyDeviceToHost, stream));
+    }
+    if (trace_c)
+        VGA_CHECK_CUDA(cudaMemcpyAsync(trace_c + (uint64_t)slot * P.n, c, 8 * P.n, cudaMemcpyDeviceToHost, stream));
+    return VGA_OK;
+}
+
+static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *md_dev, double *ball_dev,
+                    int *iterations, void *ws, uint64_t ws_bytes, cudaStream_t stream, const vga_tuning *tune,
+                    uint8_t *trace_regs, double *trace_c, int max_trace) {
+    if (!g) {
+        set_error("null graph");
+        return VGA_EINVAL;
+    }
+    if (conv_mode != 0 && conv_mode != 1) {
+        set_error("conv_mode = %d must be 0 or 1", conv_mode);
+        return VGA_EINVAL;
+    }
+    Plan P;
+    VGA_TRY(make_plan(g, p, tune, &P));
+    DeviceBuffer own_ws;
+    if (!ws) {
+        VGA_TRY(own_ws.alloc(P.total));
+        ws = own_ws.ptr;
+    } else if (ws_bytes < P.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) {
+        set_error("workspace of %llu bytes at %p: need %llu bytes, 256-byte aligned", (unsigned long long)ws_bytes,
+                  ws, (unsigned long long)P.total);
+        return VGA_EINVAL;
+    }
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    uint8_t *cur = base + P.off_cur;
+    uint8_t *nxt = base + P.off_next;
+    double *c_prev = reinterpret_cast<double *>(base + P.off_c0);
+    double *c_cur = reinterpret_cast<double *>(base + P.off_c1);
+    double *sum_d = reinterpret_cast<double *>(base + P.off_sum);
+    double *lc = reinterpret_cast<double *>(base + P.off_lc);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(base + P.off_flags);
+
+    const std::vector<double> &table = lc_table(p);
+    VGA_CHECK_CUDA(cudaMemcpyAsync(lc, table.data(), 8 * table.size(), cudaMemcpyHostToDevice, stream));
+    int t = 0;
+    if (P.n > 0) {
+        VGA_CHECK_CUDA(cudaMemsetAsync(cur, 0, P.n * P.m, stream));
+        VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
+        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed);
+        VGA_CHECK_CUDA(cudaGetLastError());
+        VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0
+        if (max_trace >= 0) VGA_TRY(copy_trace(P, cur, c_prev, 0, trace_regs, trace_c, stream));
+        uint32_t hflags[2];
+        for (t = 1;; t++) {
+            VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
+            VGA_TRY(launch_union(P, g, cur, nxt, flags, stream));
+            VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
+            if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
+            VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, stream));
+            VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+            std::swap(cur, nxt);
+            std::swap(c_prev, c_cur);
+            const bool stop = (conv_mode == 1) ? (hflags[1] == 0) : (hflags[0] == 0);
+            if (stop || (d > 0 && t >= d)) break;
+        }
+        hb_finalize_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>((uint32_t)P.n, g->d_comp, sum_d,
+                                                                               c_prev, md_dev, ball_dev);
+        VGA_CHECK_CUDA(cudaGetLastError());
+    }
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    if (iterations) *iterations = t;
+    return VGA_OK;
+}
+
+}  // namespace
+}  // namespace vga
+
+using namespace vga;
+
+extern "C" {
+
+int hyperball_workspace_bytes(const vga_graph *g, int p, uint64_t *bytes) {
+    clear_error();
+    if (!g || !bytes) {
+        set_error("hyperball_workspace_bytes: null argument");
+        return VGA_EINVAL;
+    }
+    Plan P;
+    VGA_TRY(make_plan(g, p, nullptr, &P));
+    *bytes = P.total;
+    return VGA_OK;
+}
+
+int hyperball_run_dev(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth_dev,
+                      double *ball_size_dev, int *iterations, void *workspace_dev, uint64_t workspace_bytes,
+                      void *stream, const vga_tuning *tuning) {
+    clear_error();
+    return run_impl(g, p, d, seed, conv_mode, mean_depth_dev, ball_size_dev, iterations, workspace_dev,
+                    workspace_bytes, static_cast<cudaStream_t>(stream), tuning, nullptr, nullptr, -1);
+}
+
+static int run_host_outputs(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth,
+                            double *ball_size, int *iterations, uint8_t *trace_regs, double *trace_c, int max_trace,
+                            const vga_tuning *tuning) {
+    clear_error();
+    if (!g) {
+        set_error("null graph");
+        return VGA_EINVAL;
+    }
+    DeviceBuffer out;
+    VGA_TRY(out.alloc(16 * (size_t)(g->n ? g->n : 1)));
+    double *md = out.as<double>();
+    double *ball = md + g->n;
+    cudaStream_t stream = 0;
+    VGA_TRY(run_impl(g, p, d, seed, conv_mode, md, ball, iterations, nullptr, 0, stream, tuning, trace_regs, trace_c,
+                     max_trace));
+    if (g->n) {
+        if (mean_depth) VGA_CHECK_CUDA(cudaMemcpy(mean_depth, md, 8 * (size_t)g->n, cudaMemcpyDeviceToHost));
+        if (ball_size) VGA_CHECK_CUDA(cudaMemcpy(ball_size, ball, 8 * (size_t)g->n, cudaMemcpyDeviceToHost));
+    }
+    return VGA_OK;
+}
+
+int hyperball_run(const vga_graph *g, int p, int d, uint64_t seed, double *mean_depth, double *ball_size,
+                  int *iterations) {
+    return run_host_outputs(g, p, d, seed, 0, mean_depth, ball_size, iterations, nullptr, nullptr, -1, nullptr);
+}
+
+int hyperball_run_trace(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth,
+                        double *ball_size, int *iterations, uint8_t *regs_host, double *c_host, int max_trace,
+                        const vga_tuning *tuning) {
+    return run_host_outputs(g, p, d, seed, conv_mode, mean_depth, ball_size, iterations, regs_host, c_host,
+                            max_trace, tuning);
+}
+
+}  // extern "C"

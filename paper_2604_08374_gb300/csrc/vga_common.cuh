@@ -1,0 +1,180 @@
+// vga_common.cuh -- internal declarations shared by the library's translation
+// units: the graph object, error reporting, RAII device buffers, and the warp
+// LEB128 decoder used by the validation and union kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "vga_hyperball.h"
+
+// Device-resident compressed CSR (Sec. 3.2, "CompressedCsr": u64 byte offsets,
+// u32 degrees, the LEB128 byte stream).  The byte buffer is over-allocated by
+// kBytePad zero bytes so vector loads near the end stay inside the allocation.
+struct vga_graph {
+    int device = 0;
+    uint32_t n = 0;
+    uint64_t n_bytes = 0;
+    uint64_t n_edges = 0;
+    uint32_t max_degree = 0;
+    uint64_t *d_offsets = nullptr;  // n+1
+    uint8_t *d_bytes = nullptr;     // n_bytes + kBytePad
+    uint32_t *d_degree = nullptr;   // n
+    uint32_t *d_comp = nullptr;     // n, or nullptr: every node in one component of size n
+};
+
+namespace vga {
+
+constexpr uint64_t kBytePad = 256;
+
+// Thread-local last-error message (vga_last_error).
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define VGA_CHECK_CUDA(call)                                                                   \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            ::vga::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                        \
+            return (e_ == cudaErrorMemoryAllocation) ? VGA_ENOMEM : VGA_ECUDA;                 \
+        }                                                                                      \
+    } while (0)
+
+#define VGA_TRY(expr)              \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != VGA_OK) return rc_; \
+    } while (0)
+
+// Owning device allocation, freed on scope exit unless released.
+struct DeviceBuffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DeviceBuffer() = default;
+    DeviceBuffer(const DeviceBuffer &) = delete;
+    DeviceBuffer &operator=(const DeviceBuffer &) = delete;
+    ~DeviceBuffer() { reset(); }
+    int alloc(size_t nbytes) {
+        reset();
+        if (nbytes == 0) nbytes = 256;
+        cudaError_t e = cudaMalloc(&ptr, nbytes);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            set_error("cudaMalloc(%zu bytes) failed: %s", nbytes, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? VGA_ENOMEM : VGA_ECUDA;
+        }
+        bytes = nbytes;
+        return VGA_OK;
+    }
+    void reset() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    void *release() {
+        void *p = ptr;
+        ptr = nullptr;
+        bytes = 0;
+        return p;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Pinned host scratch for small device->host reads.
+struct PinnedBuffer {
+    void *ptr = nullptr;
+    PinnedBuffer() = default;
+    PinnedBuffer(const PinnedBuffer &) = delete;
+    ~PinnedBuffer() {
+        if (ptr) cudaFreeHost(ptr);
+    }
+    int alloc(size_t nbytes) {
+        cudaError_t e = cudaMallocHost(&ptr, nbytes);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            set_error("cudaMallocHost failed: %s", cudaGetErrorString(e));
+            return VGA_ENOMEM;
+        }
+        return VGA_OK;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Creates a graph object around already-copied device offsets and bytes:
+// validates the stream on the device, derives degrees and E.  Takes
+// ownership of the device pointers on success (and frees them on failure).
+int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t *d_bytes, const uint32_t *comp_host,
+                      cudaStream_t stream, vga_graph **out);
+
+// ---------------------------------------------------------------------------
+// Warp LEB128 window decoder (Sec. 3.2 encoding; the paper decodes each list
+// with one thread into shared memory, here a whole warp decodes 32 bytes per
+// step).  The window starts on a varint boundary at `pos`; lane i holds byte
+// pos+i.  Terminators (high bit clear) are found with a ballot, each
+// terminator lane assembles its varint from up to four preceding bytes with
+// shuffles, and an inclusive warp scan of the values turns first-absolute /
+// then-delta values into ids.  Varints that do not end inside the window are
+// left for the next step.
+// ---------------------------------------------------------------------------
+template <class Id>
+struct WindowDecode {
+    uint32_t term_mask;  // lanes holding the last byte of a complete varint
+    int advance;         // bytes consumed (last terminator lane + 1), 0 if none
+    Id id;               // per lane: decoded id (valid on terminator lanes)
+    Id next_base;        // id of the window's last complete varint
+    uint32_t value;      // per lane: the varint's value (terminator lanes)
+    int bad;             // per lane: varint longer than 5 bytes or above 32 bits
+};
+
+// Id = uint32_t for the hot path (graphs are validated at load); uint64_t for
+// validation, so that a wrapping sum is seen rather than hidden.
+template <class Id>
+__device__ __forceinline__ WindowDecode<Id> decode_window(const uint8_t *__restrict__ bytes, uint64_t pos,
+                                                          uint64_t end, Id base, int lane) {
+    WindowDecode<Id> r;
+    const bool in = pos + (uint64_t)lane < end;
+    const uint32_t b = in ? (uint32_t)__ldg(bytes + pos + lane) : 0x80u;
+    const bool term = in && !(b & 0x80u);
+    const uint32_t T = __ballot_sync(0xffffffffu, term);
+    r.term_mask = T;
+    r.advance = T ? 32 - __clz(T) : 0;
+    const uint32_t b1 = __shfl_up_sync(0xffffffffu, b, 1);
+    const uint32_t b2 = __shfl_up_sync(0xffffffffu, b, 2);
+    const uint32_t b3 = __shfl_up_sync(0xffffffffu, b, 3);
+    const uint32_t b4 = __shfl_up_sync(0xffffffffu, b, 4);
+    const uint32_t below = T & ((1u << lane) - 1u);
+    const int start = below ? 32 - __clz(below) : 0;
+    const int len = lane - start + 1;
+    uint64_t v = 0;
+    r.bad = 0;
+    if (term) {
+        v = b & 0x7Fu;
+        if (len >= 2) v = (v << 7) | (b1 & 0x7Fu);
+        if (len >= 3) v = (v << 7) | (b2 & 0x7Fu);
+        if (len >= 4) v = (v << 7) | (b3 & 0x7Fu);
+        if (len >= 5) v = (v << 7) | (b4 & 0x7Fu);
+        if (len > 5 || v > 0xFFFFFFFFull) r.bad = 1;
+    }
+    r.value = (uint32_t)v;
+    Id s = (Id)(uint32_t)v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Id t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+    }
+    r.id = base + s;
+    r.next_base = T ? __shfl_sync(0xffffffffu, r.id, r.advance - 1) : base;
+    return r;
+}
+
+__device__ __forceinline__ uint4 vmax4(uint4 a, uint4 b) {
+    return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z), __vmaxu4(a.w, b.w));
+}
+
+}  // namespace vga

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Registers are compared bit for bit after every pass, as are the HLL estimates
+c_t (both sides form the harmonic sum exactly and round once), the iteration
+count, and Visual Mean Depth (bit-exact here; the stated tolerance, 1e-6
+relative, is asserted as well).  Sizes span several slices and CTAs with
+ragged tails: the tiny 32 x 32 configuration (N ~ 900, ~4e5 edges) and small
+grids, at p from 4 to 12, forced slice widths from 16 to 1024 bytes, several
+CTA sizes, both convergence rules, d = 1, 3 and unlimited.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+MD_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def vga():
+    from paper_2604_08374_gb300 import build
+    build.build()
+    import paper_2604_08374_gb300 as v
+    return v
+
+
+_cache = {}
+
+
+def tiny_graph(seed):
+    if seed not in _cache:
+        obst = workloads.tiny(seed)
+        off, b, cells = oracle.build_graph(obst)
+        _cache[seed] = (obst, off, b, cells)
+    return _cache[seed]
+
+
+def assert_same_run(got, ref, check_regs=True):
+    assert got["iterations"] == ref["iterations"]
+    T = got["iterations"]
+    for t in range(T + 1):
+        if check_regs:
+            assert np.array_equal(got["regs"][t], ref["regs"][t]), f"registers differ after pass {t}"
+        assert np.array_equal(got["c"][t], ref["c"][t]), f"estimates differ after pass {t}"
+    np.testing.assert_allclose(got["mean_depth"], ref["mean_depth"], rtol=MD_RTOL, atol=0)
+    assert np.array_equal(got["mean_depth"], ref["mean_depth"], equal_nan=True)
+    assert np.array_equal(got["ball"], ref["ball"])
+
+
+# ----------------------------------------------------------------------------
+# graph residency and the builder
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_load_round_trip(vga, seed):
+    _, off, b, cells = tiny_graph(seed)
+    row_ptr, _ = oracle.decode_csr(off, b)
+    with vga.vga_graph_load(off, b) as g:
+        assert (g.n_nodes, g.n_bytes, g.n_edges) == (len(cells), len(b), int(row_ptr[-1]))
+        o2, b2, deg = g.copy_csr()
+        assert np.array_equal(o2, off) and np.array_equal(b2, b)
+        assert np.array_equal(deg, np.diff(row_ptr.astype(np.int64)))
+
+
+@pytest.mark.parametrize("grid", ["tiny1", "tiny2", "tiny3", "tiny4", "tiny5", "rect40x23", "open9x7", "thin1x50",
+                                  "wall", "maze"])
+def test_builder_matches_oracle(vga, grid):
+    if grid.startswith("tiny"):
+        obst = workloads.tiny(int(grid[4:]))
+    elif grid == "rect40x23":
+        obst = workloads.random_rectangles(40, 23, 9, (1, 7), seed=11)
+    elif grid == "open9x7":
+        obst = workloads.open_grid(9, 7)
+    elif grid == "thin1x50":
+        obst = workloads.open_grid(50, 1)
+    elif grid == "wall":
+        obst = workloads.open_grid(20, 12)
+        obst[:, 9] = 1
+        obst[5, 9] = 0
+    else:
+        rng = np.random.default_rng(3)
+        obst = (rng.random((37, 41)) < 0.3).astype(np.uint8)
+    off, b, cells = oracle.build_graph(obst)
+    g, gcells = vga.vga_visibility_build(obst, return_cells=True)
+    with g:
+        o2, b2, _ = g.copy_csr()
+        assert np.array_equal(gcells.astype(np.int64), cells)
+        assert np.array_equal(o2, off)
+        assert np.array_equal(b2, b)
+        assert g.n_nodes == vga.vga_visibility_count(obst)
+
+
+# ----------------------------------------------------------------------------
+# HyperBall, bit-exact at every pass
+# ----------------------------------------------------------------------------
+
+CASES = [
+    # seed, p, d, slice_bytes, warps_per_cta, conv_mode
+    (1, 10, 3, 0, 0, 0),
+    (1, 10, 0, 0, 0, 0),
+    (2, 10, 0, 256, 8, 0),
+    (3, 10, 0, 64, 4, 0),
+    (4, 8, 3, 16, 16, 0),
+    (5, 12, 3, 1024, 8, 0),
+    (1, 4, 0, 16, 3, 0),
+    (2, 6, 0, 32, 5, 0),
+    (3, 12, 2, 512, 1, 0),
+    (1, 10, 0, 128, 8, 1),
+    (2, 9, 1, 0, 7, 0),
+]
+
+
+@pytest.mark.parametrize("seed,p,d,S,warps,conv", CASES)
+def test_hyperball_bit_exact(vga, seed, p, d, S, warps, conv):
+    _, off, b, cells = tiny_graph(seed)
+    T = 12
+    ref = oracle.hyperball(off, b, p, d, seed=seed * 7, conv_mode=conv, trace=T)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, p, d, seed=seed * 7, conv_mode=conv, max_trace=T, slice_bytes=S,
+                                      warps_per_cta=warps)
+    assert got["iterations"] <= T
+    assert_same_run(got, ref)
+
+
+def test_hyperball_run_plain(vga):
+    _, off, b, cells = tiny_graph(1)
+    ref = oracle.hyperball(off, b, 10, 3, seed=0)
+    with vga.vga_graph_load(off, b) as g:
+        md, ball, it = vga.hyperball_run(g, 10, 3, 0)
+    assert it == ref["iterations"] == 3
+    assert np.array_equal(md, ref["mean_depth"]) and np.array_equal(ball, ref["ball"])
+
+
+def test_hyperball_hash_seed_large(vga):
+    _, off, b, _ = tiny_graph(2)
+    seed = 0xDEADBEEFCAFEF00D
+    ref = oracle.hyperball(off, b, 10, 0, seed=seed, trace=10)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, 10, 0, seed=seed, max_trace=10)
+    assert_same_run(got, ref)
+
+
+def test_component_sizes_and_isolated_nodes(vga):
+    # two components of the visibility graph kept together, with their exact sizes
+    obst = workloads.open_grid(12, 7)
+    obst[:, 5] = 1
+    _, cells = oracle.main_component(workloads.open_grid(5, 7))
+    rp1, col1 = oracle.visibility_csr(workloads.open_grid(5, 7), cells)
+    n1 = len(cells)
+    rp2, col2 = oracle.visibility_csr(workloads.open_grid(6, 7), oracle.main_component(workloads.open_grid(6, 7))[1])
+    n2 = len(rp2) - 1
+    row_ptr = np.concatenate([rp1, rp2[1:] + rp1[-1], [rp1[-1] + rp2[-1]]]).astype(np.uint64)
+    col = np.concatenate([col1, col2 + n1]).astype(np.uint32)
+    n = n1 + n2 + 1  # plus one isolated node
+    off, b = oracle.csr_encode(row_ptr, col)
+    comp = np.array([n1] * n1 + [n2] * n2 + [1], np.uint32)
+    ref = oracle.hyperball(off, b, 8, 0, comp_size=comp, trace=8)
+    with vga.vga_graph_load(off, b, comp_size=comp) as g:
+        got = vga.hyperball_run_trace(g, 8, 0, max_trace=8)
+    assert_same_run(got, ref)
+    assert math.isnan(got["mean_depth"][-1])
+
+
+def test_degenerate_graphs(vga):
+    for n in (0, 1):
+        off = np.zeros(n + 1, np.uint64)
+        ref = oracle.hyperball(off, np.zeros(0, np.uint8), 10, 0, trace=2)
+        with vga.vga_graph_load(off, np.zeros(0, np.uint8)) as g:
+            got = vga.hyperball_run_trace(g, 10, 0, max_trace=2)
+        assert got["iterations"] == ref["iterations"]
+        assert np.array_equal(np.isnan(got["mean_depth"]), np.isnan(ref["mean_depth"]))
+    off, b, _ = oracle.build_graph(workloads.open_grid(2, 1))
+    ref = oracle.hyperball(off, b, 10, 0, trace=3)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, 10, 0, max_trace=3)
+    assert_same_run(got, ref)
+
+
+# ----------------------------------------------------------------------------
+# errors
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("stream,n", [
+    (bytes([0x80]), 2),                          # unterminated varint
+    (bytes([0x81, 0x81, 0x81, 0x81, 0x81, 0x01]), 2),  # six-byte varint
+    (bytes([0x01, 0x00]), 3),                    # duplicate neighbour (zero delta)
+    (bytes([0x05]), 3),                          # id >= n
+    (bytes([0x00]), 2),                          # self loop on node 0
+    (bytes([0xFF, 0xFF, 0xFF, 0xFF, 0x7F]), 2),  # value above 32 bits
+])
+def test_corrupt_streams_rejected(vga, stream, n):
+    off = np.zeros(n + 1, np.uint64)
+    off[1:] = len(stream)
+    with pytest.raises(vga.VgaError) as e:
+        vga.vga_graph_load(off, np.frombuffer(stream, np.uint8).copy())
+    assert e.value.status == vga.VGA_ECORRUPT
+
+
+def test_bad_offsets_rejected(vga):
+    with pytest.raises(vga.VgaError) as e:
+        vga.vga_graph_load(np.array([0, 2, 1], np.uint64), np.array([1, 0], np.uint8))
+    assert e.value.status == vga.VGA_ECORRUPT
+
+
+def test_bad_arguments(vga):
+    _, off, b, _ = tiny_graph(1)
+    with vga.vga_graph_load(off, b) as g:
+        for p in (3, 17):
+            with pytest.raises(vga.VgaError) as e:
+                vga.hyperball_run(g, p, 3, 0)
+            assert e.value.status == vga.VGA_EINVAL
+        for S in (8, 48, 2048):
+            with pytest.raises(vga.VgaError):
+                vga.hyperball_run_trace(g, 10, 1, slice_bytes=S, max_trace=1)
+        with pytest.raises(vga.VgaError):
+            vga.hyperball_run_trace(g, 6, 1, slice_bytes=128, max_trace=1)  # slice wider than m = 64
+
+
+# ----------------------------------------------------------------------------
+# device outputs, user workspace, streams, files
+# ----------------------------------------------------------------------------
+
+def test_run_dev_with_torch_buffers(vga):
+    torch = pytest.importorskip("torch")
+    _, off, b, cells = tiny_graph(3)
+    n = len(cells)
+    ref = oracle.hyperball(off, b, 10, 0, seed=5)
+    with vga.vga_graph_load(off, b) as g:
+        ws = torch.empty(vga.hyperball_workspace_bytes(g, 10), dtype=torch.uint8, device="cuda")
+        md = torch.empty(n, dtype=torch.float64, device="cuda")
+        ball = torch.empty(n, dtype=torch.float64, device="cuda")
+        s = torch.cuda.Stream()
+        it = vga.hyperball_run_dev(g, 10, 0, 5, md, ball, workspace=ws, stream=s)
+        s.synchronize()
+    assert it == ref["iterations"]
+    assert np.array_equal(md.cpu().numpy(), ref["mean_depth"])
+    assert np.array_equal(ball.cpu().numpy(), ref["ball"])
+
+
+def test_file_round_trip(vga, tmp_path):
+    _, off, b, _ = tiny_graph(2)
+    path = str(tmp_path / "g.vgacsr")
+    with vga.vga_graph_load(off, b) as g:
+        g.save(path)
+    with vga.vga_graph_load_file(path) as g2:
+        o2, b2, _ = g2.copy_csr()
+    assert np.array_equal(o2, off) and np.array_equal(b2, b)
+    with open(path, "r+b") as f:
+        f.write(b"XXXX")
+    with pytest.raises(vga.VgaError) as e:
+        vga.vga_graph_load_file(path)
+    assert e.value.status == vga.VGA_ECORRUPT

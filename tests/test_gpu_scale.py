@@ -1,0 +1,109 @@
+"""GPU parity at scale: a mid-size grid checked in full, and the ~42.7k-cell
+and 236k-cell configurations checked on sampled nodes and by properties that
+hold at any size, in the launch configuration the benchmark times (p = 10,
+automatic slice width and CTA size).
+
+Full check (96 x 96 grid, N ~ 8k, ~2e7 edges, p = 10, unlimited d, slices
+forced narrow so one pass spans several slice launches): registers, estimates
+and mean depth bit-exact against the oracle at every pass.
+
+Sampled checks (medium and city), each expected value computed by the oracle
+from the obstacle grid alone:
+  - the builder's neighbour list of each sampled node equals the oracle's;
+  - the initial counters equal the oracle's initialisation, for every node;
+  - after pass 1 a sampled node's counter equals the register-wise max of the
+    oracle's initial counters over the node and its oracle neighbours.
+Properties (every pass):
+  - Eq. hll-union holds at the sampled nodes between consecutive GPU passes;
+  - registers never decrease, for every node;
+  - each sampled estimate equals the oracle estimator applied to the GPU
+    counter, and the sampled mean depth equals Eq. sumD folded over them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vga():
+    from paper_2604_08374_gb300 import build
+    build.build()
+    import paper_2604_08374_gb300 as v
+    return v
+
+
+def test_mid_grid_full_parity(vga):
+    obst = workloads.rectangles_until(96, 96, (2, 12), int(96 * 96 * 0.88), seed=4)
+    off, b, cells = oracle.build_graph(obst)
+    ref = oracle.hyperball(off, b, 10, 0, seed=1, trace=16)
+    g = vga.vga_visibility_build(obst)
+    with g:
+        o2, b2, _ = g.copy_csr()
+        assert np.array_equal(o2, off) and np.array_equal(b2, b)
+        for S, warps in ((0, 0), (128, 8), (64, 12)):
+            got = vga.hyperball_run_trace(g, 10, 0, seed=1, max_trace=16, slice_bytes=S, warps_per_cta=warps)
+            assert got["iterations"] == ref["iterations"]
+            for t in range(got["iterations"] + 1):
+                assert np.array_equal(got["regs"][t], ref["regs"][t]), (S, t)
+                assert np.array_equal(got["c"][t], ref["c"][t]), (S, t)
+            assert np.array_equal(got["mean_depth"], ref["mean_depth"])
+
+
+def _sampled_checks(vga, obst, p, d, n_sample, seed=0, min_edges=None, max_edges=None):
+    g, gcells = vga.vga_visibility_build(obst, return_cells=True)
+    with g:
+        n = g.n_nodes
+        _, cells = oracle.main_component(obst)
+        assert np.array_equal(gcells.astype(np.int64), cells)
+        if min_edges is not None:
+            assert min_edges <= g.n_edges <= max_edges, g.n_edges
+        rng = np.random.default_rng(seed)
+        sample = np.unique(np.concatenate([[0, n - 1], rng.choice(n, n_sample, replace=False)])).astype(np.int64)
+        row_ptr, col = oracle.visibility_csr(obst, cells, nodes=sample)
+        nbrs = [col[row_ptr[k]:row_ptr[k + 1]] for k in range(len(sample))]
+        g_off, g_bytes, g_deg = g.copy_csr()
+        for k, v in enumerate(sample):
+            got = oracle.decode_list(g_bytes, int(g_off[v]), int(g_off[v + 1]), n)
+            assert np.array_equal(got, nbrs[k]), f"neighbour list of node {v}"
+        del g_bytes
+        out = vga.hyperball_run_trace(g, p, d, seed=seed, max_trace=max(d, 1))
+    regs, c, T = out["regs"], out["c"], out["iterations"]
+    if d > 0:
+        assert T == d
+    R0 = oracle.hll_init(n, p, seed)
+    assert np.array_equal(regs[0], R0)
+    for k, v in enumerate(sample):
+        expect = R0[np.concatenate([[v], nbrs[k]]).astype(np.int64)].max(axis=0)
+        assert np.array_equal(regs[1][v], expect), f"pass 1, node {v}"
+    for t in range(1, T + 1):
+        assert np.all(regs[t] >= regs[t - 1])
+        for k, v in enumerate(sample):
+            expect = np.maximum(regs[t - 1][v], regs[t - 1][nbrs[k].astype(np.int64)].max(axis=0))
+            assert np.array_equal(regs[t][v], expect), f"Eq. hll-union at pass {t}, node {v}"
+    for v in sample:
+        sum_d = 0.0
+        for t in range(T + 1):
+            assert c[t][v] == oracle.hll_estimate(regs[t][v], p), (t, v)
+            if t:
+                sum_d = oracle.accumulate(sum_d, t, c[t][v], c[t - 1][v])
+        assert out["mean_depth"][v] == sum_d / (n - 1)
+        assert out["ball"][v] == c[T][v]
+    return n, T
+
+
+def test_medium_config_sampled(vga):
+    # 220 x 220, sides 2..20, ~12 % cover, ~42.7k free cells; p = 10, d = 3
+    n, T = _sampled_checks(vga, workloads.medium(3), p=10, d=3, n_sample=48)
+    assert abs(n - 42_700) / 42_700 < 0.005
+
+
+@pytest.mark.slow
+def test_city_config_sampled(vga):
+    # 520 x 520 urban blocks, ~236k free cells, 4-5e9 directed edges; p = 10, d = 3
+    n, T = _sampled_checks(vga, workloads.city(2), p=10, d=3, n_sample=24, min_edges=4_000_000_000,
+                           max_edges=5_000_000_000)
+    assert abs(n - 236_000) / 236_000 < 0.005
