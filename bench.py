@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark: HyperBall GEdge-unions/s at p = 10 on the 236k-cell city graph.
+
+One step is one whole analysis (Algorithm 1): counter initialisation, c_0,
+d = 3 union passes (Eq. hll-union over the device-resident LEB128 CSR) with the
+HLL estimate and Eq. sumD after each, and Visual Mean Depth.  The metric is
+GEdge-unions/s = (passes x directed edges) / seconds / 1e9, the unit the
+paper's BFS-phase times translate to (Sec. 4.3 breakdown table).
+
+Workload (synthetic stand-in for the paper's 235,983-cell Valdivia graph,
+which is not available): the seeded 520 x 520 urban-block grid of
+workloads.city(2), 236,693 main-component cells, ~4.63e9 directed edges,
+~4.7 GB of compressed CSR, built on the GPU before timing.
+
+Arms:
+  default           the CUDA library; `value` is device-timed with the CSR and
+                    workspace resident, `e2e` goes through the public C API
+                    with host buffers (CSR copied in and results copied out
+                    every step).
+  --impl reference  the CPU oracle as it stands, on the host cores, over a
+                    bounded sample of the same workload (one union pass over
+                    sampled nodes per step).
+
+Multi-GPU: the analysis does not shard without a cross-device exchange, so
+`--gpus N` runs N independent replicas (weak scaling); value = all ranks'
+edge unions / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "GEdge-unions/s at p=10 (236k-cell city graph, d=3)"
+UNIT = "GEdge-unions/s"
+CONFIGS = {
+    "city": dict(grid=lambda: workloads.city(2), name="city 520x520 urban blocks, seed 2 (~236.7k cells, ~4.63e9 edges)"),
+    "medium": dict(grid=lambda: workloads.medium(3), name="medium 220x220, seed 3 (~42.7k cells, ~4.2e8 edges)"),
+    "tiny": dict(grid=lambda: workloads.tiny(1), name="tiny 32x32, seed 1 (903 cells)"),
+}
+PAPER_CONTEXT = {"paper_bfs_seconds_p10_d3_235983_cells_4.8e9_edges": 51.6,
+                 "paper_derived_geu_per_s": 0.28,
+                 "paper_hardware": "RTX 3080 Ti Laptop (sm_86), PCIe-streamed graph"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="city")
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--d", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample duration")
+    ap.add_argument("--cpu-sample", type=int, default=256, help="sampled nodes for the CPU oracle")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, d=unlimited and CPU baseline")
+    ap.add_argument("--slice-bytes", type=int, default=0, help="force the union slice width (0 = automatic)")
+    ap.add_argument("--warps", type=int, default=0, help="force union warps per CTA (0 = automatic)")
+    ap.add_argument("--backend", default="nccl")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ----------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self, backend):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def combine(units_local: float, seconds_local: float, dist: Dist):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    units = dist.sum(units_local)
+    seconds = dist.max(seconds_local)
+    return units, seconds
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+class OracleSample:
+    """One union pass of the CPU oracle over sampled nodes of the workload.
+
+    The sampled nodes' neighbour lists come from the oracle's own visibility
+    builder on the obstacle grid and its own encoder; the counters are its own
+    initialisation.  Nothing here comes from the CUDA library."""
+
+    def __init__(self, obst, p, seed, n_sample, rng_seed=12345):
+        import oracle
+        self.oracle = oracle
+        self.p = p
+        self.cores = oracle.default_threads()
+        _, cells = oracle.main_component(obst)
+        self.n = len(cells)
+        rng = np.random.default_rng(rng_seed)
+        self.sample = np.sort(rng.choice(self.n, min(n_sample, self.n), replace=False)).astype(np.int64)
+        row_ptr_s, col = oracle.visibility_csr(obst, cells, nodes=self.sample, nthreads=self.cores)
+        counts = np.zeros(self.n, np.int64)
+        counts[self.sample] = np.diff(row_ptr_s.astype(np.int64))
+        row_ptr = np.zeros(self.n + 1, np.uint64)
+        row_ptr[1:] = np.cumsum(counts)
+        self.offsets, self.bytes = oracle.csr_encode(row_ptr, col)
+        self.regs = oracle.hll_init(self.n, p, seed)
+        self.edges = int(row_ptr[-1])
+
+    def one_pass(self) -> tuple[float, int]:
+        t0 = time.perf_counter()
+        _, _, edges = self.oracle.union_pass(self.offsets, self.bytes, self.regs, self.p, nodes=self.sample,
+                                             nthreads=self.cores)
+        return time.perf_counter() - t0, edges
+
+    def describe(self, reps) -> str:
+        return (f"one Eq. hll-union pass (p={self.p}) over {len(self.sample)} sampled nodes of the "
+                f"{self.n}-node graph ({self.edges} edge unions), repeated {reps}x; lists from the oracle's own "
+                f"visibility builder")
+
+
+def cpu_baseline(obst, args) -> dict:
+    s = OracleSample(obst, args.p, args.seed, args.cpu_sample)
+    s.one_pass()  # warm caches
+    total_t, total_e, reps = 0.0, 0, 0
+    while total_t < args.cpu_seconds or reps < 1:
+        t, e = s.one_pass()
+        total_t += t
+        total_e += e
+        reps += 1
+    return {"value": total_e / total_t / 1e9, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+            "sample": s.describe(reps), "seconds": total_t}
+
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return
+    obst = CONFIGS[args.config]["grid"]()
+    s = OracleSample(obst, args.p, args.seed, args.cpu_sample)
+    for _ in range(args.warmup):
+        s.one_pass()
+    total_t, total_e = 0.0, 0
+    for _ in range(args.steps):
+        t, e = s.one_pass()
+        total_t += t
+        total_e += e
+    value = total_e / total_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
+                       "N": s.n, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+                             "sample": s.describe(args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_2604_08374_gb300/csrc/hyperball.cu", "paper_2604_08374_gb300/csrc/vga_common.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, config: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "union_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None, None
+    entry = rec.get(config, {})
+    if entry.get("kernel") != kernel or entry.get("src_sha") != kernel_source_sha():
+        return None, None
+    return entry.get("dram_bytes_per_launch"), entry.get("note")
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(args, dist: Dist):
+    import torch
+
+    from paper_2604_08374_gb300 import build as vga_build
+    vga_build.build()
+    import paper_2604_08374_gb300 as vga
+
+    torch.cuda.set_device(dist.local_rank)
+    dev = torch.device("cuda", dist.local_rank)
+    obst = CONFIGS[args.config]["grid"]()
+    t0 = time.perf_counter()
+    g = vga.vga_visibility_build(obst)
+    build_s = time.perf_counter() - t0
+    N, E, B = g.n_nodes, g.n_edges, g.n_bytes
+    ws = torch.empty(vga.hyperball_workspace_bytes(g, args.p), dtype=torch.uint8, device=dev)
+    md = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
+    ball = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(d):
+        return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=ws, stream=stream,
+                                     slice_bytes=args.slice_bytes, warps_per_cta=args.warps)
+
+    for _ in range(args.warmup):
+        step(args.d)
+
+    # ---- timed region: K analyses, inputs resident ----
+    vga.vga_profile_reset()
+    vga.vga_profile_enable(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    passes = 0
+    for _ in range(args.steps):
+        passes += step(args.d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clock_info = clocks.stop()
+    vga.vga_profile_enable(False)
+    prof = vga.vga_profile_read()
+    sec = e0.elapsed_time(e1) / 1e3
+    units, sec_max = combine(passes * E, sec, dist)
+    value = units / sec_max / 1e9
+
+    # ---- roofline of the dominant kernel (the union pass) ----
+    S = prof["slice_bytes"]
+    avg_ms = prof["union_ms"] / max(prof["union_launches"], 1)
+    gather_per_launch = E * S
+    hbm_per_launch = prof["union_hbm_bytes"] / max(prof["union_launches"], 1)
+    l2_peak = vga.vga_bench_gather(N * S, S, 1_000_000_000 * 64 // S, stream=stream)
+    achieved = gather_per_launch / (avg_ms / 1e3) / 1e9
+    kernel_name = f"hb_union_kernel<{S}>"
+    traffic, traffic_note = recorded_traffic(kernel_name, args.config)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    roofline = {
+        "bound": "l2", "kernel": kernel_name, "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+        "frac": achieved / l2_peak if l2_peak else None,
+        "traffic": traffic,
+        "peak_source": (f"in-run gather microbenchmark: {S}-byte rows of an L2-resident {N * S / 2**20:.0f} MiB "
+                        "buffer, same lane mapping as the union kernel (vga_bench_gather); MEASURED_PEAKS.json "
+                        "has no L2 figure"),
+        "algorithmic_bytes_per_launch": gather_per_launch,
+        "algorithmic_bytes_definition": "E x slice_bytes neighbour-register gathers (per-edge union traffic)",
+        "avg_launch_ms": avg_ms, "launches_timed": prof["union_launches"],
+        "hbm_term": {"algorithmic_bytes_per_launch": hbm_per_launch,
+                     "achieved": hbm_per_launch / (avg_ms / 1e3) / 1e9, "peak": hbm_peak,
+                     "frac": (hbm_per_launch / (avg_ms / 1e3) / 1e9 / hbm_peak) if hbm_peak else None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+    }
+    if traffic_note:
+        roofline["traffic_note"] = traffic_note
+    union_share = prof["union_ms"] / (sec * 1e3) if sec > 0 else None
+
+    extras = {}
+    if not args.no_extras:
+        # ---- e2e: public C API with host buffers ----
+        off_h, bytes_h, _ = g.copy_csr()
+        off_pin = torch.empty(8 * len(off_h), dtype=torch.uint8, pin_memory=True)
+        bytes_pin = torch.empty(max(len(bytes_h), 1), dtype=torch.uint8, pin_memory=True)
+        off_np = off_pin.numpy().view(np.uint64)
+        bytes_np = bytes_pin.numpy()[: len(bytes_h)]
+        off_np[:] = off_h
+        bytes_np[:] = bytes_h
+        del bytes_h
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        e2e_passes = 0
+        for _ in range(args.steps):
+            with vga.vga_graph_load(off_np, bytes_np) as g2:
+                _, _, it = vga.hyperball_run(g2, args.p, args.d, args.seed)
+            e2e_passes += it
+        s1.record()
+        torch.cuda.synchronize()
+        e2e_wall = time.perf_counter() - t0
+        e2e_sec = s0.elapsed_time(s1) / 1e3
+        e_units, e_sec = combine(e2e_passes * E, e2e_sec, dist)
+        extras["e2e"] = {"value": e_units / e_sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * (N + 1) + B,
+                         "d2h_bytes_per_step": 16 * N, "ms_per_step": 1e3 * e2e_sec / args.steps,
+                         "wall_ms_per_step": 1e3 * e2e_wall / args.steps,
+                         "calls": "vga_graph_load (pinned host CSR) + hyperball_run (host outputs) + vga_graph_free"}
+        del off_pin, bytes_pin
+        # ---- unlimited depth, once ----
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        dinf_passes = step(0)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        extras["dinf"] = {"seconds": f0.elapsed_time(f1) / 1e3, "passes": dinf_passes,
+                          "geu_per_s": dinf_passes * E / (f0.elapsed_time(f1) / 1e3) / 1e9}
+        if dist.rank == 0 and dist.world == 1:
+            extras["cpu_baseline"] = cpu_baseline(obst, args)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
+                       "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "parallelism": f"replicas x{dist.world}",
+                       "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",
+                       "graph_build_seconds": build_s},
+            "roofline": roofline, "gpu_launches": prof["kernel_launches"], "union_time_share": union_share,
+            "clocks": clock_info, "passes_per_step": passes / args.steps, "context": PAPER_CONTEXT}
+    line.update(extras)
+    if "e2e" not in line:
+        line["e2e"] = None
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    g.free()
+
+
+def main():
+    args = parse_args()
+    dist = Dist(args.backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -222,6 +222,46 @@ int hyperball_run_trace(const vga_graph *g, int p, int d, uint64_t seed, int con
                         double *ball_size, int *iterations, uint8_t *regs_host, double *c_host, int max_trace,
                         const vga_tuning *tuning);
 
+
+/* ---------------------------------------------------------------------- */
+/* Measurement (not part of the paper's method)                            */
+/* ---------------------------------------------------------------------- */
+
+/* Counters the library keeps for benchmarking.  Kernel launches are always
+ * counted; union-kernel launches are timed with CUDA events recorded on the
+ * launch stream only while profiling is enabled. */
+typedef struct vga_profile {
+    uint64_t kernel_launches;     /* library kernels launched since the last reset        */
+    uint64_t union_launches;      /* union-kernel launches timed                          */
+    double union_ms;              /* their summed device time                             */
+    uint64_t union_edges;         /* neighbour unions they performed (E per launch)       */
+    uint64_t union_gather_bytes;  /* per-edge register gathers: E x slice bytes, summed   */
+    uint64_t union_hbm_bytes;     /* CSR bytes + 8(N+1) + 2 x N x slice bytes, summed     */
+    int slice_bytes;              /* slice width of the last timed launch                 */
+    int reserved[3];
+} vga_profile;
+
+/* Enable (1) or disable (0) event timing of union launches. */
+int vga_profile_enable(int on);
+/* Zero every counter. */
+int vga_profile_reset(void);
+/* Read the counters. */
+int vga_profile_read(vga_profile *out);
+
+/*
+ * vga_bench_gather -- gather-bandwidth microbenchmark with the union kernel's
+ * access pattern: warps fold chunk_bytes-wide slices of pseudo-random rows of
+ * a resident_bytes buffer with the same lane mapping and loads in flight as
+ * the union kernel, without the LEB128 decode.  Sized below the L2 it measures
+ * the L2 gather bandwidth the union pass is bound by.
+ *   resident_bytes  buffer size (rounded down to whole chunks), >= chunk_bytes.
+ *   chunk_bytes     power of two in [16, 1024] (the union slice width).
+ *   gathers         total chunks gathered (one timed launch after a warm-up).
+ *   stream          cudaStream_t or NULL.
+ *   gb_per_s        out: gathers x chunk_bytes / kernel time.
+ */
+int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, void *stream, double *gb_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,12 @@ class VgaTuning(C.Structure):
                 ("reserved", C.c_int * 5)]
 
 
+class VgaProfile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("union_launches", C.c_uint64), ("union_ms", C.c_double),
+                ("union_edges", C.c_uint64), ("union_gather_bytes", C.c_uint64), ("union_hbm_bytes", C.c_uint64),
+                ("slice_bytes", C.c_int), ("reserved", C.c_int * 3)]
+
+
 SIGNATURES = {
     "vga_last_error": ([], C.c_char_p),
     "vga_version": ([], C.c_char_p),
@@ -52,6 +58,10 @@ SIGNATURES = {
     "hyperball_run_dev": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, u64, vp, C.POINTER(VgaTuning)], i32),
     "hyperball_run_trace": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, vp, i32, C.POINTER(VgaTuning)],
                             i32),
+    "vga_profile_enable": ([i32], i32),
+    "vga_profile_reset": ([], i32),
+    "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
+    "vga_bench_gather": ([u64, i32, u64, vp, C.POINTER(f64)], i32),
 }
 
 _lock = threading.Lock()
@@ -281,3 +291,28 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}
+
+
+# --------------------------------------------------------------------------
+# Measurement
+# --------------------------------------------------------------------------
+
+def vga_profile_enable(on: bool = True):
+    _check(lib().vga_profile_enable(1 if on else 0))
+
+
+def vga_profile_reset():
+    _check(lib().vga_profile_reset())
+
+
+def vga_profile_read() -> dict:
+    p = VgaProfile()
+    _check(lib().vga_profile_read(C.byref(p)))
+    return {name: getattr(p, name) for name, _ in VgaProfile._fields_ if name != "reserved"}
+
+
+def vga_bench_gather(resident_bytes: int, chunk_bytes: int, gathers: int, stream=None) -> float:
+    """Gather bandwidth (GB/s) with the union kernel's access pattern."""
+    out = C.c_double()
+    _check(lib().vga_bench_gather(resident_bytes, chunk_bytes, gathers, _stream_ptr(stream), C.byref(out)))
+    return out.value

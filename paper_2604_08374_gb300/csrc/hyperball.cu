@@ -8,7 +8,9 @@
 // only N*S bytes of counters (sized to stay resident in L2) and every
 // neighbour gather is S contiguous, 16-byte aligned bytes.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "vga_common.cuh"
@@ -39,22 +41,72 @@ __global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, in
     regs[((uint64_t)s * n + v) * (uint64_t)S + o] = (uint8_t)rho;
 }
 
+// Lane mapping of a slice gather: each lane moves CH bytes of a neighbour's
+// S-byte slice, G lanes cover one neighbour, P neighbours share one warp-wide
+// load instruction, U loads per lane are in flight.
+template <int S>
+struct GatherShape {
+    static constexpr int CH = (S > 512) ? S / 32 : 16;
+    static constexpr int G = S / CH;
+    static constexpr int P = 32 / G;
+    static constexpr int V4 = CH / 16;
+    static constexpr int U = (V4 == 1) ? 4 : 2;
+};
+
+// Fold the S-byte slices of rows ids[0..cnt) of `cur` into acc with __vmaxu4.
+template <int S>
+__device__ __forceinline__ void gather_fold(const uint8_t *__restrict__ cur, const uint32_t *ids, int cnt, int g,
+                                            int sub, uint4 (&acc)[GatherShape<S>::V4]) {
+    using Sh = GatherShape<S>;
+    for (int k0 = 0; k0 < cnt; k0 += Sh::P * Sh::U) {
+        uint4 x[Sh::U][Sh::V4];
+#pragma unroll
+        for (int u = 0; u < Sh::U; u++) {
+            const int k = k0 + u * Sh::P + g;
+            if (k < cnt) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(cur + (uint64_t)ids[k] * S + sub * Sh::CH);
+#pragma unroll
+                for (int q = 0; q < Sh::V4; q++) x[u][q] = __ldg(src + q);
+            } else {
+#pragma unroll
+                for (int q = 0; q < Sh::V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < Sh::U; u++)
+#pragma unroll
+            for (int q = 0; q < Sh::V4; q++) acc[q] = vmax4(acc[q], x[u][q]);
+    }
+}
+
+// Fold the P lane groups of a warp together (every lane ends with the max).
+template <int S>
+__device__ __forceinline__ void fold_groups(uint4 (&acc)[GatherShape<S>::V4]) {
+    using Sh = GatherShape<S>;
+#pragma unroll
+    for (int o = Sh::G; o < 32; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < Sh::V4; q++) {
+            uint4 y;
+            y.x = __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+            y.y = __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+            y.z = __shfl_xor_sync(0xffffffffu, acc[q].z, o);
+            y.w = __shfl_xor_sync(0xffffffffu, acc[q].w, o);
+            acc[q] = vmax4(acc[q], y);
+        }
+}
+
 // Eq. hll-union for one register slice: next[v] = max(cur[v], max_{w in N(v)}
 // cur[w]) bytewise.  One warp per node: the warp decodes the node's LEB128
-// list 32 bytes at a time, then gathers each neighbour's S-byte slice with
-// 16-byte loads (G lanes per neighbour, P = 32/G neighbours in flight per
-// load instruction, U loads per lane in flight) and folds it in with
-// __vmaxu4.  Sets flags[0] if any register of the slice changed.
+// list 32 bytes at a time (decode_window), stages the decoded ids in shared
+// memory and gathers each neighbour's S-byte slice with 16-byte loads, folding
+// it in with __vmaxu4.  Sets flags[0] if any register of the slice changed.
 template <int S>
 __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restrict__ off,
                                                        const uint8_t *__restrict__ bytes,
                                                        const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
                                                        uint32_t n, uint32_t *__restrict__ flags) {
-    constexpr int CH = (S > 512) ? S / 32 : 16;  // bytes per lane per neighbour
-    constexpr int G = S / CH;                     // lanes per neighbour
-    constexpr int P = 32 / G;                     // neighbours per warp-wide load
-    constexpr int V4 = CH / 16;                   // uint4 per lane per neighbour
-    constexpr int U = (V4 == 1) ? 4 : 2;          // loads per lane in flight
+    using Sh = GatherShape<S>;
     extern __shared__ uint32_t s_ids[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -62,12 +114,12 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
     const uint32_t v = (uint32_t)warp;
-    const int g = lane / G, sub = lane % G;
+    const int g = lane / Sh::G, sub = lane % Sh::G;
     const uint32_t lt_mask = (1u << lane) - 1u;
 
-    uint4 acc[V4];
+    uint4 acc[Sh::V4];
 #pragma unroll
-    for (int q = 0; q < V4; q++) acc[q] = make_uint4(0, 0, 0, 0);
+    for (int q = 0; q < Sh::V4; q++) acc[q] = make_uint4(0, 0, 0, 0);
 
     uint64_t pos = off[v];
     const uint64_t end = off[v + 1];
@@ -78,48 +130,18 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
         if (T == 0) break;  // cannot happen on a validated graph; guarantees progress
         if ((T >> lane) & 1u) ids[__popc(T & lt_mask)] = r.id;
         __syncwarp();
-        const int cnt = __popc(T);
-        for (int k0 = 0; k0 < cnt; k0 += P * U) {
-            uint4 x[U][V4];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const int k = k0 + u * P + g;
-                if (k < cnt) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(cur + (uint64_t)ids[k] * S + sub * CH);
-#pragma unroll
-                    for (int q = 0; q < V4; q++) x[u][q] = __ldg(src + q);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++)
-#pragma unroll
-                for (int q = 0; q < V4; q++) acc[q] = vmax4(acc[q], x[u][q]);
-        }
+        gather_fold<S>(cur, ids, __popc(T), g, sub, acc);
         __syncwarp();
         base = r.next_base;
         pos += (uint64_t)r.advance;
     }
-    // fold the P lane groups together
-#pragma unroll
-    for (int o = G; o < 32; o <<= 1)
-#pragma unroll
-        for (int q = 0; q < V4; q++) {
-            uint4 y;
-            y.x = __shfl_xor_sync(0xffffffffu, acc[q].x, o);
-            y.y = __shfl_xor_sync(0xffffffffu, acc[q].y, o);
-            y.z = __shfl_xor_sync(0xffffffffu, acc[q].z, o);
-            y.w = __shfl_xor_sync(0xffffffffu, acc[q].w, o);
-            acc[q] = vmax4(acc[q], y);
-        }
+    fold_groups<S>(acc);
     bool changed = false;
     if (g == 0) {
-        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * CH);
-        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * CH);
+        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
+        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * Sh::CH);
 #pragma unroll
-        for (int q = 0; q < V4; q++) {
+        for (int q = 0; q < Sh::V4; q++) {
             const uint4 o4 = __ldg(own + q);
             const uint4 res = vmax4(acc[q], o4);
             dst[q] = res;
@@ -129,6 +151,31 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     if (__any_sync(0xffffffffu, changed) && lane == 0) {
         if (*reinterpret_cast<volatile uint32_t *>(flags) == 0u) atomicOr(flags, 1u);
     }
+}
+
+// Microbenchmark twin of hb_union_kernel: the same gather_fold over rows
+// drawn from a hash instead of decoded from the CSR.
+template <int S>
+__global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__restrict__ buf, uint32_t rows,
+                                                           uint32_t windows, uint32_t *__restrict__ out) {
+    using Sh = GatherShape<S>;
+    extern __shared__ uint32_t s_ids[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *ids = s_ids + wib * 32;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const int g = lane / Sh::G, sub = lane % Sh::G;
+    uint4 acc[Sh::V4];
+#pragma unroll
+    for (int q = 0; q < Sh::V4; q++) acc[q] = make_uint4(0, 0, 0, 0);
+    for (uint32_t w = 0; w < windows; w++) {
+        ids[lane] = (uint32_t)(splitmix64((warp * windows + w) * 32 + lane) % rows);
+        __syncwarp();
+        gather_fold<S>(buf, ids, 32, g, sub, acc);
+        __syncwarp();
+    }
+    fold_groups<S>(acc);
+    if (lane == 0) out[warp] = acc[0].x ^ acc[0].y ^ acc[0].z ^ acc[0].w;
 }
 
 // Correctly rounded (to nearest, ties to even) conversion of hi*2^64 + lo to
@@ -305,14 +352,41 @@ static const std::vector<double> &lc_table(int p) {
     return tables[p];
 }
 
+static std::atomic<uint64_t> g_kernel_launches{0};
+
+// Benchmark counters (vga_profile_*): union launches are bracketed by CUDA
+// events on their stream while profiling is on; the events are read after the
+// run's final synchronisation.
+struct ProfileState {
+    std::mutex mu;
+    bool enabled = false;
+    vga_profile acc{};
+};
+static ProfileState &prof() {
+    static ProfileState s;
+    return s;
+}
+
+struct PendingTiming {
+    cudaEvent_t start, stop;
+    uint64_t edges, gather_bytes, hbm_bytes;
+    int S;
+};
+
 static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, uint8_t *nxt, uint32_t *flags,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, std::vector<PendingTiming> *timings) {
     const unsigned blocks = (unsigned)((P.n + P.warps - 1) / P.warps);
     const size_t smem = (size_t)P.warps * 32 * sizeof(uint32_t);
     const uint64_t slice_bytes = (uint64_t)P.n * P.S;
     for (int s = 0; s < P.slices; s++) {
         const uint8_t *c = cur + (uint64_t)s * slice_bytes;
         uint8_t *x = nxt + (uint64_t)s * slice_bytes;
+        PendingTiming pt{};
+        if (timings) {
+            VGA_CHECK_CUDA(cudaEventCreate(&pt.start));
+            VGA_CHECK_CUDA(cudaEventCreate(&pt.stop));
+            VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
+        }
         switch (P.S) {
 #define VGA_CASE(SS)                                                                                            \
     case SS:                                                                                                    \
@@ -331,9 +405,37 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
                 set_error("internal: slice width %d", P.S);
                 return VGA_EINVAL;
         }
+        count_launch();
+        if (timings) {
+            VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
+            pt.edges = g->n_edges;
+            pt.gather_bytes = g->n_edges * (uint64_t)P.S;
+            pt.hbm_bytes = g->n_bytes + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
+            pt.S = P.S;
+            timings->push_back(pt);
+        }
     }
     VGA_CHECK_CUDA(cudaGetLastError());
     return VGA_OK;
+}
+
+static void settle_timings(std::vector<PendingTiming> &timings) {
+    ProfileState &ps = prof();
+    std::lock_guard<std::mutex> lock(ps.mu);
+    for (PendingTiming &pt : timings) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pt.start, pt.stop) == cudaSuccess) {
+            ps.acc.union_launches++;
+            ps.acc.union_ms += ms;
+            ps.acc.union_edges += pt.edges;
+            ps.acc.union_gather_bytes += pt.gather_bytes;
+            ps.acc.union_hbm_bytes += pt.hbm_bytes;
+            ps.acc.slice_bytes = pt.S;
+        }
+        cudaEventDestroy(pt.start);
+        cudaEventDestroy(pt.stop);
+    }
+    timings.clear();
 }
 
 static int launch_estimate(const Plan &P, const uint8_t *regs, int t, const double *lc, const double *c_prev,
@@ -343,6 +445,7 @@ static int launch_estimate(const Plan &P, const uint8_t *regs, int t, const doub
     const double alpha_mm = hll_alpha(P.p) * (double)P.m * (double)P.m;
     hb_estimate_kernel<<<blocks, warps * 32, 0, stream>>>(regs, (uint32_t)P.n, P.p, P.S, t, alpha_mm, lc, c_prev,
                                                           c_cur, sum_d, flags);
+    count_launch();
     VGA_CHECK_CUDA(cudaGetLastError());
     return VGA_OK;
 }
@@ -391,6 +494,16 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     double *lc = reinterpret_cast<double *>(base + P.off_lc);
     uint32_t *flags = reinterpret_cast<uint32_t *>(base + P.off_flags);
 
+    bool profiling;
+    {
+        std::lock_guard<std::mutex> lock(prof().mu);
+        profiling = prof().enabled;
+    }
+    std::vector<PendingTiming> timings;
+    struct Settle {
+        std::vector<PendingTiming> &t;
+        ~Settle() { settle_timings(t); }
+    } settle{timings};
     const std::vector<double> &table = lc_table(p);
     VGA_CHECK_CUDA(cudaMemcpyAsync(lc, table.data(), 8 * table.size(), cudaMemcpyHostToDevice, stream));
     int t = 0;
@@ -398,13 +511,14 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         VGA_CHECK_CUDA(cudaMemsetAsync(cur, 0, P.n * P.m, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
         hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed);
+        count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
         VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0
         if (max_trace >= 0) VGA_TRY(copy_trace(P, cur, c_prev, 0, trace_regs, trace_c, stream));
         uint32_t hflags[2];
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
-            VGA_TRY(launch_union(P, g, cur, nxt, flags, stream));
+            VGA_TRY(launch_union(P, g, cur, nxt, flags, stream, profiling ? &timings : nullptr));
             VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
             if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
             VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, stream));
@@ -416,6 +530,7 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         }
         hb_finalize_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>((uint32_t)P.n, g->d_comp, sum_d,
                                                                                c_prev, md_dev, ball_dev);
+        count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
@@ -424,11 +539,94 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
 }
 
 }  // namespace
+
+void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+
 }  // namespace vga
 
 using namespace vga;
 
 extern "C" {
+
+int vga_profile_enable(int on) {
+    std::lock_guard<std::mutex> lock(prof().mu);
+    prof().enabled = on != 0;
+    return VGA_OK;
+}
+
+int vga_profile_reset(void) {
+    std::lock_guard<std::mutex> lock(prof().mu);
+    prof().acc = vga_profile{};
+    g_kernel_launches.store(0);
+    return VGA_OK;
+}
+
+int vga_profile_read(vga_profile *out) {
+    clear_error();
+    if (!out) {
+        set_error("vga_profile_read: null argument");
+        return VGA_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(prof().mu);
+    *out = prof().acc;
+    out->kernel_launches = g_kernel_launches.load();
+    return VGA_OK;
+}
+
+int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, void *stream_ptr,
+                     double *gb_per_s) {
+    clear_error();
+    const int S = chunk_bytes;
+    if (!gb_per_s || S < 16 || S > 1024 || (S & (S - 1)) || resident_bytes < (uint64_t)S ||
+        resident_bytes / (uint64_t)S > 0xFFFFFFFFull || gathers == 0) {
+        set_error("vga_bench_gather: bad arguments");
+        return VGA_EINVAL;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const uint32_t rows = (uint32_t)(resident_bytes / (uint64_t)S);
+    const int warps = 8;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const uint32_t blocks = (uint32_t)std::max(1, sms) * 16;
+    const uint64_t total_warps = (uint64_t)blocks * warps;
+    const uint64_t windows = std::max<uint64_t>(1, gathers / (total_warps * 32));
+    DeviceBuffer buf, out;
+    VGA_TRY(buf.alloc((uint64_t)rows * S));
+    VGA_TRY(out.alloc(total_warps * 4));
+    VGA_CHECK_CUDA(cudaMemsetAsync(buf.ptr, 0x5A, (uint64_t)rows * S, stream));
+    cudaEvent_t e0, e1;
+    VGA_CHECK_CUDA(cudaEventCreate(&e0));
+    VGA_CHECK_CUDA(cudaEventCreate(&e1));
+    const size_t smem = (size_t)warps * 32 * 4;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; rep++) {  // warm-up, then the timed launch
+        VGA_CHECK_CUDA(cudaEventRecord(e0, stream));
+        switch (S) {
+#define VGA_CASE(SS)                                                                                              \
+    case SS:                                                                                                      \
+        gather_bench_kernel<SS><<<blocks, warps * 32, smem, stream>>>(buf.as<uint8_t>(), rows, (uint32_t)windows, \
+                                                                      out.as<uint32_t>());                        \
+        break;
+            VGA_CASE(16)
+            VGA_CASE(32)
+            VGA_CASE(64)
+            VGA_CASE(128)
+            VGA_CASE(256)
+            VGA_CASE(512)
+            VGA_CASE(1024)
+#undef VGA_CASE
+        }
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+        VGA_CHECK_CUDA(cudaEventRecord(e1, stream));
+        VGA_CHECK_CUDA(cudaEventSynchronize(e1));
+        VGA_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *gb_per_s = (double)(total_warps * windows * 32) * (double)S / ((double)ms * 1e-3) / 1e9;
+    return VGA_OK;
+}
 
 int hyperball_workspace_bytes(const vga_graph *g, int p, uint64_t *bytes) {
     clear_error();

@@ -34,6 +34,9 @@ constexpr uint64_t kBytePad = 256;
 void set_error(const char *fmt, ...);
 void clear_error();
 
+// Counts one library kernel launch (vga_profile.kernel_launches).
+void count_launch();
+
 #define VGA_CHECK_CUDA(call)                                                                   \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \

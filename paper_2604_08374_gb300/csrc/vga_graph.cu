@@ -88,6 +88,7 @@ int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t
         const uint64_t blocks = ((uint64_t)n + warps - 1) / warps;
         validate_kernel<<<(unsigned)blocks, warps * 32, 0, stream>>>(d_offsets, d_bytes, n, degree.as<uint32_t>(),
                                                                       d_edges, d_maxdeg, d_bad);
+        count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
     uint8_t host_counters[16];

@@ -246,10 +246,12 @@ int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_no
         dim3 grid(n, wblocks);
         visibility_bits_kernel<<<grid, warps * 32, 0, stream>>>(d_bits.as<uint32_t>(), d_cells.as<uint32_t>(), n, W,
                                                                  words, d_mat.as<uint32_t>());
+        count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
         const unsigned rblocks = (n + warps - 1) / warps;
         encode_rows_kernel<false><<<rblocks, warps * 32, 0, stream>>>(d_mat.as<uint32_t>(), n, words,
                                                                       d_rowbytes.as<uint64_t>(), nullptr, nullptr);
+        count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
         std::vector<uint64_t> rb(n);
         VGA_CHECK_CUDA(cudaMemcpyAsync(rb.data(), d_rowbytes.ptr, (size_t)n * 8, cudaMemcpyDeviceToHost, stream));
@@ -267,6 +269,7 @@ int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_no
         const unsigned rblocks = (n + warps - 1) / warps;
         encode_rows_kernel<true><<<rblocks, warps * 32, 0, stream>>>(d_mat.as<uint32_t>(), n, words, nullptr,
                                                                      d_off.as<uint64_t>(), d_bytes.as<uint8_t>());
+        count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
