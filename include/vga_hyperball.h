@@ -210,6 +210,38 @@ int hyperball_run_dev(const vga_graph *g, int p, int d, uint64_t seed, int conv_
                       void *stream, const vga_tuning *tuning);
 
 /*
+ * hyperball_run_noalloc -- hyperball_run_dev for callers that cannot allocate
+ * device memory.  (The paper has no counterpart: this entry point exists for
+ * the library's users, not for the method.)
+ *
+ * Some callers must not call cudaMalloc or cudaFree at run time: code that
+ * runs inside a framework whose caching allocator already owns nearly all of
+ * the GPU's memory, real-time or long-running services that must not fail or
+ * stall after start-up (cudaFree can wait for the whole device to go idle, and
+ * cudaMalloc can fail once memory is fragmented or taken), and hosts that budget
+ * every device byte up front.  This entry point allocates nothing: its scratch
+ * (counters, estimates, flags) is a fixed 64 MiB array compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The caller still provides the graph and the device outputs.
+ *
+ *   Arguments are those of hyperball_run_dev without workspace or tuning;
+ *   outputs are device pointers (N doubles each, may be NULL).
+ *   Size limit: hyperball_workspace_bytes(g, p) must not exceed 64 MiB
+ *   (67,108,864 bytes), about N <= 32,000 nodes at p = 10 or N <= 125,000 at
+ *   p = 8; larger requests return VGA_EINVAL with a message naming both sizes.
+ *   The graph must live on the current device.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture begins.
+ *   Sharing: every call on a device uses the same array, and it keeps the last
+ *   call's contents; each call clears what must start at zero itself.  Calls
+ *   whose work overlaps on the GPU (other streams, other host threads) race on
+ *   the array and corrupt each other's results: serialise them.
+ */
+int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth_dev,
+                          double *ball_size_dev, int *iterations, void *stream);
+
+/*
  * hyperball_run_trace -- debug hook for bit-exact checks: as hyperball_run_dev
  * with host outputs, and additionally copies the registers and estimates after
  * every pass.

@@ -58,6 +58,7 @@ SIGNATURES = {
     "hyperball_run_dev": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, u64, vp, C.POINTER(VgaTuning)], i32),
     "hyperball_run_trace": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, vp, i32, C.POINTER(VgaTuning)],
                             i32),
+    "hyperball_run_noalloc": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp], i32),
     "vga_profile_enable": ([i32], i32),
     "vga_profile_reset": ([], i32),
     "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
@@ -272,6 +273,17 @@ def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
                                    _tuning(slice_bytes, warps_per_cta, l2_budget_mb)))
+    return it.value
+
+
+def hyperball_run_noalloc(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
+                          stream=None) -> int:
+    """Algorithm 1 into device tensors using the library's fixed 64 MiB scratch
+    instead of any device allocation (for callers that cannot allocate).
+    Returns passes run; raises VgaError(VGA_EINVAL) if the run needs more."""
+    it = C.c_int()
+    _check(lib().hyperball_run_noalloc(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
+                                       C.byref(it), _stream_ptr(stream)))
     return it.value
 
 

@@ -538,6 +538,43 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     return VGA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fixed scratch for callers that must not allocate device memory
+// (hyperball_run_noalloc).  The array lives in the library's device image:
+// every GPU the library is used on holds these bytes from module load until the
+// process exits.  Host code must not use its name as a pointer: on the host it
+// is only a stand-in for the device symbol, and the device address is looked up
+// once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kStaticScratchBytes = 64ull << 20;  // 64 MiB
+__device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device, looked up on the
+// first call made with that device current.
+int static_scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("hyperball_run_noalloc: device %d is beyond the supported %d devices", dev, kMaxDevices);
+        return VGA_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *addr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
+        if (e != cudaSuccess || !addr) {
+            set_error("hyperball_run_noalloc: cudaGetSymbolAddress of the fixed scratch failed on device %d: %s", dev,
+                      cudaGetErrorString(e));
+            return VGA_ECUDA;
+        }
+        g_static_addr[dev] = addr;
+    }
+    *out = g_static_addr[dev];
+    return VGA_OK;
+}
+
 }  // namespace
 
 void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -626,6 +663,36 @@ int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers,
     cudaEventDestroy(e1);
     *gb_per_s = (double)(total_warps * windows * 32) * (double)S / ((double)ms * 1e-3) / 1e9;
     return VGA_OK;
+}
+
+int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth_dev,
+                          double *ball_size_dev, int *iterations, void *stream) {
+    clear_error();
+    if (!g) {
+        set_error("hyperball_run_noalloc: null graph");
+        return VGA_EINVAL;
+    }
+    int dev = -1;
+    VGA_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) {
+        set_error("hyperball_run_noalloc: the graph lives on device %d but device %d is current", g->device, dev);
+        return VGA_EINVAL;
+    }
+    Plan P;
+    VGA_TRY(make_plan(g, p, nullptr, &P));
+    if (P.total > kStaticScratchBytes) {
+        set_error("hyperball_run_noalloc: N = %u at p = %d needs %llu bytes of scratch but the fixed scratch holds "
+                  "%llu bytes (64 MiB); pass a workspace to hyperball_run_dev instead",
+                  g->n, p, (unsigned long long)P.total, (unsigned long long)kStaticScratchBytes);
+        return VGA_EINVAL;
+    }
+    void *scratch = nullptr;
+    VGA_TRY(static_scratch_address(dev, &scratch));
+    // run_impl zeroes the registers, sum_d and the flags itself and overwrites
+    // everything else before reading it, so stale contents of the shared scratch
+    // from an earlier call cannot leak into this one.
+    return run_impl(g, p, d, seed, conv_mode, mean_depth_dev, ball_size_dev, iterations, scratch, kStaticScratchBytes,
+                    static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, -1);
 }
 
 int hyperball_workspace_bytes(const vga_graph *g, int p, uint64_t *bytes) {
