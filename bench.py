@@ -351,7 +351,8 @@ def run_ours(args, dist: Dist):
     avg_ms = prof["union_ms"] / max(prof["union_launches"], 1)
     gather_per_launch = E * S
     hbm_per_launch = prof["union_hbm_bytes"] / max(prof["union_launches"], 1)
-    l2_peak = vga.vga_bench_gather(N * S, S, 1_000_000_000 * 64 // S, stream=stream)
+    l2_peak = vga.vga_bench_gather(N * S, S, 1_000_000_000 * 64 // S, consumer=1, stream=stream)
+    loop_ceiling = vga.vga_bench_gather(N * S, S, 1_000_000_000 * 64 // S, consumer=0, stream=stream)
     achieved = gather_per_launch / (avg_ms / 1e3) / 1e9
     kernel_name = f"hb_union_kernel<{S}>"
     traffic, traffic_note = recorded_traffic(kernel_name, args.config)
@@ -361,9 +362,11 @@ def run_ours(args, dist: Dist):
         "bound": "l2", "kernel": kernel_name, "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
         "frac": achieved / l2_peak if l2_peak else None,
         "traffic": traffic,
-        "peak_source": (f"in-run gather microbenchmark: {S}-byte rows of an L2-resident {N * S / 2**20:.0f} MiB "
-                        "buffer, same lane mapping as the union kernel (vga_bench_gather); MEASURED_PEAKS.json "
-                        "has no L2 figure"),
+        "peak_source": (f"in-run L2 gather microbenchmark: {S}-byte rows of an L2-resident {N * S / 2**20:.0f} MiB "
+                        "buffer, same lane mapping and loads in flight as the union kernel, xor consumer "
+                        "(vga_bench_gather consumer=1); MEASURED_PEAKS.json has no L2 figure"),
+        "union_loop_ceiling": {"value": loop_ceiling, "unit": "GB/s",
+                               "what": "same microbenchmark folding with the union's bytewise max (no decode)"},
         "algorithmic_bytes_per_launch": gather_per_launch,
         "algorithmic_bytes_definition": "E x slice_bytes neighbour-register gathers (per-edge union traffic)",
         "avg_launch_ms": avg_ms, "launches_timed": prof["union_launches"],

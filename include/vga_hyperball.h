@@ -282,17 +282,20 @@ int vga_profile_read(vga_profile *out);
 
 /*
  * vga_bench_gather -- gather-bandwidth microbenchmark with the union kernel's
- * access pattern: warps fold chunk_bytes-wide slices of pseudo-random rows of
- * a resident_bytes buffer with the same lane mapping and loads in flight as
- * the union kernel, without the LEB128 decode.  Sized below the L2 it measures
- * the L2 gather bandwidth the union pass is bound by.
+ * access pattern: warps gather chunk_bytes-wide slices of pseudo-random rows
+ * of a resident_bytes buffer with the same lane mapping and loads in flight as
+ * the union kernel, without the LEB128 decode.
  *   resident_bytes  buffer size (rounded down to whole chunks), >= chunk_bytes.
  *   chunk_bytes     power of two in [16, 1024] (the union slice width).
  *   gathers         total chunks gathered (one timed launch after a warm-up).
+ *   consumer        1: xor the loaded words (the gather bandwidth itself; sized
+ *                   below the L2 this is the L2 gather roofline); 0: fold them
+ *                   with the union kernel's bytewise max (its loop's ceiling).
  *   stream          cudaStream_t or NULL.
  *   gb_per_s        out: gathers x chunk_bytes / kernel time.
  */
-int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, void *stream, double *gb_per_s);
+int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, int consumer, void *stream,
+                     double *gb_per_s);
 
 #ifdef __cplusplus
 }

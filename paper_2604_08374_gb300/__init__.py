@@ -62,7 +62,7 @@ SIGNATURES = {
     "vga_profile_enable": ([i32], i32),
     "vga_profile_reset": ([], i32),
     "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
-    "vga_bench_gather": ([u64, i32, u64, vp, C.POINTER(f64)], i32),
+    "vga_bench_gather": ([u64, i32, u64, i32, vp, C.POINTER(f64)], i32),
 }
 
 _lock = threading.Lock()
@@ -323,8 +323,12 @@ def vga_profile_read() -> dict:
     return {name: getattr(p, name) for name, _ in VgaProfile._fields_ if name != "reserved"}
 
 
-def vga_bench_gather(resident_bytes: int, chunk_bytes: int, gathers: int, stream=None) -> float:
-    """Gather bandwidth (GB/s) with the union kernel's access pattern."""
+def vga_bench_gather(resident_bytes: int, chunk_bytes: int, gathers: int, consumer: int = 1, stream=None) -> float:
+    """Gather bandwidth (GB/s) with the union kernel's access pattern.
+
+    consumer=1 xors the loaded words (the L2 gather roofline when the buffer
+    fits in L2); consumer=0 folds them with the union's bytewise max."""
     out = C.c_double()
-    _check(lib().vga_bench_gather(resident_bytes, chunk_bytes, gathers, _stream_ptr(stream), C.byref(out)))
+    _check(lib().vga_bench_gather(resident_bytes, chunk_bytes, gathers, consumer, _stream_ptr(stream),
+                                  C.byref(out)))
     return out.value

@@ -53,11 +53,35 @@ struct GatherShape {
     static constexpr int U = (V4 == 1) ? 4 : 2;
 };
 
-// Fold the S-byte slices of rows ids[0..cnt) of `cur` into acc with __vmaxu4.
+// Bytewise max through 16-bit lanes.  For a register word w = [b3 b2 b1 b0],
+// an unsigned max over u16x2 lanes of w keeps max(b3) and max(b1) in the lanes'
+// high bytes (the high byte decides the comparison; the low byte is whatever
+// came with the winner), and the same over w << 8 keeps max(b2) and max(b0).
+// Two DPX three-way maxima (__vimax3_u16x2) thus fold two gathered words into
+// the running maximum, instead of the multi-instruction __vmaxu4 emulation.
+// SplitAcc holds the two halves for one register word.
+struct SplitAcc {
+    uint32_t hi;  // u16x2 max over w: bytes 3 and 1 in the high byte of each lane
+    uint32_t lo;  // u16x2 max over w << 8: bytes 2 and 0 likewise
+};
+
+__device__ __forceinline__ void split_fold2(SplitAcc &a, uint32_t w0, uint32_t w1) {
+    a.hi = __vimax3_u16x2(a.hi, w0, w1);
+    a.lo = __vimax3_u16x2(a.lo, w0 << 8, w1 << 8);
+}
+
+__device__ __forceinline__ uint32_t split_bytes(const SplitAcc &a) {
+    return (a.hi & 0xFF00FF00u) | ((a.lo >> 8) & 0x00FF00FFu);
+}
+
+// Fold the S-byte slices of rows ids[0..cnt) of `cur` into acc (4 * V4 words
+// per lane, split form).  Loads for U neighbours per lane are issued before
+// any is folded.
 template <int S>
 __device__ __forceinline__ void gather_fold(const uint8_t *__restrict__ cur, const uint32_t *ids, int cnt, int g,
-                                            int sub, uint4 (&acc)[GatherShape<S>::V4]) {
+                                            int sub, SplitAcc (&acc)[4 * GatherShape<S>::V4]) {
     using Sh = GatherShape<S>;
+    static_assert(Sh::U % 2 == 0, "loads are folded in pairs");
     for (int k0 = 0; k0 < cnt; k0 += Sh::P * Sh::U) {
         uint4 x[Sh::U][Sh::V4];
 #pragma unroll
@@ -73,26 +97,37 @@ __device__ __forceinline__ void gather_fold(const uint8_t *__restrict__ cur, con
             }
         }
 #pragma unroll
-        for (int u = 0; u < Sh::U; u++)
+        for (int u = 0; u < Sh::U; u += 2)
 #pragma unroll
-            for (int q = 0; q < Sh::V4; q++) acc[q] = vmax4(acc[q], x[u][q]);
+            for (int q = 0; q < Sh::V4; q++) {
+                split_fold2(acc[4 * q + 0], x[u][q].x, x[u + 1][q].x);
+                split_fold2(acc[4 * q + 1], x[u][q].y, x[u + 1][q].y);
+                split_fold2(acc[4 * q + 2], x[u][q].z, x[u + 1][q].z);
+                split_fold2(acc[4 * q + 3], x[u][q].w, x[u + 1][q].w);
+            }
     }
 }
 
-// Fold the P lane groups of a warp together (every lane ends with the max).
+// Convert the split accumulators to register bytes and fold the P lane groups
+// of a warp together (every lane ends with the group maximum).
 template <int S>
-__device__ __forceinline__ void fold_groups(uint4 (&acc)[GatherShape<S>::V4]) {
+__device__ __forceinline__ void finish_groups(const SplitAcc (&acc)[4 * GatherShape<S>::V4],
+                                              uint4 (&out)[GatherShape<S>::V4]) {
     using Sh = GatherShape<S>;
+#pragma unroll
+    for (int q = 0; q < Sh::V4; q++)
+        out[q] = make_uint4(split_bytes(acc[4 * q + 0]), split_bytes(acc[4 * q + 1]), split_bytes(acc[4 * q + 2]),
+                            split_bytes(acc[4 * q + 3]));
 #pragma unroll
     for (int o = Sh::G; o < 32; o <<= 1)
 #pragma unroll
         for (int q = 0; q < Sh::V4; q++) {
             uint4 y;
-            y.x = __shfl_xor_sync(0xffffffffu, acc[q].x, o);
-            y.y = __shfl_xor_sync(0xffffffffu, acc[q].y, o);
-            y.z = __shfl_xor_sync(0xffffffffu, acc[q].z, o);
-            y.w = __shfl_xor_sync(0xffffffffu, acc[q].w, o);
-            acc[q] = vmax4(acc[q], y);
+            y.x = __shfl_xor_sync(0xffffffffu, out[q].x, o);
+            y.y = __shfl_xor_sync(0xffffffffu, out[q].y, o);
+            y.z = __shfl_xor_sync(0xffffffffu, out[q].z, o);
+            y.w = __shfl_xor_sync(0xffffffffu, out[q].w, o);
+            out[q] = vmax4(out[q], y);
         }
 }
 
@@ -117,9 +152,9 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     const int g = lane / Sh::G, sub = lane % Sh::G;
     const uint32_t lt_mask = (1u << lane) - 1u;
 
-    uint4 acc[Sh::V4];
+    SplitAcc acc[4 * Sh::V4];
 #pragma unroll
-    for (int q = 0; q < Sh::V4; q++) acc[q] = make_uint4(0, 0, 0, 0);
+    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
 
     uint64_t pos = off[v];
     const uint64_t end = off[v + 1];
@@ -135,7 +170,8 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
         base = r.next_base;
         pos += (uint64_t)r.advance;
     }
-    fold_groups<S>(acc);
+    uint4 nb[Sh::V4];
+    finish_groups<S>(acc, nb);
     bool changed = false;
     if (g == 0) {
         const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
@@ -143,7 +179,7 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
 #pragma unroll
         for (int q = 0; q < Sh::V4; q++) {
             const uint4 o4 = __ldg(own + q);
-            const uint4 res = vmax4(acc[q], o4);
+            const uint4 res = vmax4(nb[q], o4);
             dst[q] = res;
             changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
         }
@@ -153,9 +189,11 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     }
 }
 
-// Microbenchmark twin of hb_union_kernel: the same gather_fold over rows
-// drawn from a hash instead of decoded from the CSR.
-template <int S>
+// Microbenchmark twin of hb_union_kernel: rows drawn from a hash instead of
+// decoded from the CSR.  XOR = false folds them with the union's gather_fold
+// (the union loop's own ceiling); XOR = true only xors the loaded words, which
+// leaves the gathers themselves as the limit (the L2 gather bandwidth).
+template <int S, bool XOR>
 __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__restrict__ buf, uint32_t rows,
                                                            uint32_t windows, uint32_t *__restrict__ out) {
     using Sh = GatherShape<S>;
@@ -165,17 +203,44 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
     uint32_t *ids = s_ids + wib * 32;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     const int g = lane / Sh::G, sub = lane % Sh::G;
-    uint4 acc[Sh::V4];
+    SplitAcc acc[4 * Sh::V4];
 #pragma unroll
-    for (int q = 0; q < Sh::V4; q++) acc[q] = make_uint4(0, 0, 0, 0);
+    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
+    uint32_t x_acc = 0;
     for (uint32_t w = 0; w < windows; w++) {
         ids[lane] = (uint32_t)(splitmix64((warp * windows + w) * 32 + lane) % rows);
         __syncwarp();
-        gather_fold<S>(buf, ids, 32, g, sub, acc);
+        if (XOR) {
+            for (int k0 = 0; k0 < 32; k0 += Sh::P * Sh::U) {
+                uint4 x[Sh::U][Sh::V4];
+#pragma unroll
+                for (int u = 0; u < Sh::U; u++) {
+                    const int k = k0 + u * Sh::P + g;
+                    if (k < 32) {
+                        const uint4 *src = reinterpret_cast<const uint4 *>(buf + (uint64_t)ids[k] * S + sub * Sh::CH);
+#pragma unroll
+                        for (int q = 0; q < Sh::V4; q++) x[u][q] = __ldg(src + q);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < Sh::V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < Sh::U; u++)
+#pragma unroll
+                    for (int q = 0; q < Sh::V4; q++) x_acc ^= x[u][q].x ^ x[u][q].y ^ x[u][q].z ^ x[u][q].w;
+            }
+        } else {
+            gather_fold<S>(buf, ids, 32, g, sub, acc);
+        }
         __syncwarp();
     }
-    fold_groups<S>(acc);
-    if (lane == 0) out[warp] = acc[0].x ^ acc[0].y ^ acc[0].z ^ acc[0].w;
+    if (!XOR) {
+        uint4 r[Sh::V4];
+        finish_groups<S>(acc, r);
+        x_acc = r[0].x ^ r[0].y ^ r[0].z ^ r[0].w;
+    }
+    if (lane == 0) out[warp] = x_acc;
 }
 
 // Correctly rounded (to nearest, ties to even) conversion of hi*2^64 + lo to
@@ -610,12 +675,12 @@ int vga_profile_read(vga_profile *out) {
     return VGA_OK;
 }
 
-int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, void *stream_ptr,
+int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, int consumer, void *stream_ptr,
                      double *gb_per_s) {
     clear_error();
     const int S = chunk_bytes;
     if (!gb_per_s || S < 16 || S > 1024 || (S & (S - 1)) || resident_bytes < (uint64_t)S ||
-        resident_bytes / (uint64_t)S > 0xFFFFFFFFull || gathers == 0) {
+        resident_bytes / (uint64_t)S > 0xFFFFFFFFull || gathers == 0 || (consumer != 0 && consumer != 1)) {
         set_error("vga_bench_gather: bad arguments");
         return VGA_EINVAL;
     }
@@ -639,10 +704,16 @@ int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers,
     for (int rep = 0; rep < 2; rep++) {  // warm-up, then the timed launch
         VGA_CHECK_CUDA(cudaEventRecord(e0, stream));
         switch (S) {
-#define VGA_CASE(SS)                                                                                              \
-    case SS:                                                                                                      \
-        gather_bench_kernel<SS><<<blocks, warps * 32, smem, stream>>>(buf.as<uint8_t>(), rows, (uint32_t)windows, \
-                                                                      out.as<uint32_t>());                        \
+#define VGA_CASE(SS)                                                                                          \
+    case SS:                                                                                                  \
+        if (consumer)                                                                                         \
+            gather_bench_kernel<SS, true><<<blocks, warps * 32, smem, stream>>>(buf.as<uint8_t>(), rows,       \
+                                                                                (uint32_t)windows,            \
+                                                                                out.as<uint32_t>());          \
+        else                                                                                                  \
+            gather_bench_kernel<SS, false><<<blocks, warps * 32, smem, stream>>>(buf.as<uint8_t>(), rows,      \
+                                                                                 (uint32_t)windows,           \
+                                                                                 out.as<uint32_t>());         \
         break;
             VGA_CASE(16)
             VGA_CASE(32)
