@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, d=unlimited and CPU baseline")
     ap.add_argument("--slice-bytes", type=int, default=0, help="force the union slice width (0 = automatic)")
     ap.add_argument("--warps", type=int, default=0, help="force union warps per CTA (0 = automatic)")
+    ap.add_argument("--union-mode", type=int, default=0,
+                    help="0 automatic, 1 one gather per neighbour, 2 per run of consecutive ids")
     ap.add_argument("--backend", default="nccl")
     return ap.parse_args()
 
@@ -316,9 +318,10 @@ def run_ours(args, dist: Dist):
     ball = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
-    def step(d):
+    def step(d, union_mode=None):
         return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=ws, stream=stream,
-                                     slice_bytes=args.slice_bytes, warps_per_cta=args.warps)
+                                     slice_bytes=args.slice_bytes, warps_per_cta=args.warps,
+                                     union_mode=args.union_mode if union_mode is None else union_mode)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -348,13 +351,14 @@ def run_ours(args, dist: Dist):
 
     # ---- roofline of the dominant kernel (the union pass) ----
     S = prof["slice_bytes"]
+    mode = prof["union_mode"]
     avg_ms = prof["union_ms"] / max(prof["union_launches"], 1)
-    gather_per_launch = E * S
+    gather_per_launch = prof["union_gather_bytes"] / max(prof["union_launches"], 1)
     hbm_per_launch = prof["union_hbm_bytes"] / max(prof["union_launches"], 1)
     l2_peak = vga.vga_bench_gather(N * S, S, 1_000_000_000 * 64 // S, consumer=1, stream=stream)
     loop_ceiling = vga.vga_bench_gather(N * S, S, 1_000_000_000 * 64 // S, consumer=0, stream=stream)
     achieved = gather_per_launch / (avg_ms / 1e3) / 1e9
-    kernel_name = f"hb_union_kernel<{S}>"
+    kernel_name = f"hb_union_runs_kernel<{S}>" if mode == 2 else f"hb_union_kernel<{S}>"
     traffic, traffic_note = recorded_traffic(kernel_name, args.config)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
@@ -368,7 +372,11 @@ def run_ours(args, dist: Dist):
         "union_loop_ceiling": {"value": loop_ceiling, "unit": "GB/s",
                                "what": "same microbenchmark folding with the union's bytewise max (no decode)"},
         "algorithmic_bytes_per_launch": gather_per_launch,
-        "algorithmic_bytes_definition": "E x slice_bytes neighbour-register gathers (per-edge union traffic)",
+        "algorithmic_bytes_definition": (
+            "range lookups x slice_bytes register-row gathers per slice launch (sparse-table build included in the "
+            "timed launch); a lookup covers a run of consecutive neighbour ids" if mode == 2 else
+            "E x slice_bytes neighbour-register gathers per slice launch"),
+        "union_mode": mode,
         "avg_launch_ms": avg_ms, "launches_timed": prof["union_launches"],
         "hbm_term": {"algorithmic_bytes_per_launch": hbm_per_launch,
                      "achieved": hbm_per_launch / (avg_ms / 1e3) / 1e9, "peak": hbm_peak,
@@ -420,6 +428,15 @@ def run_ours(args, dist: Dist):
         torch.cuda.synchronize()
         extras["dinf"] = {"seconds": f0.elapsed_time(f1) / 1e3, "passes": dinf_passes,
                           "geu_per_s": dinf_passes * E / (f0.elapsed_time(f1) / 1e3) / 1e9}
+        # ---- the other union variant, once, for comparison ----
+        other = 1 if mode == 2 else 2
+        step(args.d, union_mode=other)
+        f0.record(stream)
+        o_passes = step(args.d, union_mode=other)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        extras["other_union_mode"] = {"union_mode": other, "seconds": f0.elapsed_time(f1) / 1e3,
+                                      "geu_per_s": o_passes * E / (f0.elapsed_time(f1) / 1e3) / 1e9}
         if dist.rank == 0 and dist.world == 1:
             extras["cpu_baseline"] = cpu_baseline(obst, args)
 
@@ -427,7 +444,8 @@ def run_ours(args, dist: Dist):
             "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
-                       "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "parallelism": f"replicas x{dist.world}",
+                       "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode,
+                       "parallelism": f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",
                        "graph_build_seconds": build_s},
             "roofline": roofline, "gpu_launches": prof["kernel_launches"], "union_time_share": union_share,

@@ -159,9 +159,14 @@ int vga_visibility_count(int W, int H, const uint8_t *obst, uint32_t *n_nodes);
 /* Tuning knobs (all 0 = choose automatically). */
 typedef struct vga_tuning {
     int slice_bytes;     /* registers per union slice: power of two in [16, min(m, 1024)] */
-    int warps_per_cta;   /* union kernel CTA size in warps: 1..32                         */
+    int warps_per_cta;   /* union kernel CTA size in warps: 1..16                         */
     int l2_budget_mb;    /* L2 share the auto slice width aims at (default: 60 % of L2)   */
-    int reserved[5];
+    int union_mode;      /* 0 auto (= 2), 1 one gather per neighbour, 2 per run of
+                            consecutive ids through a sparse table of range maxima; both
+                            give the same registers bit for bit.  Mode 2 builds, on a
+                            graph's first use, a lookup list held by the graph (~4 bytes
+                            per run, about 0.65 byte per edge on city graphs).            */
+    int reserved[4];
 } vga_tuning;
 
 /*
@@ -264,13 +269,17 @@ int hyperball_run_trace(const vga_graph *g, int p, int d, uint64_t seed, int con
  * launch stream only while profiling is enabled. */
 typedef struct vga_profile {
     uint64_t kernel_launches;     /* library kernels launched since the last reset        */
-    uint64_t union_launches;      /* union-kernel launches timed                          */
+    uint64_t union_launches;      /* union slices timed (one union kernel, plus the
+                                     sparse-table build in mode 2)                        */
     double union_ms;              /* their summed device time                             */
-    uint64_t union_edges;         /* neighbour unions they performed (E per launch)       */
-    uint64_t union_gather_bytes;  /* per-edge register gathers: E x slice bytes, summed   */
-    uint64_t union_hbm_bytes;     /* CSR bytes + 8(N+1) + 2 x N x slice bytes, summed     */
+    uint64_t union_edges;         /* neighbour unions they performed (E per slice)        */
+    uint64_t union_gather_bytes;  /* register rows gathered x slice bytes, summed: E x S
+                                     in mode 1, lookups x S in mode 2                     */
+    uint64_t union_hbm_bytes;     /* streamed list bytes (CSR, or 4 x lookups) + 8(N+1)
+                                     + 2 x N x slice bytes, summed                        */
     int slice_bytes;              /* slice width of the last timed launch                 */
-    int reserved[3];
+    int union_mode;               /* union variant of the last timed launch (1 or 2)      */
+    int reserved[2];
 } vga_profile;
 
 /* Enable (1) or disable (0) event timing of union launches. */

@@ -31,13 +31,13 @@ vp, i32, u32, u64, i64, f64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_i
 
 class VgaTuning(C.Structure):
     _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
-                ("reserved", C.c_int * 5)]
+                ("union_mode", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class VgaProfile(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("union_launches", C.c_uint64), ("union_ms", C.c_double),
                 ("union_edges", C.c_uint64), ("union_gather_bytes", C.c_uint64), ("union_hbm_bytes", C.c_uint64),
-                ("slice_bytes", C.c_int), ("reserved", C.c_int * 3)]
+                ("slice_bytes", C.c_int), ("union_mode", C.c_int), ("reserved", C.c_int * 2)]
 
 
 SIGNATURES = {
@@ -112,11 +112,11 @@ def _ptr(a) -> int | None:
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
-def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0):
-    if not (slice_bytes or warps_per_cta or l2_budget_mb):
+def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0):
+    if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode):
         return None
     t = VgaTuning()
-    t.slice_bytes, t.warps_per_cta, t.l2_budget_mb = slice_bytes, warps_per_cta, l2_budget_mb
+    t.slice_bytes, t.warps_per_cta, t.l2_budget_mb, t.union_mode = slice_bytes, warps_per_cta, l2_budget_mb, union_mode
     return C.pointer(t)
 
 
@@ -259,6 +259,7 @@ def hyperball_run(g: Graph, p: int = 10, d: int = 0, seed: int = 0):
 
 
 def hyperball_workspace_bytes(g: Graph, p: int) -> int:
+    """Workspace bytes of hyperball_run_dev with automatic tuning."""
     b = C.c_uint64()
     _check(lib().hyperball_workspace_bytes(g.handle, p, C.byref(b)))
     return b.value
@@ -266,13 +267,13 @@ def hyperball_workspace_bytes(g: Graph, p: int) -> int:
 
 def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
                       workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
-                      l2_budget_mb: int = 0) -> int:
+                      l2_budget_mb: int = 0, union_mode: int = 0) -> int:
     """Algorithm 1 into device tensors (float64, N each); returns passes run."""
     it = C.c_int()
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
-                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb)))
+                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode)))
     return it.value
 
 
@@ -288,7 +289,7 @@ def hyperball_run_noalloc(g: Graph, p: int, d: int, seed: int, mean_depth_dev, b
 
 
 def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0, max_trace: int = 8,
-                        slice_bytes: int = 0, warps_per_cta: int = 0):
+                        slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0):
     """Run with per-pass register and estimate dumps (bit-exact checks).
 
     Returns dict(mean_depth, ball, iterations, regs[(max_trace+1), N, m], c[(max_trace+1), N])."""
@@ -299,7 +300,8 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
     cc = np.zeros(max((max_trace + 1) * n, 1), np.float64)
     it = C.c_int()
     _check(lib().hyperball_run_trace(g.handle, p, d, seed, conv_mode, _ptr(md), _ptr(ball), C.byref(it),
-                                     _ptr(regs), _ptr(cc), max_trace, _tuning(slice_bytes, warps_per_cta)))
+                                     _ptr(regs), _ptr(cc), max_trace,
+                                     _tuning(slice_bytes, warps_per_cta, union_mode=union_mode)))
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}

@@ -74,12 +74,11 @@ __device__ __forceinline__ uint32_t split_bytes(const SplitAcc &a) {
     return (a.hi & 0xFF00FF00u) | ((a.lo >> 8) & 0x00FF00FFu);
 }
 
-// Fold the S-byte slices of rows ids[0..cnt) of `cur` into acc (4 * V4 words
-// per lane, split form).  Loads for U neighbours per lane are issued before
-// any is folded.
-template <int S>
-__device__ __forceinline__ void gather_fold(const uint8_t *__restrict__ cur, const uint32_t *ids, int cnt, int g,
-                                            int sub, SplitAcc (&acc)[4 * GatherShape<S>::V4]) {
+// Fold the S-byte rows row(ids[0..cnt)) into acc (4 * V4 words per lane, split
+// form).  Loads for U rows per lane are issued before any is folded.
+template <int S, class Row>
+__device__ __forceinline__ void gather_fold(const Row &row, const uint32_t *ids, int cnt, int g, int sub,
+                                            SplitAcc (&acc)[4 * GatherShape<S>::V4]) {
     using Sh = GatherShape<S>;
     static_assert(Sh::U % 2 == 0, "loads are folded in pairs");
     for (int k0 = 0; k0 < cnt; k0 += Sh::P * Sh::U) {
@@ -88,7 +87,7 @@ __device__ __forceinline__ void gather_fold(const uint8_t *__restrict__ cur, con
         for (int u = 0; u < Sh::U; u++) {
             const int k = k0 + u * Sh::P + g;
             if (k < cnt) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(cur + (uint64_t)ids[k] * S + sub * Sh::CH);
+                const uint4 *src = reinterpret_cast<const uint4 *>(row(ids[k]) + sub * Sh::CH);
 #pragma unroll
                 for (int q = 0; q < Sh::V4; q++) x[u][q] = __ldg(src + q);
             } else {
@@ -107,6 +106,26 @@ __device__ __forceinline__ void gather_fold(const uint8_t *__restrict__ cur, con
             }
     }
 }
+
+// Row of node id in one register slice.
+template <int S>
+struct SliceRow {
+    const uint8_t *__restrict__ cur;
+    __device__ __forceinline__ const uint8_t *operator()(uint32_t id) const { return cur + (uint64_t)id * S; }
+};
+
+// Row of a range lookup (level k, index i): T_0 is the slice itself, T_1..T_K
+// follow each other in `tab`, N rows each.
+template <int S>
+struct TableRow {
+    const uint8_t *__restrict__ cur;
+    const uint8_t *__restrict__ tab;
+    uint32_t n;
+    __device__ __forceinline__ const uint8_t *operator()(uint32_t lk) const {
+        const uint32_t lvl = lk >> kLkIndexBits, i = lk & kLkIndexMask;
+        return lvl ? tab + ((uint64_t)(lvl - 1) * n + i) * S : cur + (uint64_t)i * S;
+    }
+};
 
 // Convert the split accumulators to register bytes and fold the P lane groups
 // of a warp together (every lane ends with the group maximum).
@@ -165,7 +184,7 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
         if (T == 0) break;  // cannot happen on a validated graph; guarantees progress
         if ((T >> lane) & 1u) ids[__popc(T & lt_mask)] = r.id;
         __syncwarp();
-        gather_fold<S>(cur, ids, __popc(T), g, sub, acc);
+        gather_fold<S>(SliceRow<S>{cur}, ids, __popc(T), g, sub, acc);
         __syncwarp();
         base = r.next_base;
         pos += (uint64_t)r.advance;
@@ -187,6 +206,71 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     if (__any_sync(0xffffffffu, changed) && lane == 0) {
         if (*reinterpret_cast<volatile uint32_t *>(flags) == 0u) atomicOr(flags, 1u);
     }
+}
+
+// Run-aware Eq. hll-union for one register slice (runs.cu explains the
+// lookups): next[v] = max(cur[v], max over v's range lookups of T_k[i]), where
+// T_k[i] = max(cur[i .. i + 2^k)) has been built for this slice.  One warp per
+// node streams its lookups 32 at a time (evict-first: each is read once per
+// slice) and gathers the S-byte table rows exactly like the per-edge kernel.
+template <int S>
+__global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__restrict__ lk_off,
+                                                            const uint32_t *__restrict__ lk,
+                                                            const uint8_t *__restrict__ cur,
+                                                            const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt,
+                                                            uint32_t n, uint32_t *__restrict__ flags) {
+    using Sh = GatherShape<S>;
+    extern __shared__ uint32_t s_ids[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *ids = s_ids + wib * 32;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= n) return;
+    const uint32_t v = (uint32_t)warp;
+    const int g = lane / Sh::G, sub = lane % Sh::G;
+    SplitAcc acc[4 * Sh::V4];
+#pragma unroll
+    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
+    const TableRow<S> row{cur, tab, n};
+    const uint64_t end = lk_off[v + 1];
+    for (uint64_t b = lk_off[v]; b < end; b += 32) {
+        const int cnt = (end - b < 32) ? (int)(end - b) : 32;
+        if (lane < cnt) ids[lane] = __ldcs(lk + b + lane);
+        __syncwarp();
+        gather_fold<S>(row, ids, cnt, g, sub, acc);
+        __syncwarp();
+    }
+    uint4 nb[Sh::V4];
+    finish_groups<S>(acc, nb);
+    bool changed = false;
+    if (g == 0) {
+        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
+        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * Sh::CH);
+#pragma unroll
+        for (int q = 0; q < Sh::V4; q++) {
+            const uint4 o4 = __ldg(own + q);
+            const uint4 res = vmax4(nb[q], o4);
+            dst[q] = res;
+            changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
+        }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) {
+        if (*reinterpret_cast<volatile uint32_t *>(flags) == 0u) atomicOr(flags, 1u);
+    }
+}
+
+// One sparse-table level for a slice: out[i] = max(prev[i], prev[i + half]) for
+// i = 0 .. rows-1 (rows = N - 2*half + 1; later rows are never looked up).
+// One thread per 16-byte chunk.
+__global__ void hb_table_level_kernel(const uint8_t *__restrict__ prev, uint8_t *__restrict__ out, uint32_t rows,
+                                      uint32_t half, int S) {
+    const uint32_t chunks = (uint32_t)S / 16u;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)rows * chunks) return;
+    const uint64_t i = t / chunks, c = t % chunks;
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(prev + i * S) + c);
+    const uint4 b = __ldg(reinterpret_cast<const uint4 *>(prev + (i + half) * S) + c);
+    reinterpret_cast<uint4 *>(out + i * S)[c] = vmax4(a, b);
 }
 
 // Microbenchmark twin of hb_union_kernel: rows drawn from a hash instead of
@@ -231,7 +315,7 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
                     for (int q = 0; q < Sh::V4; q++) x_acc ^= x[u][q].x ^ x[u][q].y ^ x[u][q].z ^ x[u][q].w;
             }
         } else {
-            gather_fold<S>(buf, ids, 32, g, sub, acc);
+            gather_fold<S>(SliceRow<S>{buf}, ids, 32, g, sub, acc);
         }
         __syncwarp();
     }
@@ -339,15 +423,20 @@ __global__ void hb_finalize_kernel(uint32_t n, const uint32_t *__restrict__ comp
 // Host side
 // ---------------------------------------------------------------------------
 
+constexpr int kModePerEdge = 1;  // one gather per neighbour (hb_union_kernel)
+constexpr int kModeRuns = 2;     // one or two gathers per run of consecutive ids (hb_union_runs_kernel)
+
 struct Plan {
     int p = 10;
     uint32_t m = 1024;
     int S = 1024;          // slice bytes
     int slices = 1;
     int warps = 8;         // union kernel warps per CTA
+    int mode = kModeRuns;  // union variant
     uint64_t n = 0;
     // workspace layout (byte offsets, 256-aligned)
-    uint64_t off_cur = 0, off_next = 0, off_c0 = 0, off_c1 = 0, off_sum = 0, off_lc = 0, off_flags = 0, total = 0;
+    uint64_t off_cur = 0, off_next = 0, off_c0 = 0, off_c1 = 0, off_sum = 0, off_lc = 0, off_flags = 0, off_tab = 0,
+             total = 0;
 };
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -360,6 +449,18 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->p = p;
     P->m = 1u << p;
     P->n = g->n;
+    const int req_mode = tune ? tune->union_mode : 0;
+    if (req_mode < 0 || req_mode > kModeRuns) {
+        set_error("union_mode = %d must be 0 (auto), 1 (per neighbour) or 2 (per run)", req_mode);
+        return VGA_EINVAL;
+    }
+    if (req_mode == kModeRuns && (uint64_t)g->n > kRunMaxNodes) {
+        set_error("union_mode 2 supports at most 2^29 nodes (graph has %u)", g->n);
+        return VGA_EINVAL;
+    }
+    P->mode = req_mode ? req_mode : ((uint64_t)g->n <= kRunMaxNodes ? kModeRuns : kModePerEdge);
+    // rows of counters the union reads per slice: the slice, plus the sparse-table levels in runs mode
+    const uint64_t rows_per_node = P->mode == kModeRuns ? (uint64_t)kRunLevels + 1 : 1;
     int S = tune ? tune->slice_bytes : 0;
     if (S != 0) {
         if (S < 16 || S > 1024 || (S & (S - 1)) || (uint32_t)S > P->m) {
@@ -372,7 +473,7 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         uint64_t budget = (tune && tune->l2_budget_mb > 0) ? (uint64_t)tune->l2_budget_mb << 20
                                                            : (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
         S = (int)std::min<uint32_t>(P->m, 1024u);
-        while (S > 16 && (uint64_t)S * P->n > budget) S >>= 1;
+        while (S > 16 && (uint64_t)S * P->n * rows_per_node > budget) S >>= 1;
     }
     P->S = S;
     P->slices = (int)(P->m / (uint32_t)S);
@@ -390,6 +491,8 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->off_sum = o;   o = align256(o + 8 * P->n);
     P->off_lc = o;    o = align256(o + 8 * ((uint64_t)P->m + 1));
     P->off_flags = o; o = align256(o + 64);
+    P->off_tab = o;
+    if (P->mode == kModeRuns) o = align256(o + (uint64_t)kRunLevels * P->n * (uint64_t)S);
     P->total = o;
     return VGA_OK;
 }
@@ -435,13 +538,38 @@ static ProfileState &prof() {
 struct PendingTiming {
     cudaEvent_t start, stop;
     uint64_t edges, gather_bytes, hbm_bytes;
-    int S;
+    int S, mode;
 };
 
-static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, uint8_t *nxt, uint32_t *flags,
-                        cudaStream_t stream, std::vector<PendingTiming> *timings) {
+template <int SS>
+static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t *c, uint8_t *x, uint8_t *tab,
+                               uint32_t *flags, cudaStream_t stream) {
     const unsigned blocks = (unsigned)((P.n + P.warps - 1) / P.warps);
     const size_t smem = (size_t)P.warps * 32 * sizeof(uint32_t);
+    if (P.mode == kModeRuns) {
+        const uint8_t *prev = c;
+        for (int k = 1; k <= kRunLevels; k++) {
+            const uint64_t w = 1ull << k;
+            if (P.n < w) break;  // no run can be this long
+            const uint32_t rows = (uint32_t)(P.n - w + 1);
+            uint8_t *out = tab + (uint64_t)(k - 1) * P.n * SS;
+            const uint64_t threads = (uint64_t)rows * (SS / 16);
+            hb_table_level_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(prev, out, rows,
+                                                                                         (uint32_t)(w >> 1), SS);
+            count_launch();
+            prev = out;
+        }
+        hb_union_runs_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_lk_off, g->d_lk, c, tab, x,
+                                                                         (uint32_t)P.n, flags);
+    } else {
+        hb_union_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
+                                                                    flags);
+    }
+    count_launch();
+}
+
+static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, uint8_t *nxt, uint8_t *tab,
+                        uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings) {
     const uint64_t slice_bytes = (uint64_t)P.n * P.S;
     for (int s = 0; s < P.slices; s++) {
         const uint8_t *c = cur + (uint64_t)s * slice_bytes;
@@ -453,30 +581,29 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
         }
         switch (P.S) {
-#define VGA_CASE(SS)                                                                                            \
-    case SS:                                                                                                    \
-        hb_union_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n, \
-                                                                    flags);                                     \
-        break;
-            VGA_CASE(16)
-            VGA_CASE(32)
-            VGA_CASE(64)
-            VGA_CASE(128)
-            VGA_CASE(256)
-            VGA_CASE(512)
-            VGA_CASE(1024)
-#undef VGA_CASE
+            case 16: launch_union_slice<16>(P, g, c, x, tab, flags, stream); break;
+            case 32: launch_union_slice<32>(P, g, c, x, tab, flags, stream); break;
+            case 64: launch_union_slice<64>(P, g, c, x, tab, flags, stream); break;
+            case 128: launch_union_slice<128>(P, g, c, x, tab, flags, stream); break;
+            case 256: launch_union_slice<256>(P, g, c, x, tab, flags, stream); break;
+            case 512: launch_union_slice<512>(P, g, c, x, tab, flags, stream); break;
+            case 1024: launch_union_slice<1024>(P, g, c, x, tab, flags, stream); break;
             default:
                 set_error("internal: slice width %d", P.S);
                 return VGA_EINVAL;
         }
-        count_launch();
         if (timings) {
             VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
             pt.edges = g->n_edges;
-            pt.gather_bytes = g->n_edges * (uint64_t)P.S;
-            pt.hbm_bytes = g->n_bytes + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
+            if (P.mode == kModeRuns) {
+                pt.gather_bytes = g->lk_total * (uint64_t)P.S;
+                pt.hbm_bytes = 4 * g->lk_total + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
+            } else {
+                pt.gather_bytes = g->n_edges * (uint64_t)P.S;
+                pt.hbm_bytes = g->n_bytes + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
+            }
             pt.S = P.S;
+            pt.mode = P.mode;
             timings->push_back(pt);
         }
     }
@@ -496,6 +623,7 @@ static void settle_timings(std::vector<PendingTiming> &timings) {
             ps.acc.union_gather_bytes += pt.gather_bytes;
             ps.acc.union_hbm_bytes += pt.hbm_bytes;
             ps.acc.slice_bytes = pt.S;
+            ps.acc.union_mode = pt.mode;
         }
         cudaEventDestroy(pt.start);
         cudaEventDestroy(pt.stop);
@@ -558,6 +686,8 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     double *sum_d = reinterpret_cast<double *>(base + P.off_sum);
     double *lc = reinterpret_cast<double *>(base + P.off_lc);
     uint32_t *flags = reinterpret_cast<uint32_t *>(base + P.off_flags);
+    uint8_t *tab = base + P.off_tab;
+    if (P.mode == kModeRuns && P.n > 0) VGA_TRY(ensure_run_lookups(g, stream));
 
     bool profiling;
     {
@@ -583,7 +713,7 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         uint32_t hflags[2];
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
-            VGA_TRY(launch_union(P, g, cur, nxt, flags, stream, profiling ? &timings : nullptr));
+            VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, profiling ? &timings : nullptr));
             VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
             if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
             VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, stream));
@@ -749,8 +879,11 @@ int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int c
         set_error("hyperball_run_noalloc: the graph lives on device %d but device %d is current", g->device, dev);
         return VGA_EINVAL;
     }
+    // the per-neighbour union: the run-aware one would allocate its lookup list
+    vga_tuning per_edge{};
+    per_edge.union_mode = kModePerEdge;
     Plan P;
-    VGA_TRY(make_plan(g, p, nullptr, &P));
+    VGA_TRY(make_plan(g, p, &per_edge, &P));
     if (P.total > kStaticScratchBytes) {
         set_error("hyperball_run_noalloc: N = %u at p = %d needs %llu bytes of scratch but the fixed scratch holds "
                   "%llu bytes (64 MiB); pass a workspace to hyperball_run_dev instead",
@@ -763,7 +896,7 @@ int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int c
     // everything else before reading it, so stale contents of the shared scratch
     // from an earlier call cannot leak into this one.
     return run_impl(g, p, d, seed, conv_mode, mean_depth_dev, ball_size_dev, iterations, scratch, kStaticScratchBytes,
-                    static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, -1);
+                    static_cast<cudaStream_t>(stream), &per_edge, nullptr, nullptr, -1);
 }
 
 int hyperball_workspace_bytes(const vga_graph *g, int p, uint64_t *bytes) {

@@ -1,0 +1,161 @@
+// runs.cu -- range lookups for the run-aware union.
+//
+// Eq. hll-union takes the register-wise max over a node's neighbours.  In a
+// visibility graph numbered in raster order (Sec. 3.2) a neighbour list is a
+// sequence of runs of consecutive ids: a visible stretch of a grid row is a
+// block of consecutive node ids (the paper's one-byte deltas of 1).  On the
+// 236k-cell city graph a list of ~20k neighbours has ~1.8k runs.  The max over
+// a run [a, a+L) equals the max of two overlapping power-of-two windows of a
+// sparse table T_k[i] = max(cur[i .. i + 2^k)), so each run costs one or two
+// gathers instead of L; runs of 32 or more are covered by ceil(L/16) windows of
+// 16.  Max is associative, commutative and idempotent, so the result is the
+// same register array, bit for bit.
+//
+// This file turns the LEB128 CSR into the list of (level, row) lookups of
+// every node, once per graph: one warp per node decodes its list with the
+// warp window decoder, finds run boundaries across windows, and emits each
+// completed run's lookups.
+#include <vector>
+
+#include "vga_common.cuh"
+
+namespace vga {
+namespace {
+
+// Lookups covering the run [a, a + L).
+__device__ __forceinline__ uint32_t run_lookup_count(uint32_t L) {
+    if (L < 32u) {
+        const uint32_t k = 31u - __clz(L);
+        return (L == (1u << k)) ? 1u : 2u;
+    }
+    return (L >> 4) + ((L & 15u) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_t *out) {
+    if (L < 32u) {
+        const uint32_t k = 31u - __clz(L);
+        out[0] = (k << kLkIndexBits) | a;
+        if (L != (1u << k)) out[1] = (k << kLkIndexBits) | (a + L - (1u << k));
+        return;
+    }
+    const uint32_t full = L >> 4;
+    for (uint32_t j = 0; j < full; j++) out[j] = (4u << kLkIndexBits) | (a + 16u * j);
+    if (L & 15u) out[full] = (4u << kLkIndexBits) | (a + L - 16u);
+}
+
+// One warp per node.  WRITE = false stores the node's lookup count in cnt[v];
+// WRITE = true writes the lookups at lk[lk_off[v] ...].
+template <bool WRITE>
+__global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes, uint32_t n,
+                                   uint64_t *__restrict__ cnt, const uint64_t *__restrict__ lk_off,
+                                   uint32_t *__restrict__ lk) {
+    __shared__ uint32_t s_ids[8][33];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *ids = s_ids[wib];
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= n) return;
+    const uint32_t v = (uint32_t)warp;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint64_t pos = off[v];
+    const uint64_t end = off[v + 1];
+    uint32_t base = 0;
+    uint32_t run_a = 0, run_len = 0;  // the run still open at the end of the last window
+    uint64_t out = WRITE ? lk_off[v] : 0;
+    while (pos < end) {
+        const WindowDecode<uint32_t> r = decode_window<uint32_t>(bytes, pos, end, base, lane);
+        const uint32_t T = r.term_mask;
+        if (T == 0) break;  // cannot happen on a validated graph
+        if ((T >> lane) & 1u) ids[__popc(T & lt_mask)] = r.id;
+        __syncwarp();
+        const int c = __popc(T);
+        const uint32_t id = lane < c ? ids[lane] : 0u;
+        bool start = false;
+        if (lane < c) start = (lane == 0) ? !(run_len > 0 && id == run_a + run_len) : (id != ids[lane - 1] + 1u);
+        const uint32_t starts = __ballot_sync(0xffffffffu, start);
+        // 1. the open run absorbs the lanes before the window's first start (all
+        //    of them if there is none); it is complete once a start follows
+        if (run_len > 0) {
+            if (starts) {
+                run_len += (uint32_t)(__ffs(starts) - 1);
+                if (WRITE && lane == 0) run_lookup_write(run_a, run_len, lk + out);
+                out += run_lookup_count(run_len);
+                run_len = 0;
+            } else {
+                run_len += (uint32_t)c;
+            }
+        }
+        // 2. runs starting in this window: complete if another start follows
+        const uint32_t later = starts & ~((2u << lane) - 1u);  // starts after this lane (lane < 31)
+        const bool complete = start && lane < 31 && later != 0u;
+        const uint32_t L = complete ? (uint32_t)(__ffs(later) - 1 - lane) : 0u;
+        const uint32_t my = complete ? run_lookup_count(L) : 0u;
+        uint32_t incl = my;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (WRITE && complete) run_lookup_write(id, L, lk + out + (incl - my));
+        out += __shfl_sync(0xffffffffu, incl, 31);
+        // 3. the last start of the window opens a run that may continue
+        if (starts) {
+            const int last = 31 - __clz(starts);
+            run_a = __shfl_sync(0xffffffffu, id, last);
+            run_len = (uint32_t)(c - last);
+        }
+        __syncwarp();
+        base = r.next_base;
+        pos += (uint64_t)r.advance;
+    }
+    if (run_len > 0) {
+        if (WRITE && lane == 0) run_lookup_write(run_a, run_len, lk + out);
+        out += run_lookup_count(run_len);
+    }
+    if (!WRITE && lane == 0) cnt[v] = out;
+}
+
+}  // namespace
+
+int ensure_run_lookups(const vga_graph *g, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lock(g->lk_mu);
+    if (g->lk_ready) return VGA_OK;
+    if ((uint64_t)g->n > kRunMaxNodes) {
+        set_error("run-aware union supports at most 2^29 nodes (graph has %u)", g->n);
+        return VGA_EINVAL;
+    }
+    const uint32_t n = g->n;
+    DeviceBuffer d_cnt, d_off, d_lk;
+    VGA_TRY(d_cnt.alloc(8 * (size_t)(n ? n : 1)));
+    VGA_TRY(d_off.alloc(8 * ((size_t)n + 1)));
+    const int warps = 8;
+    const unsigned blocks = (unsigned)(((uint64_t)n + warps - 1) / warps);
+    std::vector<uint64_t> h_off((size_t)n + 1, 0);
+    if (n) {
+        run_lookups_kernel<false><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n,
+                                                                     d_cnt.as<uint64_t>(), nullptr, nullptr);
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+        std::vector<uint64_t> h_cnt(n);
+        VGA_CHECK_CUDA(cudaMemcpyAsync(h_cnt.data(), d_cnt.ptr, 8 * (size_t)n, cudaMemcpyDeviceToHost, stream));
+        VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+        for (uint32_t v = 0; v < n; v++) h_off[v + 1] = h_off[v] + h_cnt[v];
+    }
+    const uint64_t total = h_off[n];
+    VGA_TRY(d_lk.alloc(4 * (size_t)(total ? total : 1)));
+    VGA_CHECK_CUDA(cudaMemcpyAsync(d_off.ptr, h_off.data(), 8 * ((size_t)n + 1), cudaMemcpyHostToDevice, stream));
+    if (n) {
+        run_lookups_kernel<true><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, nullptr,
+                                                                    d_off.as<uint64_t>(), d_lk.as<uint32_t>());
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+    }
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    g->d_lk_off = static_cast<uint64_t *>(d_off.release());
+    g->d_lk = static_cast<uint32_t *>(d_lk.release());
+    g->lk_total = total;
+    g->lk_ready = true;
+    return VGA_OK;
+}
+
+}  // namespace vga

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include "vga_hyperball.h"
 
@@ -24,6 +25,13 @@ struct vga_graph {
     uint8_t *d_bytes = nullptr;     // n_bytes + kBytePad
     uint32_t *d_degree = nullptr;   // n
     uint32_t *d_comp = nullptr;     // n, or nullptr: every node in one component of size n
+    // Range lookups of the run-aware union, built on first use (see runs.cu):
+    // node v's lookups are d_lk[d_lk_off[v] .. d_lk_off[v+1]).
+    mutable std::mutex lk_mu;
+    mutable uint64_t *d_lk_off = nullptr;  // n+1
+    mutable uint32_t *d_lk = nullptr;      // lk_total
+    mutable uint64_t lk_total = 0;
+    mutable bool lk_ready = false;
 };
 
 namespace vga {
@@ -108,6 +116,18 @@ struct PinnedBuffer {
     template <class T>
     T *as() const { return static_cast<T *>(ptr); }
 };
+
+// Range lookups of the run-aware union.  A neighbour list in raster order is a
+// sequence of runs of consecutive ids; the maximum over a run [a, a+L) is read
+// from a sparse table T_k[i] = max(cur[i .. i + 2^k)) for k = 0..kRunLevels.
+// Each lookup is one u32: level k in the top 3 bits, row i in the low 29.
+constexpr int kRunLevels = 4;        // windows of 1, 2, 4, 8, 16 rows
+constexpr uint32_t kLkIndexBits = 29;
+constexpr uint32_t kLkIndexMask = (1u << kLkIndexBits) - 1u;
+constexpr uint64_t kRunMaxNodes = 1ull << kLkIndexBits;
+
+// Build the graph's lookup list on first use (thread-safe); no-op afterwards.
+int ensure_run_lookups(const vga_graph *g, cudaStream_t stream);
 
 // Creates a graph object around already-copied device offsets and bytes:
 // validates the stream on the device, derives degrees and E.  Takes

@@ -250,6 +250,8 @@ void vga_graph_free(vga_graph *g) {
     cudaFree(g->d_bytes);
     cudaFree(g->d_degree);
     if (g->d_comp) cudaFree(g->d_comp);
+    if (g->d_lk_off) cudaFree(g->d_lk_off);
+    if (g->d_lk) cudaFree(g->d_lk);
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     delete g;
 }

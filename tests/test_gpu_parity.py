@@ -114,16 +114,39 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("seed,p,d,S,warps,conv", CASES)
-def test_hyperball_bit_exact(vga, seed, p, d, S, warps, conv):
+def test_hyperball_bit_exact(vga, seed, p, d, S, warps, conv, mode):
+    # mode 1: one gather per neighbour; mode 2: per run of consecutive ids via range maxima
     _, off, b, cells = tiny_graph(seed)
     T = 12
     ref = oracle.hyperball(off, b, p, d, seed=seed * 7, conv_mode=conv, trace=T)
     with vga.vga_graph_load(off, b) as g:
         got = vga.hyperball_run_trace(g, p, d, seed=seed * 7, conv_mode=conv, max_trace=T, slice_bytes=S,
-                                      warps_per_cta=warps)
+                                      warps_per_cta=warps, union_mode=mode)
     assert got["iterations"] <= T
     assert_same_run(got, ref)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("grid", ["open40x30", "open1x300", "comb"])
+def test_long_runs(vga, grid, mode):
+    # complete graphs (every list is one or two runs of up to N-1 ids) and a comb
+    # of walls (many short runs): range lookups of every level, windows split
+    # into 16-row pieces, runs ending at the last node id
+    if grid == "open40x30":
+        obst = workloads.open_grid(40, 30)
+    elif grid == "open1x300":
+        obst = workloads.open_grid(300, 1)
+    else:
+        obst = workloads.open_grid(33, 21)
+        obst[2:19:2, 3:30] = 1
+    off, b, cells = oracle.build_graph(obst)
+    ref = oracle.hyperball(off, b, 8, 0, seed=3, trace=10)
+    with vga.vga_graph_load(off, b) as g:
+        for S in (0, 16, 256):
+            got = vga.hyperball_run_trace(g, 8, 0, seed=3, max_trace=10, slice_bytes=S, union_mode=mode)
+            assert_same_run(got, ref)
 
 
 def test_hyperball_run_plain(vga):
@@ -218,6 +241,8 @@ def test_bad_arguments(vga):
                 vga.hyperball_run_trace(g, 10, 1, slice_bytes=S, max_trace=1)
         with pytest.raises(vga.VgaError):
             vga.hyperball_run_trace(g, 6, 1, slice_bytes=128, max_trace=1)  # slice wider than m = 64
+        with pytest.raises(vga.VgaError):
+            vga.hyperball_run_trace(g, 10, 1, max_trace=1, union_mode=3)
 
 
 # ----------------------------------------------------------------------------

@@ -44,8 +44,9 @@ def test_mid_grid_full_parity(vga):
     with g:
         o2, b2, _ = g.copy_csr()
         assert np.array_equal(o2, off) and np.array_equal(b2, b)
-        for S, warps in ((0, 0), (128, 8), (64, 12)):
-            got = vga.hyperball_run_trace(g, 10, 0, seed=1, max_trace=16, slice_bytes=S, warps_per_cta=warps)
+        for S, warps, mode in ((0, 0, 0), (128, 8, 1), (64, 12, 2), (256, 4, 2)):
+            got = vga.hyperball_run_trace(g, 10, 0, seed=1, max_trace=16, slice_bytes=S, warps_per_cta=warps,
+                                          union_mode=mode)
             assert got["iterations"] == ref["iterations"]
             for t in range(got["iterations"] + 1):
                 assert np.array_equal(got["regs"][t], ref["regs"][t]), (S, t)
@@ -53,7 +54,7 @@ def test_mid_grid_full_parity(vga):
             assert np.array_equal(got["mean_depth"], ref["mean_depth"])
 
 
-def _sampled_checks(vga, obst, p, d, n_sample, seed=0, min_edges=None, max_edges=None):
+def _sampled_checks(vga, obst, p, d, n_sample, seed=0, min_edges=None, max_edges=None, union_mode=0):
     g, gcells = vga.vga_visibility_build(obst, return_cells=True)
     with g:
         n = g.n_nodes
@@ -70,7 +71,7 @@ def _sampled_checks(vga, obst, p, d, n_sample, seed=0, min_edges=None, max_edges
             got = oracle.decode_list(g_bytes, int(g_off[v]), int(g_off[v + 1]), n)
             assert np.array_equal(got, nbrs[k]), f"neighbour list of node {v}"
         del g_bytes
-        out = vga.hyperball_run_trace(g, p, d, seed=seed, max_trace=max(d, 1))
+        out = vga.hyperball_run_trace(g, p, d, seed=seed, max_trace=max(d, 1), union_mode=union_mode)
     regs, c, T = out["regs"], out["c"], out["iterations"]
     if d > 0:
         assert T == d
@@ -95,9 +96,10 @@ def _sampled_checks(vga, obst, p, d, n_sample, seed=0, min_edges=None, max_edges
     return n, T
 
 
-def test_medium_config_sampled(vga):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_medium_config_sampled(vga, mode):
     # 220 x 220, sides 2..20, ~12 % cover, ~42.7k free cells; p = 10, d = 3
-    n, T = _sampled_checks(vga, workloads.medium(3), p=10, d=3, n_sample=48)
+    n, T = _sampled_checks(vga, workloads.medium(3), p=10, d=3, n_sample=48, union_mode=mode)
     assert abs(n - 42_700) / 42_700 < 0.005
 
 
