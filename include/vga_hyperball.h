@@ -260,6 +260,25 @@ int hyperball_run_trace(const vga_graph *g, int p, int d, uint64_t seed, int con
                         const vga_tuning *tuning);
 
 
+/*
+ * vga_metrics -- the closed-form VGA metrics of Sec. 3.3 ("Metric
+ * derivation"), from mean depth, the exact component sizes N_v and the
+ * degrees of a loaded graph, for every node:
+ *   RA = 2 (MD - 1) / (k - 2), k = N_v;
+ *   Integration [HH] = 1 / RRA = D_k / RA, with the RRA normaliser
+ *     D_k = 2 (k (log2((k+2)/3) - 1) + 1) / ((k-1)(k-2)), the RA of the root of
+ *     a diamond-shaped graph of k nodes (Hillier & Hanson; the paper names RRA
+ *     but prints no normaliser);
+ *   Integration [Tekl] = log2((MD + 2) / 3);
+ *   P-value = max(0, 1 - RA);
+ *   Point First Moment = MD x deg(v).
+ * HH and P-value are NaN when k <= 2 (RA undefined); HH is +inf when MD = 1.
+ *   mean_depth_dev  device, N doubles (hyperball_run_dev's output).
+ *   out_dev         device out, N x 4 doubles: HH, Tekl, P-value, PFM per node.
+ *   stream          cudaStream_t or NULL; the call does not synchronise.
+ */
+int vga_metrics(const vga_graph *g, const double *mean_depth_dev, double *out_dev, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Measurement (not part of the paper's method)                            */
 /* ---------------------------------------------------------------------- */

@@ -10,9 +10,9 @@ arrays through ctypes.  Each wrapper names the passage of the paper
 ("City-Scale Visibility Graph Analysis via GPU-Accelerated HyperBall") that the
 C function follows.
 
-Parity pins live in ``tests/test_oracle_*.py``.  Nothing here is "parity
-unpinned" except the items listed in the header of ``vga_oracle.c``'s
-readings, each of which has a pin in those tests.
+Parity pins live in ``tests/test_oracle_*.py``; every function here has one
+(the readings of the paper each function takes are listed in the header of
+``vga_oracle.c``).
 """
 from __future__ import annotations
 
@@ -106,6 +106,10 @@ def lib():
             L.orc_hyperball.restype = C.c_int
             L.orc_bfs.argtypes = [C.c_int64, u64p, u8p, C.c_int64, i32p]
             L.orc_bfs.restype = C.c_int
+            L.orc_dvalue.argtypes = [C.c_double]
+            L.orc_dvalue.restype = C.c_double
+            L.orc_metrics.argtypes = [C.c_int64, f64p, _nullable(u32p), u32p, f64p]
+            L.orc_metrics.restype = None
             _lib = L
     return _lib
 
@@ -323,3 +327,23 @@ def bfs(offsets, bytes_, src: int):
     if ecc < 0:
         raise ValueError("malformed CSR")
     return dist[:n], int(ecc)
+
+
+# --------------------------------------------------------------------------
+# Closed-form metrics (Sec. 3.3 "Metric derivation")
+# --------------------------------------------------------------------------
+
+def dvalue(k: float) -> float:
+    """RA of the root of a diamond-shaped graph with k nodes (RRA normaliser)."""
+    return float(lib().orc_dvalue(k))
+
+
+def metrics(mean_depth, degree, comp_size=None):
+    """(N, 4) array of Integration [HH], Integration [Tekl], P-value, Point First Moment."""
+    md = np.ascontiguousarray(mean_depth, np.float64)
+    n = len(md)
+    deg = np.ascontiguousarray(degree, np.uint32)
+    cs = None if comp_size is None else np.ascontiguousarray(comp_size, np.uint32)
+    out = np.zeros(max(4 * n, 1), np.float64)
+    lib().orc_metrics(n, md if n else np.zeros(1), cs, deg if n else np.zeros(1, np.uint32), out)
+    return out[: 4 * n].reshape(n, 4)

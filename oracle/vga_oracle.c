@@ -545,3 +545,39 @@ int orc_bfs(int64_t n, const uint64_t *offsets, const uint8_t *bytes, int64_t sr
     free(queue);
     return ecc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Closed-form VGA metrics (Sec. 3.3, "Metric derivation").                  */
+/* From MD(v), the exact component size k = N_v and the degree:            */
+/*   RA    = 2 (MD - 1) / (k - 2)                                            */
+/*   D_k   = 2 (k (log2((k + 2) / 3) - 1) + 1) / ((k - 1)(k - 2)), the RA of  */
+/*           the root of a diamond-shaped graph of k nodes (Hillier & Hanson */
+/*           1984; the paper names RRA but prints no normaliser)            */
+/*   HH    = 1 / RRA = D_k / RA                                              */
+/*   Tekl  = log2((MD + 2) / 3)                                              */
+/*   P     = max(0, 1 - RA)                                                  */
+/*   PFM   = MD x deg                                                        */
+/* k <= 2 leaves RA undefined: HH and P are NaN.  out is N x 4 (HH, Tekl,   */
+/* P, PFM) per node.                                                         */
+/* ------------------------------------------------------------------------ */
+double orc_dvalue(double k) {
+    return 2.0 * (k * (log2((k + 2.0) / 3.0) - 1.0) + 1.0) / ((k - 1.0) * (k - 2.0));
+}
+
+void orc_metrics(int64_t n, const double *md, const uint32_t *comp_size, const uint32_t *degree, double *out) {
+    for (int64_t v = 0; v < n; v++) {
+        double k = comp_size ? (double)comp_size[v] : (double)n;
+        double m = md[v];
+        double hh = NAN, pv = NAN;
+        if (k > 2.0) {
+            double ra = 2.0 * (m - 1.0) / (k - 2.0);
+            hh = orc_dvalue(k) / ra;
+            pv = 1.0 - ra;
+            if (pv < 0.0) pv = 0.0;
+        }
+        out[4 * v + 0] = hh;
+        out[4 * v + 1] = log2((m + 2.0) / 3.0);
+        out[4 * v + 2] = pv;
+        out[4 * v + 3] = m * (double)degree[v];
+    }
+}

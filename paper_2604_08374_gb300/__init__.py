@@ -59,6 +59,7 @@ SIGNATURES = {
     "hyperball_run_trace": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, vp, i32, C.POINTER(VgaTuning)],
                             i32),
     "hyperball_run_noalloc": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp], i32),
+    "vga_metrics": ([vp, vp, vp, vp], i32),
     "vga_profile_enable": ([i32], i32),
     "vga_profile_reset": ([], i32),
     "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
@@ -305,6 +306,15 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}
+
+
+def vga_metrics(g: Graph, mean_depth_dev, out_dev=None, stream=None):
+    """Closed-form metrics (Sec. 3.3): (N, 4) device tensor of HH, Tekl, P-value, PFM."""
+    if out_dev is None:
+        import torch
+        out_dev = torch.empty((g.n_nodes, 4), dtype=torch.float64, device=mean_depth_dev.device)
+    _check(lib().vga_metrics(g.handle, _ptr(mean_depth_dev), _ptr(out_dev), _stream_ptr(stream)))
+    return out_dev
 
 
 # --------------------------------------------------------------------------

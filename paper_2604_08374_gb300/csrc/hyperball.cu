@@ -50,7 +50,7 @@ struct GatherShape {
     static constexpr int G = S / CH;
     static constexpr int P = 32 / G;
     static constexpr int V4 = CH / 16;
-    static constexpr int U = (V4 == 1) ? 4 : 2;
+    static constexpr int U = (V4 == 1) ? (S <= 128 ? 8 : 4) : 2;  // narrow rows: more loads in flight
 };
 
 // Bytewise max through 16-bit lanes.  For a register word w = [b3 b2 b1 b0],

@@ -279,3 +279,36 @@ def test_file_round_trip(vga, tmp_path):
     with pytest.raises(vga.VgaError) as e:
         vga.vga_graph_load_file(path)
     assert e.value.status == vga.VGA_ECORRUPT
+
+
+# ----------------------------------------------------------------------------
+# closed-form metrics (Sec. 3.3 "Metric derivation")
+# ----------------------------------------------------------------------------
+
+def test_metrics_match_oracle(vga):
+    torch = pytest.importorskip("torch")
+    _, off, b, cells = tiny_graph(4)
+    n = len(cells)
+    row_ptr, _ = oracle.decode_csr(off, b)
+    deg = np.diff(row_ptr.astype(np.int64)).astype(np.uint32)
+    comp = np.full(n, n, np.uint32)
+    comp[:3] = [2, 1, 40]  # degenerate and small components too
+    ref_md = oracle.hyperball(off, b, 10, 3, comp_size=comp)["mean_depth"]
+    md_in = ref_md.copy()
+    md_in[5] = 1.0          # exact MD = 1 gives HH = +inf
+    ref = oracle.metrics(md_in, deg, comp_size=comp)
+    with vga.vga_graph_load(off, b, comp_size=comp) as g:
+        md_dev = torch.from_numpy(md_in).cuda()
+        got = vga.vga_metrics(g, md_dev).cpu().numpy()
+        torch.cuda.synchronize()
+        # the same MD straight from the GPU run feeds the same metrics
+        md_gpu = torch.empty(n, dtype=torch.float64, device="cuda")
+        vga.hyperball_run_dev(g, 10, 3, 0, md_gpu, None)
+        got_run = vga.vga_metrics(g, md_gpu).cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    assert np.array_equal(np.isinf(got), np.isinf(ref))
+    fin = np.isfinite(ref)
+    np.testing.assert_allclose(got[fin], ref[fin], rtol=1e-12, atol=0)
+    ref_run = oracle.metrics(ref_md, deg, comp_size=comp)
+    fin = np.isfinite(ref_run)
+    np.testing.assert_allclose(got_run[fin], ref_run[fin], rtol=MD_RTOL, atol=0)
