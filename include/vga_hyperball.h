@@ -260,6 +260,106 @@ int hyperball_run_trace(const vga_graph *g, int p, int d, uint64_t seed, int con
                         const vga_tuning *tuning);
 
 
+/* ---------------------------------------------------------------------- */
+/* Batched analyses                                                        */
+/* ---------------------------------------------------------------------- */
+
+/* One analysis of a batch. */
+typedef struct vga_job {
+    const vga_graph *graph;  /* in: loaded graph on the current device                 */
+    int p;                   /* in: HLL precision, 4..16                               */
+    int d;                   /* in: depth limit (<= 0: unlimited)                      */
+    uint64_t seed;           /* in: hash seed                                          */
+    int conv_mode;           /* in: 0 or 1, as in hyperball_run_dev                    */
+    int reserved;
+    double *mean_depth_dev;  /* out: device, N doubles, or NULL                        */
+    double *ball_size_dev;   /* out: device, N doubles, or NULL                        */
+    int iterations;          /* out: union passes run                                  */
+    int status;              /* out: VGA_OK                                            */
+} vga_job;
+
+/* Workspace bytes hyperball_run_batch needs for these jobs. */
+int hyperball_batch_workspace_bytes(const vga_job *jobs, int n_jobs, uint64_t *bytes);
+
+/*
+ * hyperball_run_batch -- run many analyses (Algorithm 1) together, on graphs
+ * of any size and mixed p, d, seed and convergence rule.  Each phase of a pass
+ * is one launch for the whole batch: a persistent union kernel whose CTAs take
+ * (job, register slice, block of nodes) items from an atomic queue, a batched
+ * estimate + Eq. sumD launch, a per-job step (stop rules), and the mean-depth
+ * epilogue of the jobs that stopped.  Per job the results are bit-identical
+ * to hyperball_run_dev with union_mode 1 (one gather per neighbour).
+ *   jobs, n_jobs     the batch (jobs with N = 0 are skipped, iterations 0).
+ *   workspace_dev    device, >= hyperball_batch_workspace_bytes, 256-byte
+ *                    aligned, or NULL to let the library allocate.
+ *   stream           cudaStream_t or NULL; the call returns when all jobs are done.
+ *   use_graph        0: the host reads a running flag after every pass;
+ *                    1: the pass loop is captured once as a CUDA graph with a
+ *                    WHILE conditional node and runs with no host round trip.
+ */
+int hyperball_run_batch(vga_job *jobs, int n_jobs, void *workspace_dev, uint64_t workspace_bytes, void *stream,
+                        int use_graph);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: a request loop with continuous batching                        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct vga_server vga_server;
+
+typedef struct vga_server_config {
+    uint64_t hbm_budget_bytes;  /* device bytes requests may hold at once (0: 150 GiB)      */
+    int max_batch;              /* requests advanced together in the batched lane (0: 256) */
+    int solo_nodes;             /* graphs above this many nodes use the solo lane (0: 65536) */
+    int reserved[4];
+} vga_server_config;
+
+typedef struct vga_server_stats_t {
+    uint64_t submitted, completed, queued;
+    uint64_t batched_passes;    /* passes the batched lane has run                   */
+    uint64_t budget_used, budget_peak;
+    uint64_t batched_peak;      /* most requests advanced together in one pass       */
+} vga_server_stats_t;
+
+/*
+ * vga_server_create -- start a server on the current device.  Analyses
+ * (Algorithm 1) of already-loaded graphs are submitted from any thread and run
+ * as soon as their device state fits the HBM budget:
+ *   - the batched lane (graphs up to solo_nodes nodes) admits waiting requests
+ *     between passes and advances all admitted ones together, one pass per
+ *     round, through the batched engine (hyperball_run_batch's kernels);
+ *     requests join and leave between passes (continuous batching);
+ *   - the solo lane runs larger graphs one at a time with hyperball_run_dev's
+ *     run-aware union, on its own stream, overlapping the batched lane.
+ * Each request's results are bit-identical to running it alone.  Graph
+ * memory is the caller's and is not charged to the budget.
+ */
+int vga_server_create(const vga_server_config *cfg, vga_server **out);
+
+/*
+ * vga_server_submit -- queue one analysis.  mean_depth_host and
+ * ball_size_host (N doubles each, or NULL) are written when it completes and
+ * must stay valid until vga_server_wait returns for it.  The graph must stay
+ * loaded until then.  VGA_EBUSY if the request alone exceeds the budget or the
+ * server is stopping.
+ */
+int vga_server_submit(vga_server *s, const vga_graph *g, int p, int d, uint64_t seed, int conv_mode,
+                      double *mean_depth_host, double *ball_size_host, uint64_t *request_id);
+
+/*
+ * vga_server_wait -- block until the request completes or timeout_s elapses
+ * (<= 0: no limit; VGA_ETIMEOUT then).  On completion returns the request's
+ * status, passes run, latency (submit to outputs written, seconds) and the
+ * part of it spent waiting for admission.  Each id can be waited for once.
+ */
+int vga_server_wait(vga_server *s, uint64_t request_id, double timeout_s, int *iterations, double *latency_s,
+                    double *queued_s);
+
+/* Counters of the server. */
+int vga_server_stats(vga_server *s, vga_server_stats_t *out);
+
+/* Finish every submitted request, then stop the lanes and free the server. */
+void vga_server_destroy(vga_server *s);
+
 /*
  * vga_metrics -- the closed-form VGA metrics of Sec. 3.3 ("Metric
  * derivation"), from mean depth, the exact component sizes N_v and the

@@ -34,6 +34,23 @@ class VgaTuning(C.Structure):
                 ("union_mode", C.c_int), ("reserved", C.c_int * 4)]
 
 
+class VgaJob(C.Structure):
+    _fields_ = [("graph", C.c_void_p), ("p", C.c_int), ("d", C.c_int), ("seed", C.c_uint64), ("conv_mode", C.c_int),
+                ("reserved", C.c_int), ("mean_depth_dev", C.c_void_p), ("ball_size_dev", C.c_void_p),
+                ("iterations", C.c_int), ("status", C.c_int)]
+
+
+class VgaServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_batch", C.c_int), ("solo_nodes", C.c_int),
+                ("reserved", C.c_int * 4)]
+
+
+class VgaServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("queued", C.c_uint64),
+                ("batched_passes", C.c_uint64), ("budget_used", C.c_uint64), ("budget_peak", C.c_uint64),
+                ("batched_peak", C.c_uint64)]
+
+
 class VgaProfile(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("union_launches", C.c_uint64), ("union_ms", C.c_double),
                 ("union_edges", C.c_uint64), ("union_gather_bytes", C.c_uint64), ("union_hbm_bytes", C.c_uint64),
@@ -60,6 +77,13 @@ SIGNATURES = {
                             i32),
     "hyperball_run_noalloc": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp], i32),
     "vga_metrics": ([vp, vp, vp, vp], i32),
+    "hyperball_batch_workspace_bytes": ([C.POINTER(VgaJob), i32, C.POINTER(u64)], i32),
+    "hyperball_run_batch": ([C.POINTER(VgaJob), i32, vp, u64, vp, i32], i32),
+    "vga_server_create": ([C.POINTER(VgaServerConfig), C.POINTER(vp)], i32),
+    "vga_server_submit": ([vp, vp, i32, i32, u64, i32, vp, vp, C.POINTER(u64)], i32),
+    "vga_server_wait": ([vp, u64, f64, C.POINTER(i32), C.POINTER(f64), C.POINTER(f64)], i32),
+    "vga_server_stats": ([vp, C.POINTER(VgaServerStats)], i32),
+    "vga_server_destroy": ([vp], None),
     "vga_profile_enable": ([i32], i32),
     "vga_profile_reset": ([], i32),
     "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
@@ -306,6 +330,90 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}
+
+
+def _job_array(jobs):
+    arr = (VgaJob * max(len(jobs), 1))()
+    for k, j in enumerate(jobs):
+        arr[k].graph = j["graph"].handle.value
+        arr[k].p, arr[k].d, arr[k].seed = j["p"], j.get("d", 0), j.get("seed", 0)
+        arr[k].conv_mode = j.get("conv_mode", 0)
+        arr[k].mean_depth_dev = _ptr(j.get("mean_depth"))
+        arr[k].ball_size_dev = _ptr(j.get("ball"))
+    return arr
+
+
+def hyperball_batch_workspace_bytes(jobs) -> int:
+    arr = _job_array(jobs)
+    b = C.c_uint64()
+    _check(lib().hyperball_batch_workspace_bytes(arr, len(jobs), C.byref(b)))
+    return b.value
+
+
+def hyperball_run_batch(jobs, workspace=None, stream=None, use_graph: bool = True):
+    """Run many analyses together.  jobs: dicts with graph, p, d, seed,
+    conv_mode and device tensors mean_depth / ball (float64, N each, optional).
+    Returns the passes run per job."""
+    arr = _job_array(jobs)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().hyperball_run_batch(arr, len(jobs), _ptr(workspace), ws_bytes, _stream_ptr(stream),
+                                     1 if use_graph else 0))
+    return [arr[k].iterations for k in range(len(jobs))]
+
+
+class Server:
+    """Request loop with continuous batching (vga_server_*).  Results arrive in
+    host numpy arrays; keep graphs loaded until their requests are waited for."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_batch: int = 0, solo_nodes: int = 0):
+        cfg = VgaServerConfig()
+        cfg.hbm_budget_bytes, cfg.max_batch, cfg.solo_nodes = hbm_budget_bytes, max_batch, solo_nodes
+        h = C.c_void_p()
+        _check(lib().vga_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._outputs = {}
+
+    def submit(self, g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0) -> int:
+        md = np.empty(max(g.n_nodes, 1), np.float64)
+        ball = np.empty(max(g.n_nodes, 1), np.float64)
+        rid = C.c_uint64()
+        _check(lib().vga_server_submit(self._h, g.handle, p, d, seed, conv_mode, _ptr(md), _ptr(ball),
+                                       C.byref(rid)))
+        self._outputs[rid.value] = (md, ball, g.n_nodes)
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 0.0):
+        """-> dict(mean_depth, ball, iterations, latency_s, queued_s)."""
+        it, lat, q = C.c_int(), C.c_double(), C.c_double()
+        status = lib().vga_server_wait(self._h, rid, timeout_s, C.byref(it), C.byref(lat), C.byref(q))
+        if status == VGA_ETIMEOUT:
+            _check(status)
+        md, ball, n = self._outputs.pop(rid)
+        _check(status)
+        return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value, "latency_s": lat.value,
+                "queued_s": q.value}
+
+    def stats(self) -> dict:
+        st = VgaServerStats()
+        _check(lib().vga_server_stats(self._h, C.byref(st)))
+        return {name: getattr(st, name) for name, _ in VgaServerStats._fields_}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().vga_server_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def vga_metrics(g: Graph, mean_depth_dev, out_dev=None, stream=None):

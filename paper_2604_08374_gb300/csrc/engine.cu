@@ -1,0 +1,479 @@
+// engine.cu -- many HyperBall analyses (Algorithm 1) advanced together.
+//
+// A batch holds jobs (graph, p, d, seed, convergence rule) of any size.  Each
+// phase of a pass is one launch for the whole batch:
+//   union     a persistent kernel: CTAs claim work items (job, slice, block of
+//             W nodes) from an atomic counter, so uneven jobs balance across
+//             the GPU; items run in job-major, slice-major order, so the
+//             counters being gathered are one job's slice at a time and stay
+//             in L2;
+//   estimate  one warp per node of every running job (estimator + Eq. sumD);
+//   step      one thread per job: pass count, stop rule, flags;
+//   finalize  mean depth and ball sizes of the jobs that just stopped.
+// The pass loop is either driven from the host (one flag read per pass) or
+// captured once as a CUDA graph whose WHILE conditional node repeats the four
+// launches until no job is running, with no host round trip at all.
+//
+// Every job's registers, estimates and outputs are bit-identical to a
+// single-graph run of the same job (same device functions, same order of
+// floating-point operations per node).
+#include <algorithm>
+#include <vector>
+
+#include "engine.cuh"
+#include "hb_device.cuh"
+
+namespace vga {
+
+
+
+namespace {
+
+
+
+// Index of the job whose [start[j], start[j+1]) range holds x.
+__device__ __forceinline__ int find_job(const uint64_t *__restrict__ start, int n_jobs, uint64_t x) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void batch_init_kernel(JobDev *jobs, const uint64_t *__restrict__ node_start, int n_jobs,
+                                  uint64_t total_nodes) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total_nodes;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const int j = find_job(node_start, n_jobs, x);
+        const JobDev &J = jobs[j];
+        init_node(J.regs[0], J.n, J.p, J.S, J.seed, (uint32_t)(x - node_start[j]));
+    }
+}
+
+// initial != 0: c_0 of every job; otherwise pass t = job.t + 1 of running jobs.
+__global__ void batch_estimate_kernel(JobDev *jobs, const uint64_t *__restrict__ node_start, int n_jobs,
+                                      uint64_t total_nodes, int initial) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t x = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); x < total_nodes; x += warps) {
+        const int j = find_job(node_start, n_jobs, x);
+        JobDev &J = jobs[j];
+        if (!initial && J.state != 0) continue;
+        const int t = initial ? 0 : J.t + 1;
+        const double *c_prev = t ? J.c[(t - 1) & 1] : nullptr;
+        estimate_node(J.regs[t & 1], J.n, J.p, J.S, t, J.alpha_mm, J.lc, c_prev, J.c[t & 1], J.sum_d, &J.inc,
+                      (uint32_t)(x - node_start[j]), lane);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void batch_union_item(JobDev &J, uint32_t s, uint32_t v, uint32_t *ids, int lane) {
+    const int t = J.t + 1;
+    const uint64_t slice = (uint64_t)s * J.n * S;
+    union_node_edges<S>(J.off, J.bytes, J.regs[(t - 1) & 1] + slice, J.regs[t & 1] + slice, v, ids, lane,
+                        &J.changed);
+}
+
+// Persistent union over all running jobs' (slice, node-block) items.
+__global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *jobs,
+                                                                        const uint64_t *__restrict__ item_start,
+                                                                        int n_jobs, uint64_t total_items,
+                                                                        unsigned long long *counter) {
+    __shared__ uint32_t s_ids[kEngineWarps][32];
+    __shared__ unsigned long long s_item;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+        __syncthreads();
+        const uint64_t item = s_item;
+        __syncthreads();
+        if (item >= total_items) break;
+        const int j = find_job(item_start, n_jobs, item);
+        JobDev &J = jobs[j];
+        if (J.state != 0) continue;
+        const uint64_t r = item - item_start[j];
+        const uint32_t s = (uint32_t)(r / (uint64_t)J.blocks);
+        const uint32_t v = (uint32_t)(r % (uint64_t)J.blocks) * kEngineWarps + wib;
+        if (v >= J.n) continue;
+        uint32_t *ids = s_ids[wib];
+        switch (J.S) {
+            case 16: batch_union_item<16>(J, s, v, ids, lane); break;
+            case 32: batch_union_item<32>(J, s, v, ids, lane); break;
+            case 64: batch_union_item<64>(J, s, v, ids, lane); break;
+            case 128: batch_union_item<128>(J, s, v, ids, lane); break;
+            case 256: batch_union_item<256>(J, s, v, ids, lane); break;
+            case 512: batch_union_item<512>(J, s, v, ids, lane); break;
+            default: batch_union_item<1024>(J, s, v, ids, lane); break;
+        }
+    }
+}
+
+// One thread per job: close the pass, apply the stop rule, reset the flags and
+// the union's item counter; report whether any job still runs.
+__global__ void batch_step_kernel(JobDev *jobs, int n_jobs, unsigned long long *counter, int *any_running,
+                                  cudaGraphConditionalHandle cond, int use_cond) {
+    int running = 0;
+    for (int j = threadIdx.x; j < n_jobs; j += blockDim.x) {
+        JobDev &J = jobs[j];
+        if (J.state == 1) J.state = 2;
+        if (J.state == 0) {
+            const int t = J.t + 1;
+            J.t = t;
+            bool stop = J.conv ? (J.inc == 0u) : (J.changed == 0u);
+            if (J.d > 0 && t >= J.d) stop = true;
+            if (stop) J.state = 1;
+            J.changed = 0u;
+            J.inc = 0u;
+        }
+        running |= (J.state == 0);
+    }
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        *counter = 0ull;
+        *any_running = running;
+        if (use_cond) cudaGraphSetConditional(cond, running ? 1u : 0u);
+    }
+}
+
+__global__ void batch_finalize_kernel(JobDev *jobs, const uint64_t *__restrict__ node_start, int n_jobs,
+                                      uint64_t total_nodes) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total_nodes;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const int j = find_job(node_start, n_jobs, x);
+        const JobDev &J = jobs[j];
+        if (J.state != 1) continue;
+        finalize_node(J.n, J.comp, J.sum_d, J.c[J.t & 1], J.md, J.ball, (uint32_t)(x - node_start[j]));
+    }
+}
+
+}  // namespace
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+
+
+uint64_t l2_budget_bytes(int dev) {
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
+}
+
+JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget) {
+    JobLayout L;
+    const uint32_t m = 1u << p;
+    int S = (int)std::min<uint32_t>(m, (uint32_t)(slice_cap > 0 ? slice_cap : 1024));
+    while (S > 16 && (uint64_t)S * n > budget) S >>= 1;
+    L.S = S;
+    L.slices = (int)(m / (uint32_t)S);
+    L.blocks = (int)((n + kEngineWarps - 1) / kEngineWarps);
+    uint64_t o = 0;
+    o = align256(o + (uint64_t)n * m);
+    o = align256(o + (uint64_t)n * m);
+    o = align256(o + 8ull * n);
+    o = align256(o + 8ull * n);
+    o = align256(o + 8ull * n);
+    L.bytes = o;
+    return L;
+}
+
+JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
+                   const double *lc, double *md, double *ball) {
+    JobDev J{};
+    const uint64_t n = g->n, m = 1ull << p;
+    uint64_t o = 0;
+    J.regs[0] = ws + o; o = align256(o + n * m);
+    J.regs[1] = ws + o; o = align256(o + n * m);
+    J.c[0] = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
+    J.c[1] = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
+    J.sum_d = reinterpret_cast<double *>(ws + o);
+    J.off = g->d_offsets;
+    J.bytes = g->d_bytes;
+    J.comp = g->d_comp;
+    J.lc = lc;
+    J.md = md;
+    J.ball = ball;
+    J.alpha_mm = hll_alpha_host(p) * (double)m * (double)m;
+    J.seed = seed;
+    J.n = g->n;
+    J.p = p;
+    J.S = L.S;
+    J.slices = L.slices;
+    J.d = d;
+    J.conv = conv;
+    J.blocks = L.blocks;
+    return J;
+}
+
+// Linear-counting tables of p = 4..16 side by side (8 (2^p + 1) bytes each).
+uint64_t lc_offset(int p) {
+    uint64_t o = 0;
+    for (int q = 4; q < p; q++) o = align256(o + 8ull * ((1ull << q) + 1));
+    return o;
+}
+uint64_t lc_all_bytes() { return lc_offset(17); }
+
+int upload_lc_tables(uint8_t *dst, const bool *used, cudaStream_t stream) {
+    for (int p = 4; p <= 16; p++) {
+        if (used && !used[p]) continue;
+        const std::vector<double> &t = lc_table(p);
+        VGA_CHECK_CUDA(cudaMemcpyAsync(dst + lc_offset(p), t.data(), 8 * t.size(), cudaMemcpyHostToDevice, stream));
+    }
+    return VGA_OK;
+}
+
+
+
+uint64_t engine_arrays_bytes(int cap) {
+    return align256(sizeof(JobDev) * (uint64_t)std::max(cap, 1)) + 2 * align256(8ull * (cap + 1)) + 256;
+}
+
+EngineArrays engine_arrays_at(uint8_t *base, int cap) {
+    EngineArrays A;
+    uint64_t o = 0;
+    A.jobs = reinterpret_cast<JobDev *>(base + o); o = align256(o + sizeof(JobDev) * (uint64_t)std::max(cap, 1));
+    A.node_start = reinterpret_cast<uint64_t *>(base + o); o = align256(o + 8ull * (cap + 1));
+    A.item_start = reinterpret_cast<uint64_t *>(base + o); o = align256(o + 8ull * (cap + 1));
+    A.counter = reinterpret_cast<unsigned long long *>(base + o);
+    A.any_running = reinterpret_cast<int *>(base + o + 8);
+    A.cap = cap;
+    return A;
+}
+
+
+
+// Upload descriptors and prefix arrays of `jobs` (host copies) into A; the
+// host vectors are copied synchronously before the function returns.
+int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, EngineSet *E, cudaStream_t stream) {
+    const int nj = (int)jobs.size();
+    if (nj > A.cap) {
+        set_error("internal: %d jobs exceed the engine capacity %d", nj, A.cap);
+        return VGA_EINVAL;
+    }
+    std::vector<uint64_t> ns(nj + 1, 0), is(nj + 1, 0);
+    for (int k = 0; k < nj; k++) {
+        ns[k + 1] = ns[k] + jobs[k].n;
+        is[k + 1] = is[k] + (uint64_t)jobs[k].slices * (uint64_t)jobs[k].blocks;
+    }
+    if (nj) VGA_CHECK_CUDA(cudaMemcpyAsync(A.jobs, jobs.data(), sizeof(JobDev) * nj, cudaMemcpyHostToDevice, stream));
+    VGA_CHECK_CUDA(cudaMemcpyAsync(A.node_start, ns.data(), 8 * (nj + 1), cudaMemcpyHostToDevice, stream));
+    VGA_CHECK_CUDA(cudaMemcpyAsync(A.item_start, is.data(), 8 * (nj + 1), cudaMemcpyHostToDevice, stream));
+    VGA_CHECK_CUDA(cudaMemsetAsync(A.counter, 0, 16, stream));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));  // ns / is are about to go out of scope
+    E->n_jobs = nj;
+    E->total_nodes = ns[nj];
+    E->total_items = is[nj];
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_union_kernel, kEngineWarps * 32, 0);
+    E->grid_union = (unsigned)std::max(1, sms * std::max(1, per_sm));
+    E->grid_nodes = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((E->total_nodes + 255) / 256, (uint64_t)sms * 32));
+    E->grid_warps = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((E->total_nodes + 7) / 8, (uint64_t)sms * 64));
+    return VGA_OK;
+}
+
+// Counters of freshly uploaded jobs: zero their initial registers and sum_d,
+// insert every node into its own counter, and estimate c_0.
+int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const EngineSet &E, cudaStream_t stream) {
+    for (const JobDev &J : jobs) {
+        VGA_CHECK_CUDA(cudaMemsetAsync(J.regs[0], 0, (uint64_t)J.n << J.p, stream));
+        VGA_CHECK_CUDA(cudaMemsetAsync(J.sum_d, 0, 8ull * J.n, stream));
+    }
+    if (!E.n_jobs) return VGA_OK;
+    batch_init_kernel<<<E.grid_nodes, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes);
+    count_launch();
+    batch_estimate_kernel<<<E.grid_warps, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes, 1);
+    count_launch();
+    VGA_CHECK_CUDA(cudaGetLastError());
+    return VGA_OK;
+}
+
+int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, cudaGraphConditionalHandle cond,
+                int use_cond) {
+    batch_union_kernel<<<E.grid_union, kEngineWarps * 32, 0, stream>>>(A.jobs, A.item_start, E.n_jobs,
+                                                                       E.total_items, A.counter);
+    count_launch();
+    batch_estimate_kernel<<<E.grid_warps, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes, 0);
+    count_launch();
+    batch_step_kernel<<<1, 256, 0, stream>>>(A.jobs, E.n_jobs, A.counter, A.any_running, cond, use_cond);
+    count_launch();
+    batch_finalize_kernel<<<E.grid_nodes, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes);
+    count_launch();
+    VGA_CHECK_CUDA(cudaGetLastError());
+    return VGA_OK;
+}
+
+// Capture one pass as the body of a WHILE conditional node and run it until
+// no job is running.
+int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t stream) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    VGA_CHECK_CUDA(cudaGraphCreate(&graph, 0));
+    struct GraphGuard {
+        cudaGraph_t &g;
+        cudaGraphExec_t &e;
+        ~GraphGuard() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{graph, exec};
+    cudaGraphConditionalHandle cond;
+    VGA_CHECK_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams params = {};
+    params.type = cudaGraphNodeTypeConditional;
+    params.conditional.handle = cond;
+    params.conditional.type = cudaGraphCondTypeWhile;
+    params.conditional.size = 1;
+    cudaGraphNode_t node;
+    VGA_CHECK_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &params));
+    cudaGraph_t body = params.conditional.phGraph_out[0];
+    cudaStream_t cap = nullptr;
+    VGA_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = VGA_OK;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        rc = engine_pass(A, E, cap, cond, 1);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &captured);
+        if (rc == VGA_OK && e2 != cudaSuccess) {
+            set_error("capturing the pass loop failed: %s", cudaGetErrorString(e2));
+            rc = VGA_ECUDA;
+        }
+    } else {
+        set_error("cudaStreamBeginCaptureToGraph failed: %s", cudaGetErrorString(e));
+        rc = VGA_ECUDA;
+    }
+    cudaStreamDestroy(cap);
+    VGA_TRY(rc);
+    VGA_CHECK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    VGA_CHECK_CUDA(cudaGraphLaunch(exec, stream));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    return VGA_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// hyperball_run_batch
+// ---------------------------------------------------------------------------
+
+struct BatchPlan {
+    std::vector<int> idx;          // jobs with N > 0, in batch order
+    std::vector<JobLayout> lay;
+    std::vector<uint64_t> job_off; // workspace offset of each job's block
+    bool lc_used[17] = {false};
+    uint64_t off_lc = 0, off_arrays = 0, total = 0;
+};
+
+int plan_batch(const vga_job *jobs, int n_jobs, int slice_cap, BatchPlan *B) {
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) {
+        set_error("hyperball batch: bad job list");
+        return VGA_EINVAL;
+    }
+    int dev = -1;
+    VGA_CHECK_CUDA(cudaGetDevice(&dev));
+    const uint64_t budget = l2_budget_bytes(dev);
+    uint64_t o = 0;
+    for (int i = 0; i < n_jobs; i++) {
+        const vga_job &jb = jobs[i];
+        if (!jb.graph || jb.p < 4 || jb.p > 16 || (jb.conv_mode != 0 && jb.conv_mode != 1)) {
+            set_error("hyperball batch: job %d has a null graph, p outside 4..16 or a bad conv_mode", i);
+            return VGA_EINVAL;
+        }
+        if (jb.graph->device != dev) {
+            set_error("hyperball batch: job %d's graph lives on device %d, device %d is current", i,
+                      jb.graph->device, dev);
+            return VGA_EINVAL;
+        }
+        if (jb.graph->n == 0) continue;
+        const JobLayout L = job_layout(jb.graph->n, jb.p, slice_cap, budget);
+        B->idx.push_back(i);
+        B->lay.push_back(L);
+        B->job_off.push_back(o);
+        o = align256(o + L.bytes);
+        B->lc_used[jb.p] = true;
+    }
+    B->off_lc = o;
+    o = align256(o + lc_all_bytes());
+    B->off_arrays = o;
+    o = align256(o + engine_arrays_bytes((int)B->idx.size()));
+    B->total = o;
+    return VGA_OK;
+}
+
+int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaStream_t stream, int use_graph,
+              int slice_cap) {
+    BatchPlan B;
+    VGA_TRY(plan_batch(jobs, n_jobs, slice_cap, &B));
+    DeviceBuffer own;
+    if (!ws_ptr) {
+        VGA_TRY(own.alloc(B.total));
+        ws_ptr = own.ptr;
+    } else if (ws_bytes < B.total || (reinterpret_cast<uintptr_t>(ws_ptr) & 255u)) {
+        set_error("hyperball batch: workspace of %llu bytes, need %llu (256-byte aligned)",
+                  (unsigned long long)ws_bytes, (unsigned long long)B.total);
+        return VGA_EINVAL;
+    }
+    uint8_t *ws = static_cast<uint8_t *>(ws_ptr);
+    for (int i = 0; i < n_jobs; i++) {
+        jobs[i].iterations = 0;
+        jobs[i].status = VGA_OK;
+    }
+    if (B.idx.empty()) return VGA_OK;
+    VGA_TRY(upload_lc_tables(ws + B.off_lc, B.lc_used, stream));
+    std::vector<JobDev> host(B.idx.size());
+    for (size_t k = 0; k < B.idx.size(); k++) {
+        const vga_job &jb = jobs[B.idx[k]];
+        host[k] = make_jobdev(jb.graph, jb.p, jb.d, jb.seed, jb.conv_mode, B.lay[k], ws + B.job_off[k],
+                              reinterpret_cast<const double *>(ws + B.off_lc + lc_offset(jb.p)), jb.mean_depth_dev,
+                              jb.ball_size_dev);
+    }
+    const EngineArrays A = engine_arrays_at(ws + B.off_arrays, (int)host.size());
+    EngineSet E;
+    VGA_TRY(engine_upload(A, host, &E, stream));
+    VGA_TRY(engine_start(A, host, E, stream));
+    if (use_graph) {
+        VGA_TRY(engine_run_graph(A, E, stream));
+    } else {
+        int running = 1;
+        while (running) {
+            VGA_TRY(engine_pass(A, E, stream, 0, 0));
+            VGA_CHECK_CUDA(cudaMemcpyAsync(&running, A.any_running, sizeof(int), cudaMemcpyDeviceToHost, stream));
+            VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+        }
+    }
+    VGA_CHECK_CUDA(cudaMemcpyAsync(host.data(), A.jobs, sizeof(JobDev) * host.size(), cudaMemcpyDeviceToHost, stream));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    for (size_t k = 0; k < host.size(); k++) jobs[B.idx[k]].iterations = host[k].t;
+    return VGA_OK;
+}
+
+}  // namespace
+}  // namespace vga
+
+using namespace vga;
+
+extern "C" {
+
+int hyperball_batch_workspace_bytes(const vga_job *jobs, int n_jobs, uint64_t *bytes) {
+    clear_error();
+    if (!bytes) {
+        set_error("hyperball_batch_workspace_bytes: null argument");
+        return VGA_EINVAL;
+    }
+    BatchPlan B;
+    VGA_TRY(plan_batch(jobs, n_jobs, 0, &B));
+    *bytes = B.total;
+    return VGA_OK;
+}
+
+int hyperball_run_batch(vga_job *jobs, int n_jobs, void *workspace_dev, uint64_t workspace_bytes, void *stream,
+                        int use_graph) {
+    clear_error();
+    return run_batch(jobs, n_jobs, workspace_dev, workspace_bytes, static_cast<cudaStream_t>(stream), use_graph, 0);
+}
+
+}  // extern "C"

@@ -13,251 +13,74 @@
 #include <mutex>
 #include <vector>
 
-#include "vga_common.cuh"
+#include "hb_device.cuh"
 
 namespace vga {
-namespace {
 
-// SplitMix64 (Steele, Lea, Flood 2014): one golden-ratio state step, then the
-// output mix.  Sec. 3.3 inserts node v into its own counter with this hash.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
+// HLL alpha_m (Flajolet et al. 2007).
+double hll_alpha_host(int p) {
+    const double m = (double)(1u << p);
+    if (p == 4) return 0.673;
+    if (p == 5) return 0.697;
+    if (p == 6) return 0.709;
+    return 0.7213 / (1.0 + 1.079 / m);
 }
 
-// Alg. 1 initialisation: node v's counter gets rho in register j, where j is
-// the top p bits of the hash and rho the position of the first set bit of the
-// remaining 64-p bits (65-p if none).  The registers were zeroed beforehand.
+// Linear-counting table m ln(m / V), V = 1..m, computed once per p on the host
+// so that the device and any host consumer see the same doubles.
+const std::vector<double> &lc_table(int p) {
+    static std::vector<double> tables[17];
+    static bool ready[17] = {false};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[p]) {
+        const uint32_t m = 1u << p;
+        std::vector<double> t(m + 1, 0.0);
+        for (uint32_t V = 1; V <= m; V++) t[V] = (double)m * std::log((double)m / (double)V);
+        tables[p].swap(t);
+        ready[p] = true;
+    }
+    return tables[p];
+}
+
+namespace {
+
 __global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed) {
     const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    const uint64_t h = splitmix64(v ^ seed);
-    const uint32_t j = (uint32_t)(h >> (64 - p));
-    const uint64_t w = h << p;
-    const uint32_t rho = w ? (uint32_t)__clzll((long long)w) + 1u : (uint32_t)(65 - p);
-    const uint32_t s = j / (uint32_t)S, o = j % (uint32_t)S;
-    regs[((uint64_t)s * n + v) * (uint64_t)S + o] = (uint8_t)rho;
+    init_node(regs, n, p, S, seed, (uint32_t)v);
 }
 
-// Lane mapping of a slice gather: each lane moves CH bytes of a neighbour's
-// S-byte slice, G lanes cover one neighbour, P neighbours share one warp-wide
-// load instruction, U loads per lane are in flight.
-template <int S>
-struct GatherShape {
-    static constexpr int CH = (S > 512) ? S / 32 : 16;
-    static constexpr int G = S / CH;
-    static constexpr int P = 32 / G;
-    static constexpr int V4 = CH / 16;
-    static constexpr int U = (V4 == 1) ? (S <= 128 ? 8 : 4) : 2;  // narrow rows: more loads in flight
-};
-
-// Bytewise max through 16-bit lanes.  For a register word w = [b3 b2 b1 b0],
-// an unsigned max over u16x2 lanes of w keeps max(b3) and max(b1) in the lanes'
-// high bytes (the high byte decides the comparison; the low byte is whatever
-// came with the winner), and the same over w << 8 keeps max(b2) and max(b0).
-// Two DPX three-way maxima (__vimax3_u16x2) thus fold two gathered words into
-// the running maximum, instead of the multi-instruction __vmaxu4 emulation.
-// SplitAcc holds the two halves for one register word.
-struct SplitAcc {
-    uint32_t hi;  // u16x2 max over w: bytes 3 and 1 in the high byte of each lane
-    uint32_t lo;  // u16x2 max over w << 8: bytes 2 and 0 likewise
-};
-
-__device__ __forceinline__ void split_fold2(SplitAcc &a, uint32_t w0, uint32_t w1) {
-    a.hi = __vimax3_u16x2(a.hi, w0, w1);
-    a.lo = __vimax3_u16x2(a.lo, w0 << 8, w1 << 8);
-}
-
-__device__ __forceinline__ uint32_t split_bytes(const SplitAcc &a) {
-    return (a.hi & 0xFF00FF00u) | ((a.lo >> 8) & 0x00FF00FFu);
-}
-
-// Fold the S-byte rows row(ids[0..cnt)) into acc (4 * V4 words per lane, split
-// form).  Loads for U rows per lane are issued before any is folded.
-template <int S, class Row>
-__device__ __forceinline__ void gather_fold(const Row &row, const uint32_t *ids, int cnt, int g, int sub,
-                                            SplitAcc (&acc)[4 * GatherShape<S>::V4]) {
-    using Sh = GatherShape<S>;
-    static_assert(Sh::U % 2 == 0, "loads are folded in pairs");
-    for (int k0 = 0; k0 < cnt; k0 += Sh::P * Sh::U) {
-        uint4 x[Sh::U][Sh::V4];
-#pragma unroll
-        for (int u = 0; u < Sh::U; u++) {
-            const int k = k0 + u * Sh::P + g;
-            if (k < cnt) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(row(ids[k]) + sub * Sh::CH);
-#pragma unroll
-                for (int q = 0; q < Sh::V4; q++) x[u][q] = __ldg(src + q);
-            } else {
-#pragma unroll
-                for (int q = 0; q < Sh::V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < Sh::U; u += 2)
-#pragma unroll
-            for (int q = 0; q < Sh::V4; q++) {
-                split_fold2(acc[4 * q + 0], x[u][q].x, x[u + 1][q].x);
-                split_fold2(acc[4 * q + 1], x[u][q].y, x[u + 1][q].y);
-                split_fold2(acc[4 * q + 2], x[u][q].z, x[u + 1][q].z);
-                split_fold2(acc[4 * q + 3], x[u][q].w, x[u + 1][q].w);
-            }
-    }
-}
-
-// Row of node id in one register slice.
-template <int S>
-struct SliceRow {
-    const uint8_t *__restrict__ cur;
-    __device__ __forceinline__ const uint8_t *operator()(uint32_t id) const { return cur + (uint64_t)id * S; }
-};
-
-// Row of a range lookup (level k, index i): T_0 is the slice itself, T_1..T_K
-// follow each other in `tab`, N rows each.
-template <int S>
-struct TableRow {
-    const uint8_t *__restrict__ cur;
-    const uint8_t *__restrict__ tab;
-    uint32_t n;
-    __device__ __forceinline__ const uint8_t *operator()(uint32_t lk) const {
-        const uint32_t lvl = lk >> kLkIndexBits, i = lk & kLkIndexMask;
-        return lvl ? tab + ((uint64_t)(lvl - 1) * n + i) * S : cur + (uint64_t)i * S;
-    }
-};
-
-// Convert the split accumulators to register bytes and fold the P lane groups
-// of a warp together (every lane ends with the group maximum).
-template <int S>
-__device__ __forceinline__ void finish_groups(const SplitAcc (&acc)[4 * GatherShape<S>::V4],
-                                              uint4 (&out)[GatherShape<S>::V4]) {
-    using Sh = GatherShape<S>;
-#pragma unroll
-    for (int q = 0; q < Sh::V4; q++)
-        out[q] = make_uint4(split_bytes(acc[4 * q + 0]), split_bytes(acc[4 * q + 1]), split_bytes(acc[4 * q + 2]),
-                            split_bytes(acc[4 * q + 3]));
-#pragma unroll
-    for (int o = Sh::G; o < 32; o <<= 1)
-#pragma unroll
-        for (int q = 0; q < Sh::V4; q++) {
-            uint4 y;
-            y.x = __shfl_xor_sync(0xffffffffu, out[q].x, o);
-            y.y = __shfl_xor_sync(0xffffffffu, out[q].y, o);
-            y.z = __shfl_xor_sync(0xffffffffu, out[q].z, o);
-            y.w = __shfl_xor_sync(0xffffffffu, out[q].w, o);
-            out[q] = vmax4(out[q], y);
-        }
-}
-
-// Eq. hll-union for one register slice: next[v] = max(cur[v], max_{w in N(v)}
-// cur[w]) bytewise.  One warp per node: the warp decodes the node's LEB128
-// list 32 bytes at a time (decode_window), stages the decoded ids in shared
-// memory and gathers each neighbour's S-byte slice with 16-byte loads, folding
-// it in with __vmaxu4.  Sets flags[0] if any register of the slice changed.
+// Eq. hll-union for one register slice, one warp per node (union_node_edges).
 template <int S>
 __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restrict__ off,
                                                        const uint8_t *__restrict__ bytes,
                                                        const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
                                                        uint32_t n, uint32_t *__restrict__ flags) {
-    using Sh = GatherShape<S>;
     extern __shared__ uint32_t s_ids[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint32_t *ids = s_ids + wib * 32;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
-    const uint32_t v = (uint32_t)warp;
-    const int g = lane / Sh::G, sub = lane % Sh::G;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-
-    SplitAcc acc[4 * Sh::V4];
-#pragma unroll
-    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
-
-    uint64_t pos = off[v];
-    const uint64_t end = off[v + 1];
-    uint32_t base = 0;
-    while (pos < end) {
-        const WindowDecode<uint32_t> r = decode_window<uint32_t>(bytes, pos, end, base, lane);
-        const uint32_t T = r.term_mask;
-        if (T == 0) break;  // cannot happen on a validated graph; guarantees progress
-        if ((T >> lane) & 1u) ids[__popc(T & lt_mask)] = r.id;
-        __syncwarp();
-        gather_fold<S>(SliceRow<S>{cur}, ids, __popc(T), g, sub, acc);
-        __syncwarp();
-        base = r.next_base;
-        pos += (uint64_t)r.advance;
-    }
-    uint4 nb[Sh::V4];
-    finish_groups<S>(acc, nb);
-    bool changed = false;
-    if (g == 0) {
-        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
-        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * Sh::CH);
-#pragma unroll
-        for (int q = 0; q < Sh::V4; q++) {
-            const uint4 o4 = __ldg(own + q);
-            const uint4 res = vmax4(nb[q], o4);
-            dst[q] = res;
-            changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
-        }
-    }
-    if (__any_sync(0xffffffffu, changed) && lane == 0) {
-        if (*reinterpret_cast<volatile uint32_t *>(flags) == 0u) atomicOr(flags, 1u);
-    }
+    union_node_edges<S>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags);
 }
 
-// Run-aware Eq. hll-union for one register slice (runs.cu explains the
-// lookups): next[v] = max(cur[v], max over v's range lookups of T_k[i]), where
-// T_k[i] = max(cur[i .. i + 2^k)) has been built for this slice.  One warp per
-// node streams its lookups 32 at a time (evict-first: each is read once per
-// slice) and gathers the S-byte table rows exactly like the per-edge kernel.
+// Run-aware Eq. hll-union for one register slice, one warp per node
+// (union_node_runs), after the slice's sparse table has been built.
 template <int S>
 __global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__restrict__ lk_off,
                                                             const uint32_t *__restrict__ lk,
                                                             const uint8_t *__restrict__ cur,
                                                             const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt,
                                                             uint32_t n, uint32_t *__restrict__ flags) {
-    using Sh = GatherShape<S>;
     extern __shared__ uint32_t s_ids[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint32_t *ids = s_ids + wib * 32;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
-    const uint32_t v = (uint32_t)warp;
-    const int g = lane / Sh::G, sub = lane % Sh::G;
-    SplitAcc acc[4 * Sh::V4];
-#pragma unroll
-    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
-    const TableRow<S> row{cur, tab, n};
-    const uint64_t end = lk_off[v + 1];
-    for (uint64_t b = lk_off[v]; b < end; b += 32) {
-        const int cnt = (end - b < 32) ? (int)(end - b) : 32;
-        if (lane < cnt) ids[lane] = __ldcs(lk + b + lane);
-        __syncwarp();
-        gather_fold<S>(row, ids, cnt, g, sub, acc);
-        __syncwarp();
-    }
-    uint4 nb[Sh::V4];
-    finish_groups<S>(acc, nb);
-    bool changed = false;
-    if (g == 0) {
-        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
-        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * Sh::CH);
-#pragma unroll
-        for (int q = 0; q < Sh::V4; q++) {
-            const uint4 o4 = __ldg(own + q);
-            const uint4 res = vmax4(nb[q], o4);
-            dst[q] = res;
-            changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
-        }
-    }
-    if (__any_sync(0xffffffffu, changed) && lane == 0) {
-        if (*reinterpret_cast<volatile uint32_t *>(flags) == 0u) atomicOr(flags, 1u);
-    }
+    union_node_runs<S>(lk_off, lk, cur, tab, nxt, n, (uint32_t)warp, s_ids + wib * 32, lane, flags);
 }
+
 
 // One sparse-table level for a slice: out[i] = max(prev[i], prev[i + half]) for
 // i = 0 .. rows-1 (rows = N - 2*half + 1; later rows are never looked up).
@@ -327,31 +150,8 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
     if (lane == 0) out[warp] = x_acc;
 }
 
-// Correctly rounded (to nearest, ties to even) conversion of hi*2^64 + lo to
-// double: shift the value into 64 bits keeping a sticky bit for everything
-// shifted out, let the hardware round the 64-bit integer, scale back exactly.
-__device__ __forceinline__ double u128_to_double(uint64_t hi, uint64_t lo) {
-    if (hi == 0) return __ull2double_rn(lo);
-    const int k = 64 - __clzll((long long)hi);  // significant bits in hi, 1..64
-    uint64_t y, sticky;
-    if (k == 64) {
-        y = hi;
-        sticky = lo != 0;
-    } else {
-        y = (hi << (64 - k)) | (lo >> k);
-        sticky = (lo & ((1ull << k) - 1ull)) != 0;
-    }
-    const double scale = __longlong_as_double((long long)(1023 + k) << 52);  // 2^k
-    return __dmul_rn(__ull2double_rn(y | sticky), scale);
-}
-
-// HLL estimator (Sec. 2.3, Sec. 3.3) for every node, then Eq. sumD.
-// The harmonic sum Z = sum_j 2^-M[j] is formed exactly as the integer
-// Z * 2^(65-p) (zero registers V * 2^(65-p) plus 2^(65-p-M) for M >= 1) and
-// rounded once, so the result does not depend on summation order.
-// E = alpha_m m^2 / Z; c = lc[V] = m ln(m/V) if E <= 2.5m and V > 0, else E.
-// For t >= 1: sum_d += t * (c - c_prev), and flags[1] records
-// max_v(c - c_prev) > 0.5 (the paper's convergence test).
+// HLL estimate of every node, then Eq. sumD (estimate_node); flags[1]
+// records the paper's convergence test max_v(c_t - c_{t-1}) > 0.5.
 __global__ void hb_estimate_kernel(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, int t,
                                    double alpha_mm, const double *__restrict__ lc, const double *__restrict__ c_prev,
                                    double *__restrict__ c_cur, double *__restrict__ sum_d,
@@ -359,54 +159,7 @@ __global__ void hb_estimate_kernel(const uint8_t *__restrict__ regs, uint32_t n,
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= n) return;
-    const uint32_t v = (uint32_t)warp;
-    const uint32_t m = 1u << p;
-    const int K = 65 - p;
-    uint64_t lo = 0, hi = 0;
-    uint32_t zeros = 0;
-    for (uint32_t q = lane; q * 16u < m; q += 32) {
-        const uint32_t r0 = q * 16u;
-        const uint32_t s = r0 / (uint32_t)S, o = r0 % (uint32_t)S;
-        const uint4 x = *reinterpret_cast<const uint4 *>(regs + ((uint64_t)s * n + v) * (uint64_t)S + o);
-        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) {
-                const uint32_t M = (wv[i] >> (8 * b)) & 0xFFu;
-                if (M == 0) {
-                    zeros++;
-                } else {
-                    const uint64_t term = 1ull << (K - (int)M);
-                    lo += term;
-                    hi += (lo < term);
-                }
-            }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
-        const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
-        const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-        lo += olo;
-        hi += ohi + (lo < olo);
-    }
-    if (lane != 0) return;
-    // add V * 2^K (V <= 2^16, K <= 61: fits in 128 bits)
-    const uint64_t zlo = (uint64_t)zeros << K;
-    const uint64_t zhi = (uint64_t)zeros >> (64 - K);
-    lo += zlo;
-    hi += zhi + (lo < zlo);
-    const double inv_scale = __longlong_as_double((long long)(1023 - K) << 52);  // 2^-K
-    const double Z = __dmul_rn(u128_to_double(hi, lo), inv_scale);
-    const double E = __ddiv_rn(alpha_mm, Z);
-    const double c = (E <= 2.5 * (double)m && zeros > 0) ? lc[zeros] : E;
-    if (t > 0) {
-        const double diff = __dsub_rn(c, c_prev[v]);
-        sum_d[v] = __dadd_rn(sum_d[v], __dmul_rn((double)t, diff));
-        if (diff > 0.5 && *reinterpret_cast<volatile uint32_t *>(flags + 1) == 0u) atomicOr(flags + 1, 1u);
-    }
-    c_cur[v] = c;
+    estimate_node(regs, n, p, S, t, alpha_mm, lc, c_prev, c_cur, sum_d, flags + 1, (uint32_t)warp, lane);
 }
 
 // MD(v) = sum_d[v] / (N_v - 1) (Sec. 3.3), NaN when N_v <= 1; ball = c_t.
@@ -414,10 +167,9 @@ __global__ void hb_finalize_kernel(uint32_t n, const uint32_t *__restrict__ comp
                                    const double *__restrict__ c, double *__restrict__ md, double *__restrict__ ball) {
     const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    const double nv = comp ? (double)comp[v] : (double)n;
-    if (md) md[v] = (nv <= 1.0) ? __longlong_as_double(0x7FF8000000000000ll) : __ddiv_rn(sum_d[v], __dsub_rn(nv, 1.0));
-    if (ball) ball[v] = c[v];
+    finalize_node(n, comp, sum_d, c, md, ball, (uint32_t)v);
 }
+
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -497,28 +249,6 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     return VGA_OK;
 }
 
-static double hll_alpha(int p) {
-    const double m = (double)(1u << p);
-    if (p == 4) return 0.673;
-    if (p == 5) return 0.697;
-    if (p == 6) return 0.709;
-    return 0.7213 / (1.0 + 1.079 / m);
-}
-
-// Linear-counting table m ln(m / V), V = 1..m, computed once per p on the host
-// so that the device and any host consumer see the same doubles.
-static const std::vector<double> &lc_table(int p) {
-    static std::vector<double> tables[17];
-    static bool ready[17] = {false};
-    if (!ready[p]) {
-        const uint32_t m = 1u << p;
-        std::vector<double> t(m + 1, 0.0);
-        for (uint32_t V = 1; V <= m; V++) t[V] = (double)m * std::log((double)m / (double)V);
-        tables[p].swap(t);
-        ready[p] = true;
-    }
-    return tables[p];
-}
 
 static std::atomic<uint64_t> g_kernel_launches{0};
 
@@ -635,7 +365,7 @@ static int launch_estimate(const Plan &P, const uint8_t *regs, int t, const doub
                            double *c_cur, double *sum_d, uint32_t *flags, cudaStream_t stream) {
     const int warps = 8;
     const unsigned blocks = (unsigned)((P.n + warps - 1) / warps);
-    const double alpha_mm = hll_alpha(P.p) * (double)P.m * (double)P.m;
+    const double alpha_mm = hll_alpha_host(P.p) * (double)P.m * (double)P.m;
     hb_estimate_kernel<<<blocks, warps * 32, 0, stream>>>(regs, (uint32_t)P.n, P.p, P.S, t, alpha_mm, lc, c_prev,
                                                           c_cur, sum_d, flags);
     count_launch();

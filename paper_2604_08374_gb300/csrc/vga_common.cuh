@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "vga_hyperball.h"
 
@@ -44,6 +45,11 @@ void clear_error();
 
 // Counts one library kernel launch (vga_profile.kernel_launches).
 void count_launch();
+
+// HLL alpha_m and the linear-counting table m ln(m/V), V = 0..m (host, cached
+// per p), shared by the single-graph and batched paths.
+double hll_alpha_host(int p);
+const std::vector<double> &lc_table(int p);
 
 #define VGA_CHECK_CUDA(call)                                                                   \
     do {                                                                                       \
