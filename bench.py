@@ -74,6 +74,11 @@ def parse_args():
     ap.add_argument("--warps", type=int, default=0, help="force union warps per CTA (0 = automatic)")
     ap.add_argument("--union-mode", type=int, default=0,
                     help="0 automatic, 1 one gather per neighbour, 2 per run of consecutive ids")
+    ap.add_argument("--mode", choices=["metric", "batch", "serve"], default="metric",
+                    help="metric: the headline analysis; batch: 256-graph batched workload; serve: Poisson requests")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=150, help="requests per offered load")
+    ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--backend", default="nccl")
     return ap.parse_args()
 
@@ -458,12 +463,182 @@ def run_ours(args, dist: Dist):
     g.free()
 
 
+# ----------------------------------------------------------------------------
+# batched and served workloads (our arm only)
+# ----------------------------------------------------------------------------
+
+def _percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, np.float64), q)) if len(xs) else None
+
+
+def run_batch_mode(args, dist):
+    """256 graphs of 1k-30k cells, p in {8,10,12}, d in {3, unlimited}: one
+    hyperball_run_batch call (CUDA-graph pass loop) against the same analyses
+    run one at a time with hyperball_run_dev."""
+    import torch
+
+    from paper_2604_08374_gb300 import build as vga_build
+    vga_build.build()
+    import paper_2604_08374_gb300 as vga
+    torch.cuda.set_device(dist.local_rank)
+    specs = workloads.batch(args.batch_count, seed=0)
+    t0 = time.perf_counter()
+    graphs = [vga.vga_visibility_build(sp["grid"]) for sp in specs]
+    build_s = time.perf_counter() - t0
+    jobs = [dict(graph=g, p=sp["p"], d=sp["d"], seed=k, conv_mode=0,
+                 mean_depth=torch.empty(max(g.n_nodes, 1), dtype=torch.float64, device="cuda"),
+                 ball=torch.empty(max(g.n_nodes, 1), dtype=torch.float64, device="cuda"))
+            for k, (g, sp) in enumerate(zip(graphs, specs))]
+    nodes = [g.n_nodes for g in graphs]
+    edges = [g.n_edges for g in graphs]
+    # one at a time (each with a reused workspace); first round warms caches and lookup lists
+    ws_single = torch.empty(max(vga.hyperball_workspace_bytes(j["graph"], j["p"]) for j in jobs), dtype=torch.uint8,
+                            device="cuda")
+    single_md = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        passes_single = 0
+        for j in jobs:
+            md = torch.empty_like(j["mean_depth"])
+            passes_single += vga.hyperball_run_dev(j["graph"], j["p"], j["d"], j["seed"], md, None, workspace=ws_single)
+            if rep:
+                single_md.append(md)
+        torch.cuda.synchronize()
+        single_s = time.perf_counter() - t0
+    # batched: warm-up, then timed, in CUDA-graph mode and host-driven mode
+    ws = torch.empty(vga.hyperball_batch_workspace_bytes(jobs), dtype=torch.uint8, device="cuda")
+    vga.hyperball_run_batch(jobs, workspace=ws, use_graph=True)
+    timings = {}
+    for mode in (True, False):
+        reps = []
+        for _ in range(max(1, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = vga.hyperball_run_batch(jobs, workspace=ws, use_graph=mode)
+            torch.cuda.synchronize()
+            reps.append(time.perf_counter() - t0)
+        timings["graph" if mode else "host"] = min(reps)
+    identical = all(torch.equal(torch.nan_to_num(j["mean_depth"][: j["graph"].n_nodes], nan=-1.0),
+                                torch.nan_to_num(m[: j["graph"].n_nodes], nan=-1.0))
+                    for j, m in zip(jobs, single_md))
+    n = len(jobs)
+    line = {"metric": "batched analyses/s (256 graphs of 1k-30k cells, p in {8,10,12}, d in {3, unlimited})",
+            "value": n / timings["graph"], "unit": "analyses/s", "n_gpus": dist.world, "higher_is_better": True,
+            "data": "synthetic", "dtype": "u8",
+            "config": {"workload": f"{n} medium-style grids, free cells log-uniform 1k-30k, per-graph seeds",
+                       "nodes_total": int(sum(nodes)), "edges_total": int(sum(edges)),
+                       "graph_build_seconds": build_s},
+            "batched_seconds": timings["graph"], "batched_host_loop_seconds": timings["host"],
+            "batched_host_loop_analyses_per_s": n / timings["host"],
+            "one_at_a_time_seconds": single_s, "one_at_a_time_analyses_per_s": n / single_s,
+            "speedup_vs_one_at_a_time": single_s / timings["graph"],
+            "passes_total": int(sum(its)), "results_identical_to_one_at_a_time": bool(identical),
+            "timing": "wall clock around each call with device synchronisation (best of runs)"}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.free()
+
+
+def run_serve_mode(args, dist):
+    """Poisson (graph, p, d) requests over a resident pool of graphs at 0.5x,
+    0.9x and 1.5x the measured one-at-a-time capacity, through vga_server
+    (150 GiB budget); the one-at-a-time reference is a FIFO single server fed
+    the same arrivals with each request's measured solo service time."""
+    import threading
+
+    import torch
+
+    from paper_2604_08374_gb300 import build as vga_build
+    vga_build.build()
+    import paper_2604_08374_gb300 as vga
+    torch.cuda.set_device(dist.local_rank)
+    t0 = time.perf_counter()
+    pool = [vga.vga_visibility_build(g) for g in workloads.serve_pool(args.serve_pool, seed=0)]
+    build_s = time.perf_counter() - t0
+    R = args.serve_requests
+    base = workloads.serve_requests(R, len(pool), rate=1.0, seed=1)
+    # solo service time of every request (first, warm every graph's lookup list)
+    for g in pool:
+        vga.hyperball_run(g, 8, 1, 0)
+    service = []
+    for (_, gi, p, d) in base:
+        g = pool[gi]
+        md = torch.empty(max(g.n_nodes, 1), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        vga.hyperball_run_dev(g, p, d, 0, md, None)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t1)
+    capacity = R / sum(service)
+    loads = []
+    for f in (0.5, 0.9, 1.5):
+        rate = f * capacity
+        arrivals = [a / rate for (a, _, _, _) in base]
+        # one at a time: FIFO single server with the measured service times
+        free_at, lat_single = 0.0, []
+        for a, s_k in zip(arrivals, service):
+            start = max(a, free_at)
+            free_at = start + s_k
+            lat_single.append(free_at - a)
+        single_makespan = free_at - arrivals[0]
+        # served
+        with vga.Server(hbm_budget_bytes=150 << 30) as srv:
+            ids = [None] * R
+            submit_t = [0.0] * R
+            t_start = time.perf_counter()
+
+            def submitter():
+                for k, (a, (_, gi, p, d)) in enumerate(zip(arrivals, base)):
+                    delay = t_start + a - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    submit_t[k] = time.perf_counter()
+                    ids[k] = srv.submit(pool[gi], p, d, k)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat, done_t = [], []
+            for k in range(R):
+                while ids[k] is None:
+                    time.sleep(0.0005)
+                out = srv.wait(ids[k], timeout_s=600)
+                lat.append(out["latency_s"])
+                done_t.append(submit_t[k] + out["latency_s"])
+            th.join()
+            st = srv.stats()
+        served_makespan = max(done_t) - submit_t[0]
+        loads.append({"offered_load": f, "rate_per_s": rate,
+                      "served": {"analyses_per_s": R / served_makespan, "p50_s": _percentile(lat, 50),
+                                 "p99_s": _percentile(lat, 99), "batched_peak": st["batched_peak"],
+                                 "budget_peak_bytes": st["budget_peak"]},
+                      "one_at_a_time": {"analyses_per_s": R / single_makespan, "p50_s": _percentile(lat_single, 50),
+                                        "p99_s": _percentile(lat_single, 99)}})
+    line = {"metric": "served analyses/s and p50/p99 latency (Poisson requests, pool of 64 graphs 1k-236k cells)",
+            "value": loads[-1]["served"]["analyses_per_s"], "unit": "analyses/s", "n_gpus": dist.world,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u8",
+            "config": {"workload": f"pool of {len(pool)} medium-style grids, free cells log-uniform 1k-236k; "
+                                   f"{R} requests per load, p in {{8,10,12}}, d in {{3,5,unlimited}}",
+                       "pool_nodes": [g.n_nodes for g in pool], "pool_edges_total": int(sum(g.n_edges for g in pool)),
+                       "hbm_budget_bytes": 150 << 30, "graph_build_seconds": build_s},
+            "one_at_a_time_capacity_per_s": capacity, "loads": loads}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    for g in pool:
+        g.free()
+
+
 def main():
     args = parse_args()
     dist = Dist(args.backend)
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.mode == "batch":
+            run_batch_mode(args, dist)
+        elif args.mode == "serve":
+            run_serve_mode(args, dist)
         else:
             run_ours(args, dist)
     finally:

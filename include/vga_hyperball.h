@@ -271,7 +271,7 @@ typedef struct vga_job {
     int d;                   /* in: depth limit (<= 0: unlimited)                      */
     uint64_t seed;           /* in: hash seed                                          */
     int conv_mode;           /* in: 0 or 1, as in hyperball_run_dev                    */
-    int reserved;
+    int union_mode;          /* in: 0 auto (= 2), 1 per neighbour, 2 per run (vga_tuning) */
     double *mean_depth_dev;  /* out: device, N doubles, or NULL                        */
     double *ball_size_dev;   /* out: device, N doubles, or NULL                        */
     int iterations;          /* out: union passes run                                  */
@@ -287,8 +287,10 @@ int hyperball_batch_workspace_bytes(const vga_job *jobs, int n_jobs, uint64_t *b
  * is one launch for the whole batch: a persistent union kernel whose CTAs take
  * (job, register slice, block of nodes) items from an atomic queue, a batched
  * estimate + Eq. sumD launch, a per-job step (stop rules), and the mean-depth
- * epilogue of the jobs that stopped.  Per job the results are bit-identical
- * to hyperball_run_dev with union_mode 1 (one gather per neighbour).
+ * epilogue of the jobs that stopped.  In union mode 2 each (job, slice) is
+ * queued as sparse-table items followed by union items, which start once
+ * their slice's tables are complete (bounded wait; VGA_ETIMEOUT if it ever
+ * gave up).  Per job the results are bit-identical to hyperball_run_dev.
  *   jobs, n_jobs     the batch (jobs with N = 0 are skipped, iterations 0).
  *   workspace_dev    device, >= hyperball_batch_workspace_bytes, 256-byte
  *                    aligned, or NULL to let the library allocate.

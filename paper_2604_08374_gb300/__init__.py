@@ -36,7 +36,7 @@ class VgaTuning(C.Structure):
 
 class VgaJob(C.Structure):
     _fields_ = [("graph", C.c_void_p), ("p", C.c_int), ("d", C.c_int), ("seed", C.c_uint64), ("conv_mode", C.c_int),
-                ("reserved", C.c_int), ("mean_depth_dev", C.c_void_p), ("ball_size_dev", C.c_void_p),
+                ("union_mode", C.c_int), ("mean_depth_dev", C.c_void_p), ("ball_size_dev", C.c_void_p),
                 ("iterations", C.c_int), ("status", C.c_int)]
 
 
@@ -338,6 +338,7 @@ def _job_array(jobs):
         arr[k].graph = j["graph"].handle.value
         arr[k].p, arr[k].d, arr[k].seed = j["p"], j.get("d", 0), j.get("seed", 0)
         arr[k].conv_mode = j.get("conv_mode", 0)
+        arr[k].union_mode = j.get("union_mode", 0)
         arr[k].mean_depth_dev = _ptr(j.get("mean_depth"))
         arr[k].ball_size_dev = _ptr(j.get("ball"))
     return arr

@@ -68,21 +68,35 @@ __global__ void batch_estimate_kernel(JobDev *jobs, const uint64_t *__restrict__
     }
 }
 
-template <int S>
-__device__ __forceinline__ void batch_union_item(JobDev &J, uint32_t s, uint32_t v, uint32_t *ids, int lane) {
-    const int t = J.t + 1;
-    const uint64_t slice = (uint64_t)s * J.n * S;
-    union_node_edges<S>(J.off, J.bytes, J.regs[(t - 1) & 1] + slice, J.regs[t & 1] + slice, v, ids, lane,
-                        &J.changed);
+// Bounded wait (about a second) for the table items of a slice, published by
+// their CTAs (every writer fences before the counter increment).
+__device__ __forceinline__ bool wait_tables(const uint32_t *done, uint32_t target) {
+    for (uint32_t spin = 0; spin < (1u << 22); spin++) {
+        if (*reinterpret_cast<const volatile uint32_t *>(done) >= target) {
+            __threadfence();
+            return true;
+        }
+        __nanosleep(256);
+    }
+    return false;
 }
 
-// Persistent union over all running jobs' (slice, node-block) items.
+// Persistent union over the running jobs of one group (same union variant,
+// same slice width S).  CTAs claim items from the group's queue.  Per job and
+// slice the queue holds, in run-aware jobs (RUNS), first the sparse-table items
+// and then the union items (one node per warp); a union item starts once its
+// slice's table items are done.  Table items never wait, and every table item
+// of a slice is claimed before any of its union items, so each wait ends.
+template <int S, bool RUNS>
 __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *jobs,
+                                                                        const uint32_t *__restrict__ gjobs,
                                                                         const uint64_t *__restrict__ item_start,
                                                                         int n_jobs, uint64_t total_items,
-                                                                        unsigned long long *counter) {
+                                                                        unsigned long long *counter, int *error) {
     __shared__ uint32_t s_ids[kEngineWarps][32];
+    __shared__ __align__(16) uint8_t s_tab[RUNS ? TableShape<S>::R * S : 16];
     __shared__ unsigned long long s_item;
+    __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     for (;;) {
@@ -91,29 +105,46 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         const uint64_t item = s_item;
         __syncthreads();
         if (item >= total_items) break;
-        const int j = find_job(item_start, n_jobs, item);
-        JobDev &J = jobs[j];
+        const int k = find_job(item_start, n_jobs, item);
+        JobDev &J = jobs[gjobs[k]];
         if (J.state != 0) continue;
-        const uint64_t r = item - item_start[j];
-        const uint32_t s = (uint32_t)(r / (uint64_t)J.blocks);
-        const uint32_t v = (uint32_t)(r % (uint64_t)J.blocks) * kEngineWarps + wib;
-        if (v >= J.n) continue;
-        uint32_t *ids = s_ids[wib];
-        switch (J.S) {
-            case 16: batch_union_item<16>(J, s, v, ids, lane); break;
-            case 32: batch_union_item<32>(J, s, v, ids, lane); break;
-            case 64: batch_union_item<64>(J, s, v, ids, lane); break;
-            case 128: batch_union_item<128>(J, s, v, ids, lane); break;
-            case 256: batch_union_item<256>(J, s, v, ids, lane); break;
-            case 512: batch_union_item<512>(J, s, v, ids, lane); break;
-            default: batch_union_item<1024>(J, s, v, ids, lane); break;
+        const uint64_t per_slice = (uint64_t)J.blocks + (RUNS ? (uint64_t)J.tblocks : 0);
+        const uint64_t r = item - item_start[k];
+        const uint32_t s = (uint32_t)(r / per_slice);
+        uint64_t q = r % per_slice;
+        const int t = J.t + 1;
+        const uint64_t slice = (uint64_t)s * J.n * S;
+        const uint8_t *cur = J.regs[(t - 1) & 1] + slice;
+        uint8_t *tab = RUNS ? J.tab + (uint64_t)s * kRunLevels * J.n * S : nullptr;
+        if (RUNS) {
+            if (q < (uint64_t)J.tblocks) {
+                table_item<S>(cur, tab, J.n, (uint32_t)q * (uint32_t)TableShape<S>::B, s_tab);
+                __threadfence();  // every writer publishes its table rows device-wide
+                __syncthreads();
+                if (threadIdx.x == 0) atomicAdd(J.tab_done + s, 1u);
+                continue;
+            }
+            q -= J.tblocks;
+            if (threadIdx.x == 0) {
+                s_ok = wait_tables(J.tab_done + s, (uint32_t)t * (uint32_t)J.tblocks);
+                if (!s_ok) atomicExch(error, 1);
+            }
+            __syncthreads();
+            if (!s_ok) continue;
         }
+        const uint32_t v = (uint32_t)q * kEngineWarps + wib;
+        if (v >= J.n) continue;
+        uint8_t *nxt = J.regs[t & 1] + slice;
+        if (RUNS)
+            union_node_runs<S>(J.lk_off, J.lk, cur, tab, nxt, J.n, v, s_ids[wib], lane, &J.changed);
+        else
+            union_node_edges<S>(J.off, J.bytes, cur, nxt, v, s_ids[wib], lane, &J.changed);
     }
 }
 
 // One thread per job: close the pass, apply the stop rule, reset the flags and
 // the union's item counter; report whether any job still runs.
-__global__ void batch_step_kernel(JobDev *jobs, int n_jobs, unsigned long long *counter, int *any_running,
+__global__ void batch_step_kernel(JobDev *jobs, int n_jobs, unsigned long long *counters, int *any_running,
                                   cudaGraphConditionalHandle cond, int use_cond) {
     int running = 0;
     for (int j = threadIdx.x; j < n_jobs; j += blockDim.x) {
@@ -131,8 +162,8 @@ __global__ void batch_step_kernel(JobDev *jobs, int n_jobs, unsigned long long *
         running |= (J.state == 0);
     }
     running = __syncthreads_or(running);
+    if (threadIdx.x < kGroups) counters[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) {
-        *counter = 0ull;
         *any_running = running;
         if (use_cond) cudaGraphSetConditional(cond, running ? 1u : 0u);
     }
@@ -161,20 +192,28 @@ uint64_t l2_budget_bytes(int dev) {
     return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
 }
 
-JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget) {
+JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode) {
     JobLayout L;
+    L.mode = (mode == 1 || (uint64_t)n > kRunMaxNodes) ? 1 : 2;
     const uint32_t m = 1u << p;
+    const uint64_t rows = L.mode == 2 ? (uint64_t)kRunLevels + 1 : 1;
     int S = (int)std::min<uint32_t>(m, (uint32_t)(slice_cap > 0 ? slice_cap : 1024));
-    while (S > 16 && (uint64_t)S * n > budget) S >>= 1;
+    while (S > 16 && (uint64_t)S * n * rows > budget) S >>= 1;
     L.S = S;
     L.slices = (int)(m / (uint32_t)S);
     L.blocks = (int)((n + kEngineWarps - 1) / kEngineWarps);
+    const int B = S >= 1024 ? 16 : 32;  // rows of a table item (TableShape)
+    L.tblocks = L.mode == 2 ? (int)((n + B - 1) / B) : 0;
     uint64_t o = 0;
     o = align256(o + (uint64_t)n * m);
     o = align256(o + (uint64_t)n * m);
     o = align256(o + 8ull * n);
     o = align256(o + 8ull * n);
     o = align256(o + 8ull * n);
+    if (L.mode == 2) {
+        o = align256(o + (uint64_t)kRunLevels * n * m);
+        o = align256(o + 4ull * L.slices);
+    }
     L.bytes = o;
     return L;
 }
@@ -188,7 +227,13 @@ JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, co
     J.regs[1] = ws + o; o = align256(o + n * m);
     J.c[0] = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
     J.c[1] = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
-    J.sum_d = reinterpret_cast<double *>(ws + o);
+    J.sum_d = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
+    if (L.mode == 2) {
+        J.tab = ws + o; o = align256(o + (uint64_t)kRunLevels * n * m);
+        J.tab_done = reinterpret_cast<uint32_t *>(ws + o);
+        J.lk_off = g->d_lk_off;
+        J.lk = g->d_lk;
+    }
     J.off = g->d_offsets;
     J.bytes = g->d_bytes;
     J.comp = g->d_comp;
@@ -204,6 +249,8 @@ JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, co
     J.d = d;
     J.conv = conv;
     J.blocks = L.blocks;
+    J.mode = L.mode;
+    J.tblocks = L.tblocks;
     return J;
 }
 
@@ -227,49 +274,97 @@ int upload_lc_tables(uint8_t *dst, const bool *used, cudaStream_t stream) {
 
 
 uint64_t engine_arrays_bytes(int cap) {
-    return align256(sizeof(JobDev) * (uint64_t)std::max(cap, 1)) + 2 * align256(8ull * (cap + 1)) + 256;
+    const uint64_t c = (uint64_t)std::max(cap, 1);
+    return align256(sizeof(JobDev) * c) + align256(8 * (c + 1)) + align256(4 * c) + align256(8 * (c + kGroups)) +
+           align256(8 * kGroups) + 256;
 }
 
 EngineArrays engine_arrays_at(uint8_t *base, int cap) {
     EngineArrays A;
+    const uint64_t c = (uint64_t)std::max(cap, 1);
     uint64_t o = 0;
-    A.jobs = reinterpret_cast<JobDev *>(base + o); o = align256(o + sizeof(JobDev) * (uint64_t)std::max(cap, 1));
-    A.node_start = reinterpret_cast<uint64_t *>(base + o); o = align256(o + 8ull * (cap + 1));
-    A.item_start = reinterpret_cast<uint64_t *>(base + o); o = align256(o + 8ull * (cap + 1));
-    A.counter = reinterpret_cast<unsigned long long *>(base + o);
-    A.any_running = reinterpret_cast<int *>(base + o + 8);
+    A.jobs = reinterpret_cast<JobDev *>(base + o); o = align256(o + sizeof(JobDev) * c);
+    A.node_start = reinterpret_cast<uint64_t *>(base + o); o = align256(o + 8 * (c + 1));
+    A.gjobs = reinterpret_cast<uint32_t *>(base + o); o = align256(o + 4 * c);
+    A.item_start = reinterpret_cast<uint64_t *>(base + o); o = align256(o + 8 * (c + kGroups));
+    A.counters = reinterpret_cast<unsigned long long *>(base + o); o = align256(o + 8 * kGroups);
+    A.any_running = reinterpret_cast<int *>(base + o);
+    A.error = reinterpret_cast<int *>(base + o + 4);
     A.cap = cap;
     return A;
 }
 
+int group_index(int mode, int S) { return (mode == 2 ? 7 : 0) + (31 - __builtin_clz((unsigned)S)) - 4; }
 
+template <int S, bool RUNS>
+int union_grid(int sms) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_union_kernel<S, RUNS>, kEngineWarps * 32, 0);
+    return std::max(1, sms * std::max(1, per_sm));
+}
 
-// Upload descriptors and prefix arrays of `jobs` (host copies) into A; the
-// host vectors are copied synchronously before the function returns.
+int union_grid_for(int mode, int S, int sms) {
+#define VGA_G(SS)                                                                               \
+    case SS:                                                                                    \
+        return mode == 2 ? union_grid<SS, true>(sms) : union_grid<SS, false>(sms);
+    switch (S) {
+        VGA_G(16) VGA_G(32) VGA_G(64) VGA_G(128) VGA_G(256) VGA_G(512) VGA_G(1024)
+    }
+#undef VGA_G
+    return sms;
+}
+
+// Upload descriptors, the node prefix and the per-group item queues of `jobs`
+// (host copies) into A; the host vectors are copied synchronously before the
+// function returns.
 int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, EngineSet *E, cudaStream_t stream) {
     const int nj = (int)jobs.size();
     if (nj > A.cap) {
         set_error("internal: %d jobs exceed the engine capacity %d", nj, A.cap);
         return VGA_EINVAL;
     }
-    std::vector<uint64_t> ns(nj + 1, 0), is(nj + 1, 0);
-    for (int k = 0; k < nj; k++) {
-        ns[k + 1] = ns[k] + jobs[k].n;
-        is[k + 1] = is[k] + (uint64_t)jobs[k].slices * (uint64_t)jobs[k].blocks;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<uint64_t> ns(nj + 1, 0);
+    for (int k = 0; k < nj; k++) ns[k + 1] = ns[k] + jobs[k].n;
+    std::vector<std::vector<uint32_t>> members(kGroups);
+    for (int k = 0; k < nj; k++) members[group_index(jobs[k].mode, jobs[k].S)].push_back((uint32_t)k);
+    std::vector<uint32_t> gj;
+    std::vector<uint64_t> is;
+    E->groups.clear();
+    for (int g = 0; g < kGroups; g++) {
+        if (members[g].empty()) continue;
+        EngineGroup G;
+        G.index = g;
+        G.mode = jobs[members[g][0]].mode;
+        G.S = jobs[members[g][0]].S;
+        G.n = (int)members[g].size();
+        G.gjob_off = gj.size();
+        G.item_off = is.size();
+        uint64_t items = 0;
+        for (uint32_t k : members[g]) {
+            gj.push_back(k);
+            is.push_back(items);
+            const JobDev &J = jobs[k];
+            items += (uint64_t)J.slices * ((uint64_t)J.blocks + (J.mode == 2 ? (uint64_t)J.tblocks : 0));
+        }
+        is.push_back(items);
+        G.total_items = items;
+        G.grid = (unsigned)union_grid_for(G.mode, G.S, sms);
+        E->groups.push_back(G);
     }
     if (nj) VGA_CHECK_CUDA(cudaMemcpyAsync(A.jobs, jobs.data(), sizeof(JobDev) * nj, cudaMemcpyHostToDevice, stream));
     VGA_CHECK_CUDA(cudaMemcpyAsync(A.node_start, ns.data(), 8 * (nj + 1), cudaMemcpyHostToDevice, stream));
-    VGA_CHECK_CUDA(cudaMemcpyAsync(A.item_start, is.data(), 8 * (nj + 1), cudaMemcpyHostToDevice, stream));
-    VGA_CHECK_CUDA(cudaMemsetAsync(A.counter, 0, 16, stream));
-    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));  // ns / is are about to go out of scope
+    if (!gj.empty()) {
+        VGA_CHECK_CUDA(cudaMemcpyAsync(A.gjobs, gj.data(), 4 * gj.size(), cudaMemcpyHostToDevice, stream));
+        VGA_CHECK_CUDA(cudaMemcpyAsync(A.item_start, is.data(), 8 * is.size(), cudaMemcpyHostToDevice, stream));
+    }
+    VGA_CHECK_CUDA(cudaMemsetAsync(A.counters, 0, 8 * kGroups, stream));
+    VGA_CHECK_CUDA(cudaMemsetAsync(A.any_running, 0, 8, stream));  // running flag and error
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));                  // the host vectors go out of scope
     E->n_jobs = nj;
     E->total_nodes = ns[nj];
-    E->total_items = is[nj];
-    int dev = 0, sms = 1, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_union_kernel, kEngineWarps * 32, 0);
-    E->grid_union = (unsigned)std::max(1, sms * std::max(1, per_sm));
     E->grid_nodes = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((E->total_nodes + 255) / 256, (uint64_t)sms * 32));
     E->grid_warps = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((E->total_nodes + 7) / 8, (uint64_t)sms * 64));
     return VGA_OK;
@@ -281,6 +376,7 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
     for (const JobDev &J : jobs) {
         VGA_CHECK_CUDA(cudaMemsetAsync(J.regs[0], 0, (uint64_t)J.n << J.p, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(J.sum_d, 0, 8ull * J.n, stream));
+        if (J.mode == 2) VGA_CHECK_CUDA(cudaMemsetAsync(J.tab_done, 0, 4ull * J.slices, stream));
     }
     if (!E.n_jobs) return VGA_OK;
     batch_init_kernel<<<E.grid_nodes, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes);
@@ -291,14 +387,30 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
     return VGA_OK;
 }
 
+template <int S, bool RUNS>
+void launch_group(const EngineArrays &A, const EngineGroup &G, cudaStream_t stream) {
+    batch_union_kernel<S, RUNS><<<G.grid, kEngineWarps * 32, 0, stream>>>(A.jobs, A.gjobs + G.gjob_off,
+                                                                         A.item_start + G.item_off, G.n,
+                                                                         G.total_items, A.counters + G.index, A.error);
+}
+
 int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, cudaGraphConditionalHandle cond,
                 int use_cond) {
-    batch_union_kernel<<<E.grid_union, kEngineWarps * 32, 0, stream>>>(A.jobs, A.item_start, E.n_jobs,
-                                                                       E.total_items, A.counter);
-    count_launch();
+    for (const EngineGroup &G : E.groups) {
+#define VGA_G(SS)                                                                         \
+    case SS:                                                                              \
+        if (G.mode == 2) launch_group<SS, true>(A, G, stream);                            \
+        else launch_group<SS, false>(A, G, stream);                                       \
+        break;
+        switch (G.S) {
+            VGA_G(16) VGA_G(32) VGA_G(64) VGA_G(128) VGA_G(256) VGA_G(512) VGA_G(1024)
+        }
+#undef VGA_G
+        count_launch();
+    }
     batch_estimate_kernel<<<E.grid_warps, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes, 0);
     count_launch();
-    batch_step_kernel<<<1, 256, 0, stream>>>(A.jobs, E.n_jobs, A.counter, A.any_running, cond, use_cond);
+    batch_step_kernel<<<1, 256, 0, stream>>>(A.jobs, E.n_jobs, A.counters, A.any_running, cond, use_cond);
     count_launch();
     batch_finalize_kernel<<<E.grid_nodes, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes);
     count_launch();
@@ -388,8 +500,12 @@ int plan_batch(const vga_job *jobs, int n_jobs, int slice_cap, BatchPlan *B) {
                       jb.graph->device, dev);
             return VGA_EINVAL;
         }
+        if (jb.union_mode < 0 || jb.union_mode > 2) {
+            set_error("hyperball batch: job %d has union_mode %d (0, 1 or 2)", i, jb.union_mode);
+            return VGA_EINVAL;
+        }
         if (jb.graph->n == 0) continue;
-        const JobLayout L = job_layout(jb.graph->n, jb.p, slice_cap, budget);
+        const JobLayout L = job_layout(jb.graph->n, jb.p, slice_cap, budget, jb.union_mode);
         B->idx.push_back(i);
         B->lay.push_back(L);
         B->job_off.push_back(o);
@@ -423,6 +539,8 @@ int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaSt
         jobs[i].status = VGA_OK;
     }
     if (B.idx.empty()) return VGA_OK;
+    for (size_t k = 0; k < B.idx.size(); k++)
+        if (B.lay[k].mode == 2) VGA_TRY(ensure_run_lookups(jobs[B.idx[k]].graph, stream));
     VGA_TRY(upload_lc_tables(ws + B.off_lc, B.lc_used, stream));
     std::vector<JobDev> host(B.idx.size());
     for (size_t k = 0; k < B.idx.size(); k++) {
@@ -446,7 +564,13 @@ int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaSt
         }
     }
     VGA_CHECK_CUDA(cudaMemcpyAsync(host.data(), A.jobs, sizeof(JobDev) * host.size(), cudaMemcpyDeviceToHost, stream));
+    int err = 0;
+    VGA_CHECK_CUDA(cudaMemcpyAsync(&err, A.error, sizeof(int), cudaMemcpyDeviceToHost, stream));
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    if (err) {
+        set_error("hyperball batch: a union item gave up waiting for its sparse tables");
+        return VGA_ETIMEOUT;
+    }
     for (size_t k = 0; k < host.size(); k++) jobs[B.idx[k]].iterations = host[k].t;
     return VGA_OK;
 }

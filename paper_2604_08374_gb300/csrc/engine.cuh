@@ -9,12 +9,17 @@
 namespace vga {
 
 constexpr int kEngineWarps = 8;
+constexpr int kGroups = 14;  // union kernels: (per neighbour | per run) x slice width 16..1024
 
 // One analysis as the batched kernels see it (device memory).
 struct JobDev {
     const uint64_t *off;
     const uint8_t *bytes;
     const uint32_t *comp;
+    const uint64_t *lk_off;  // run-aware union: the graph's range lookups
+    const uint32_t *lk;
+    uint8_t *tab;            // sparse tables, slice s at tab + s * kRunLevels * N * S
+    uint32_t *tab_done;      // per slice: table items finished, over all passes
     uint8_t *regs[2];   // slice-major [m/S][N][S]; pass t reads regs[(t-1)&1], writes regs[t&1]
     double *c[2];       // c_t lives in c[t&1]
     double *sum_d;
@@ -24,36 +29,51 @@ struct JobDev {
     uint64_t seed;
     uint32_t n;
     int p, S, slices, d, conv, blocks;
+    int mode;               // 1 one gather per neighbour, 2 per run (sparse tables)
+    int tblocks;            // table items per slice (mode 2)
     uint32_t changed, inc;  // flags of the pass in progress
     int t;                  // passes completed
     int state;              // 0 running, 1 stopped at this step (finalize), 2 done
 };
 
-// Per-job slice width and workspace size (regs0, regs1, c0, c1, sum_d).
+// Per-job union variant, slice width and workspace size (regs0, regs1, c0,
+// c1, sum_d, and in mode 2 the sparse tables of every slice and their counters).
 struct JobLayout {
-    int S = 0, slices = 0, blocks = 0;
+    int mode = 2, S = 0, slices = 0, blocks = 0, tblocks = 0;
     uint64_t bytes = 0;
 };
 
 // Device arrays the batched kernels read, sized for `cap` jobs.
 struct EngineArrays {
     JobDev *jobs = nullptr;
-    uint64_t *node_start = nullptr, *item_start = nullptr;
-    unsigned long long *counter = nullptr;
+    uint64_t *node_start = nullptr;         // cap + 1: prefix of nodes over all jobs
+    uint32_t *gjobs = nullptr;              // cap: job indices ordered by union group
+    uint64_t *item_start = nullptr;         // cap + kGroups: per group, prefix of items over its jobs
+    unsigned long long *counters = nullptr; // kGroups: the groups' item queues
     int *any_running = nullptr;
+    int *error = nullptr;                   // set when a bounded wait gave up
     int cap = 0;
+};
+
+// One union kernel launch: the jobs sharing a union variant and slice width.
+struct EngineGroup {
+    int mode = 1, S = 0, n = 0;
+    uint64_t gjob_off = 0, item_off = 0, total_items = 0;
+    unsigned grid = 1;
+    int index = 0;
 };
 
 // Sizes and launch shapes of the job set currently uploaded.
 struct EngineSet {
     int n_jobs = 0;
-    uint64_t total_nodes = 0, total_items = 0;
-    unsigned grid_nodes = 1, grid_warps = 1, grid_union = 1;
+    uint64_t total_nodes = 0;
+    unsigned grid_nodes = 1, grid_warps = 1;
+    std::vector<EngineGroup> groups;
 };
 
 uint64_t align256(uint64_t x);
 uint64_t l2_budget_bytes(int dev);
-JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget);
+JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode);
 JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
                    const double *lc, double *md, double *ball);
 uint64_t lc_offset(int p);

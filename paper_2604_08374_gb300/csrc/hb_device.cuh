@@ -227,6 +227,51 @@ __device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_
     union_store<S>(acc, cur, nxt, v, lane, flag);
 }
 
+// Rows of one slice's sparse table built by one CTA (`table_item`), and the
+// shared memory that takes them with their 15-row halo.
+template <int S>
+struct TableShape {
+    static constexpr int B = (S >= 1024) ? 16 : 32;
+    static constexpr int R = B + 15;
+    static constexpr int C16 = S / 16;  // 16-byte chunks per row
+};
+constexpr int kTableSmemBytes = (16 + 15) * 1024;  // largest (B + 15) * S
+
+// Sparse-table rows [r0, r0 + B) of one slice, all levels, straight from the
+// slice's counters: T_k[i] = max(cur[i .. i + 2^k)) for k = 1..kRunLevels and
+// the rows with i + 2^k <= n.  The rows and their halo are staged once in
+// `buf`; each thread then owns one 16-byte chunk of one output row and folds
+// the 16 rows of its widest window, writing T_1, T_2, T_3, T_4 as the window
+// reaches 2, 4, 8 and 16 rows (tab + (k-1) * n * S for level k).  All threads
+// of the CTA (256) take part.
+template <int S>
+__device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict__ tab, uint32_t n, uint32_t r0,
+                           uint8_t *buf) {
+    using T = TableShape<S>;
+    uint4 *b4 = reinterpret_cast<uint4 *>(buf);
+    const uint32_t avail = (n - r0 < (uint32_t)T::R) ? n - r0 : (uint32_t)T::R;
+    for (int x = threadIdx.x; x < T::R * T::C16; x += blockDim.x) {
+        const uint32_t row = x / T::C16, c = x % T::C16;
+        b4[x] = (row < avail) ? __ldg(reinterpret_cast<const uint4 *>(cur + (uint64_t)(r0 + row) * S) + c)
+                              : make_uint4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < T::B * T::C16; x += blockDim.x) {
+        const uint32_t row = x / T::C16, c = x % T::C16;
+        const uint64_t i = (uint64_t)r0 + row;
+        uint4 acc = b4[x];
+#pragma unroll
+        for (int j = 1; j < 16; j++) {
+            acc = vmax4(acc, b4[x + j * T::C16]);
+            if ((j & (j + 1)) == 0) {  // window of j + 1 = 2^k rows complete
+                const int k = 31 - __clz(j + 1);
+                if (i + (1u << k) <= n)
+                    reinterpret_cast<uint4 *>(tab + ((uint64_t)(k - 1) * n + i) * S)[c] = acc;
+            }
+        }
+    }
+}
+
 // Correctly rounded (to nearest, ties to even) conversion of hi*2^64 + lo to
 // double: shift the value into 64 bits keeping a sticky bit for everything
 // shifted out, let the hardware round the 64-bit integer, scale back exactly.

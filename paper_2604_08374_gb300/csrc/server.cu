@@ -150,6 +150,13 @@ void batched_lane(vga_server *S) {
         std::vector<JobDev> start;
         std::vector<std::shared_ptr<Request>> started;
         for (const auto &r : fresh) {
+            if (r->L.mode == 2) {
+                const int rc = ensure_run_lookups(r->g, stream);
+                if (rc != VGA_OK) {
+                    fail(S, r, rc, vga_last_error(), stream);
+                    continue;
+                }
+            }
             void *mem = nullptr;
             if (cudaMallocAsync(&mem, r->bytes, stream) != cudaSuccess) {
                 cudaGetLastError();
@@ -182,10 +189,13 @@ void batched_lane(vga_server *S) {
         int rc = engine_upload(A_run, host, &E, stream);
         if (rc == VGA_OK) rc = engine_pass(A_run, E, stream, 0, 0);
         cudaError_t e = cudaSuccess;
+        int err = 0;
         if (rc == VGA_OK) {
             e = cudaMemcpyAsync(host.data(), A_run.jobs, sizeof(JobDev) * host.size(), cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&err, A_run.error, sizeof(int), cudaMemcpyDeviceToHost, stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
             if (e != cudaSuccess) rc = VGA_ECUDA;
+            if (err) rc = VGA_ETIMEOUT;
         }
         {
             std::lock_guard<std::mutex> lock(S->mu);
@@ -315,7 +325,7 @@ int vga_server_submit(vga_server *S, const vga_graph *g, int p, int d, uint64_t 
     r->t_submit = Clock::now();
     r->lane = g->n > (uint32_t)S->cfg.solo_nodes ? 1 : 0;
     if (r->lane == 0) {
-        r->L = job_layout(g->n, p, 0, S->l2_budget);
+        r->L = job_layout(g->n, p, 0, S->l2_budget, 0);
         r->bytes = request_bytes_batched(r->L, g->n);
     } else {
         uint64_t ws = 0;

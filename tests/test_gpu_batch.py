@@ -1,7 +1,8 @@
 """GPU tests of the batched engine (hyperball_run_batch).
 
 Each job of a mixed batch (graphs of different sizes, p from 4 to 12, depth
-limits 0/1/3, both convergence rules, empty and one-node graphs) must give
+limits 0/1/3, both convergence rules, both union variants, empty and one-node
+graphs) must give
 exactly what a single-graph run of the same job gives (bit for bit), in both
 host-driven and CUDA-graph (conditional WHILE node) modes; a few jobs are also
 checked against the CPU oracle directly.
@@ -50,6 +51,7 @@ def _jobs(torch, graphs):
         conv = 1 if k % 7 == 3 else 0
         n = g.n_nodes
         jobs.append(dict(graph=g, off=off, b=b, p=p, d=d, seed=int(rng.integers(0, 2**62)), conv_mode=conv,
+                         union_mode=[0, 1, 2][k % 3],
                          mean_depth=torch.full((max(n, 1),), -7.0, dtype=torch.float64, device="cuda"),
                          ball=torch.full((max(n, 1),), -7.0, dtype=torch.float64, device="cuda")))
     return jobs
@@ -68,7 +70,7 @@ def test_batch_matches_single_runs(vga, graphs, use_graph):
             continue
         md = torch.empty(n, dtype=torch.float64, device="cuda")
         ball = torch.empty(n, dtype=torch.float64, device="cuda")
-        it = vga.hyperball_run_dev(g, j["p"], j["d"], j["seed"], md, ball, conv_mode=j["conv_mode"], union_mode=1)
+        it = vga.hyperball_run_dev(g, j["p"], j["d"], j["seed"], md, ball, conv_mode=j["conv_mode"])
         torch.cuda.synchronize()
         assert its[k] == it, k
         assert np.array_equal(j["mean_depth"][:n].cpu().numpy(), md.cpu().numpy(), equal_nan=True), k

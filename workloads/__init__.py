@@ -16,7 +16,10 @@ of the edge-density table in Sec. 4.3):
           component is about 42,700 cells (about 12 % cover);
   city    520 x 520 grid of urban blocks with sides uniform in 8..40 cells on a
           jittered street lattice, some slots left open as plazas, about
-          236,000 free cells and 4-5e9 directed visibility edges.
+          236,000 free cells and 4-5e9 directed visibility edges;
+  batch   256 grids of 1,000-30,000 free cells (log-uniform), mixed p and d;
+  serve   a pool of 64 grids of 1,000-236,000 free cells and a Poisson stream
+          of (graph, p, d) requests.
 
 All randomness comes from numpy's PCG64 ``default_rng(seed)``; a rectangle's
 top-left corner is uniform over the positions that keep it inside the grid,
@@ -117,13 +120,42 @@ def open_grid(W: int, H: int) -> np.ndarray:
     return np.zeros((H, W), np.uint8)
 
 
-def batch_sizes(count: int = 256, lo: int = 1_000, hi: int = 30_000, seed: int = 0) -> np.ndarray:
-    """Free-cell targets log-uniform in [lo, hi] (batched workload)."""
+def log_uniform_sizes(count: int, lo: int, hi: int, seed: int = 0) -> np.ndarray:
+    """Free-cell targets log-uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
 
 
 def grid_for_free_cells(target_free: int, seed: int = 0, cover: float = 0.12, side=(2, 20)) -> np.ndarray:
-    """Square grid sized so that about `target_free` cells stay free at the given cover."""
+    """Square grid sized so that about `target_free` cells stay free at the
+    given cover, filled like the medium workload (sides 2..20)."""
     side_len = int(np.ceil(np.sqrt(target_free / (1.0 - cover))))
     return rectangles_until(side_len, side_len, side, target_free, seed)
+
+
+def batch(count: int = 256, seed: int = 0):
+    """Batched workload: `count` grids with free cells log-uniform in 1,000-30,000
+    (medium-style generator, per-graph seed = seed + i), each with p uniform
+    over {8, 10, 12} and d uniform over {3, unlimited (0)}.  Returns a list of
+    dicts (grid, p, d)."""
+    sizes = log_uniform_sizes(count, 1_000, 30_000, seed)
+    rng = np.random.default_rng(seed + 1)
+    return [dict(grid=grid_for_free_cells(int(n), seed=seed + i), p=int(rng.choice([8, 10, 12])),
+                 d=int(rng.choice([3, 0]))) for i, n in enumerate(sizes)]
+
+
+def serve_pool(count: int = 64, seed: int = 0):
+    """Serving pool: `count` grids with free cells log-uniform in 1,000-236,000
+    (medium-style generator, per-graph seed = seed + 1000 + i)."""
+    sizes = log_uniform_sizes(count, 1_000, 236_000, seed)
+    return [grid_for_free_cells(int(n), seed=seed + 1000 + i) for i, n in enumerate(sizes)]
+
+
+def serve_requests(count: int, pool_size: int, rate: float, seed: int = 0):
+    """Poisson arrivals at `rate` per second: (arrival_s, graph index, p, d)
+    with graph uniform over the pool, p uniform over {8, 10, 12}, d uniform
+    over {3, 5, unlimited (0)}."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    return [(float(t[k]), int(rng.integers(pool_size)), int(rng.choice([8, 10, 12])), int(rng.choice([3, 5, 0])))
+            for k in range(count)]
