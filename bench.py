@@ -79,6 +79,8 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=150, help="requests per offered load")
     ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--lane-priority", type=int, default=0, help="server: 1 favours the solo lane, -1 the batched")
+    ap.add_argument("--solo-nodes", type=int, default=0, help="server: solo-lane threshold (0 = library default)")
     ap.add_argument("--backend", default="nccl")
     return ap.parse_args()
 
@@ -584,7 +586,8 @@ def run_serve_mode(args, dist):
             lat_single.append(free_at - a)
         single_makespan = free_at - arrivals[0]
         # served
-        with vga.Server(hbm_budget_bytes=150 << 30) as srv:
+        with vga.Server(hbm_budget_bytes=150 << 30, solo_nodes=args.solo_nodes,
+                        lane_priority=args.lane_priority) as srv:
             ids = [None] * R
             submit_t = [0.0] * R
             t_start = time.perf_counter()
@@ -621,7 +624,8 @@ def run_serve_mode(args, dist):
             "config": {"workload": f"pool of {len(pool)} medium-style grids, free cells log-uniform 1k-236k; "
                                    f"{R} requests per load, p in {{8,10,12}}, d in {{3,5,unlimited}}",
                        "pool_nodes": [g.n_nodes for g in pool], "pool_edges_total": int(sum(g.n_edges for g in pool)),
-                       "hbm_budget_bytes": 150 << 30, "graph_build_seconds": build_s},
+                       "hbm_budget_bytes": 150 << 30, "graph_build_seconds": build_s,
+                       "lane_priority": args.lane_priority, "solo_nodes": args.solo_nodes or 65536},
             "one_at_a_time_capacity_per_s": capacity, "loads": loads}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)

@@ -312,7 +312,9 @@ typedef struct vga_server_config {
     uint64_t hbm_budget_bytes;  /* device bytes requests may hold at once (0: 150 GiB)      */
     int max_batch;              /* requests advanced together in the batched lane (0: 256) */
     int solo_nodes;             /* graphs above this many nodes use the solo lane (0: 65536) */
-    int reserved[4];
+    int lane_priority;          /* 0: lanes equal; 1: solo lane's stream gets the higher
+                                   priority; -1: batched lane's does                          */
+    int reserved[3];
 } vga_server_config;
 
 typedef struct vga_server_stats_t {

@@ -95,10 +95,13 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
                                                                         unsigned long long *counter, int *error) {
     __shared__ uint32_t s_ids[kEngineWarps][32];
     __shared__ __align__(16) uint8_t s_tab[RUNS ? TableShape<S>::R * S : 16];
+    __shared__ __align__(128) LkStage s_stage[RUNS ? kEngineWarps : 1];
     __shared__ unsigned long long s_item;
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    uint32_t phase = 0;  // barrier phases of this warp's TMA stage
+    if (RUNS) lk_stage_init(s_stage[wib], lane);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
         __syncthreads();
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         if (v >= J.n) continue;
         uint8_t *nxt = J.regs[t & 1] + slice;
         if (RUNS)
-            union_node_runs<S>(J.lk_off, J.lk, cur, tab, nxt, J.n, v, s_ids[wib], lane, &J.changed);
+            union_node_runs<S>(J.lk_off, J.lk, cur, tab, nxt, J.n, v, s_stage[wib], phase, lane, &J.changed, error);
         else
             union_node_edges<S>(J.off, J.bytes, cur, nxt, v, s_ids[wib], lane, &J.changed);
     }

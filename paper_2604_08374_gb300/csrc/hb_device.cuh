@@ -200,29 +200,104 @@ __device__ __forceinline__ void union_node_edges(const uint64_t *__restrict__ of
     union_store<S>(acc, cur, nxt, v, lane, flag);
 }
 
+// ---------------------------------------------------------------------------
+// 1D TMA (cp.async.bulk) staging of a node's range lookups into shared memory.
+// Each warp owns two 512-byte buffers and two mbarriers; lane 0 issues a bulk
+// copy per buffer and the warp consumes one buffer while the next is in
+// flight.  Source and size are 16-byte multiples: a node's range is widened to
+// whole 4-lookup groups (the lookup list carries 4 entries of tail padding).
+// Every wait is bounded; a wait that runs out sets *err.
+// ---------------------------------------------------------------------------
+constexpr int kLkChunk = 128;  // lookups per bulk copy
+
+struct LkStage {
+    uint32_t buf[2][kLkChunk];
+    unsigned long long bar[2];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Lane 0: initialise the warp's two barriers (one arrival per phase).
+__device__ __forceinline__ void lk_stage_init(LkStage &st, int lane) {
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&st.bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&st.bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void lk_bulk_load(LkStage &st, int slot, const uint32_t *src, uint32_t bytes) {
+    const uint32_t bar = smem_u32(&st.bar[slot]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(st.buf[slot])),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Bounded wait for the phase `parity` of a barrier to complete.
+__device__ __forceinline__ bool lk_wait(LkStage &st, int slot, uint32_t parity) {
+    const uint32_t bar = smem_u32(&st.bar[slot]);
+    uint32_t done = 0;
+    for (uint32_t i = 0; i < (1u << 21) && !done; i++) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
 // Run-aware Eq. hll-union of node v for one register slice (runs.cu explains
 // the lookups): next[v] = max(cur[v], max over v's range lookups of T_k[i]),
 // where T_k[i] = max(cur[i .. i + 2^k)) has been built for this slice.  The
-// warp streams the node's lookups 32 at a time (evict-first: each is read once
-// per slice) and gathers the S-byte table rows like the per-neighbour union.
+// node's lookups stream through the warp's TMA stage (`st`, with its barrier
+// phases in `phase`) and each chunk's rows are gathered like the
+// per-neighbour union.
 template <int S>
 __device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_off, const uint32_t *__restrict__ lk,
                                                 const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab,
-                                                uint8_t *__restrict__ nxt, uint32_t n, uint32_t v, uint32_t *ids,
-                                                int lane, uint32_t *flag) {
+                                                uint8_t *__restrict__ nxt, uint32_t n, uint32_t v, LkStage &st,
+                                                uint32_t &phase, int lane, uint32_t *flag, int *err) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
     SplitAcc acc[4 * Sh::V4];
 #pragma unroll
     for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
     const TableRow<S> row{cur, tab, n};
-    const uint64_t end = lk_off[v + 1];
-    for (uint64_t b = lk_off[v]; b < end; b += 32) {
-        const int cnt = (end - b < 32) ? (int)(end - b) : 32;
-        if (lane < cnt) ids[lane] = __ldcs(lk + b + lane);
-        __syncwarp();
-        gather_fold<S>(row, ids, cnt, g, sub, acc);
-        __syncwarp();
+    const uint64_t b = lk_off[v], e = lk_off[v + 1];
+    if (b < e) {
+        const uint64_t a0 = b & ~3ull, e4 = (e + 3) & ~3ull;
+        const uint32_t chunks = (uint32_t)((e4 - a0 + kLkChunk - 1) / kLkChunk);
+        if (lane == 0) {
+            for (uint32_t c = 0; c < 2 && c < chunks; c++) {
+                const uint64_t s0 = a0 + (uint64_t)c * kLkChunk;
+                const uint32_t cnt = (uint32_t)((e4 - s0 < (uint64_t)kLkChunk) ? e4 - s0 : kLkChunk);
+                lk_bulk_load(st, (int)c, lk + s0, cnt * 4u);
+            }
+        }
+        for (uint32_t c = 0; c < chunks; c++) {
+            const int slot = (int)(c & 1u);
+            // every lane observes the barrier phase itself (acquire for its reads)
+            if (!__all_sync(0xffffffffu, lk_wait(st, slot, (phase >> slot) & 1u))) {
+                if (lane == 0) atomicExch(err, 1);
+                lk_wait(st, slot, (phase >> slot) & 1u);  // give an in-flight copy a last chance
+            }
+            phase ^= 1u << slot;
+            const uint64_t s0 = a0 + (uint64_t)c * kLkChunk;
+            const uint64_t lo = b > s0 ? b : s0;
+            const uint64_t hi = (e < s0 + kLkChunk) ? e : s0 + kLkChunk;
+            if (hi > lo) gather_fold<S>(row, st.buf[slot] + (lo - s0), (int)(hi - lo), g, sub, acc);
+            __syncwarp();
+            if (lane == 0 && c + 2 < chunks) {
+                const uint64_t s2 = a0 + (uint64_t)(c + 2) * kLkChunk;
+                const uint32_t cnt = (uint32_t)((e4 - s2 < (uint64_t)kLkChunk) ? e4 - s2 : kLkChunk);
+                lk_bulk_load(st, slot, lk + s2, cnt * 4u);
+            }
+        }
     }
     union_store<S>(acc, cur, nxt, v, lane, flag);
 }

@@ -66,21 +66,26 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
 }
 
 // Run-aware Eq. hll-union for one register slice, one warp per node
-// (union_node_runs), after the slice's sparse table has been built.
+// (union_node_runs, lookups staged by TMA), after the slice's sparse table has
+// been built.  flags[2] records a bounded wait that ran out.
 template <int S>
 __global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__restrict__ lk_off,
                                                             const uint32_t *__restrict__ lk,
                                                             const uint8_t *__restrict__ cur,
                                                             const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt,
                                                             uint32_t n, uint32_t *__restrict__ flags) {
-    extern __shared__ uint32_t s_ids[];
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    LkStage *stages = reinterpret_cast<LkStage *>(s_dyn);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
-    union_node_runs<S>(lk_off, lk, cur, tab, nxt, n, (uint32_t)warp, s_ids + wib * 32, lane, flags);
+    LkStage &st = stages[wib];
+    lk_stage_init(st, lane);
+    uint32_t phase = 0;
+    union_node_runs<S>(lk_off, lk, cur, tab, nxt, n, (uint32_t)warp, st, phase, lane, flags,
+                       reinterpret_cast<int *>(flags + 2));
 }
-
 
 // One sparse-table level for a slice: out[i] = max(prev[i], prev[i + half]) for
 // i = 0 .. rows-1 (rows = N - 2*half + 1; later rows are never looked up).
@@ -289,8 +294,8 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
             count_launch();
             prev = out;
         }
-        hb_union_runs_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_lk_off, g->d_lk, c, tab, x,
-                                                                         (uint32_t)P.n, flags);
+        hb_union_runs_kernel<SS><<<blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
+            g->d_lk_off, g->d_lk, c, tab, x, (uint32_t)P.n, flags);
     } else {
         hb_union_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
                                                                     flags);
@@ -440,14 +445,19 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         VGA_CHECK_CUDA(cudaGetLastError());
         VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0
         if (max_trace >= 0) VGA_TRY(copy_trace(P, cur, c_prev, 0, trace_regs, trace_c, stream));
-        uint32_t hflags[2];
+        uint32_t hflags[3];
+        VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 12, stream));
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
             VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, profiling ? &timings : nullptr));
             VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
             if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
-            VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, stream));
+            VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 12, cudaMemcpyDeviceToHost, stream));
             VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+            if (hflags[2]) {
+                set_error("a bounded wait for a TMA copy ran out in pass %d", t);
+                return VGA_ETIMEOUT;
+            }
             std::swap(cur, nxt);
             std::swap(c_prev, c_cur);
             const bool stop = (conv_mode == 1) ? (hflags[1] == 0) : (hflags[0] == 0);

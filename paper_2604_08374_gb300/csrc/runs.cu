@@ -142,7 +142,8 @@ int ensure_run_lookups(const vga_graph *g, cudaStream_t stream) {
         for (uint32_t v = 0; v < n; v++) h_off[v + 1] = h_off[v] + h_cnt[v];
     }
     const uint64_t total = h_off[n];
-    VGA_TRY(d_lk.alloc(4 * (size_t)(total ? total : 1)));
+    VGA_TRY(d_lk.alloc(4 * ((size_t)total + 4)));  // + one 16-byte group: TMA copies round up to whole groups
+    VGA_CHECK_CUDA(cudaMemsetAsync(d_lk.as<uint8_t>() + 4 * total, 0, 16, stream));
     VGA_CHECK_CUDA(cudaMemcpyAsync(d_off.ptr, h_off.data(), 8 * ((size_t)n + 1), cudaMemcpyHostToDevice, stream));
     if (n) {
         run_lookups_kernel<true><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, nullptr,

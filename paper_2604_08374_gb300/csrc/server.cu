@@ -291,8 +291,12 @@ int vga_server_create(const vga_server_config *cfg, vga_server **out) {
     void *mem = nullptr;
     VGA_CHECK_CUDA(cudaMalloc(&mem, arrays));
     S->arrays = static_cast<uint8_t *>(mem);
-    VGA_CHECK_CUDA(cudaStreamCreateWithFlags(&S->stream_batched, cudaStreamNonBlocking));
-    VGA_CHECK_CUDA(cudaStreamCreateWithFlags(&S->stream_solo, cudaStreamNonBlocking));
+    int prio_low = 0, prio_high = 0;
+    VGA_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    const int prio_batched = S->cfg.lane_priority < 0 ? prio_high : prio_low;
+    const int prio_solo = S->cfg.lane_priority > 0 ? prio_high : prio_low;
+    VGA_CHECK_CUDA(cudaStreamCreateWithPriority(&S->stream_batched, cudaStreamNonBlocking, prio_batched));
+    VGA_CHECK_CUDA(cudaStreamCreateWithPriority(&S->stream_solo, cudaStreamNonBlocking, prio_solo));
     VGA_TRY(upload_lc_tables(S->arrays + 2 * align256(engine_arrays_bytes(S->cfg.max_batch)), nullptr,
                              S->stream_batched));
     VGA_CHECK_CUDA(cudaStreamSynchronize(S->stream_batched));

@@ -7,7 +7,8 @@
 //
 // Pipeline: (host) main component and numbering; (device) one warp per
 // (source, 32 consecutive targets) walks each segment through the grid and
-// ballots the results into an N x ceil(N/32) bit matrix; (device) one warp per
+// ballots the results into an N x ceil(N/32) bit matrix, upper block triangle
+// only, then 32 x 32 bit-block transposes fill the lower one; (device) one warp per
 // source counts the LEB128 bytes of its row; (host) prefix sum into offsets;
 // (device) one warp per source writes the bytes; then the ordinary load path
 // validates the stream and derives degrees.
@@ -97,13 +98,16 @@ __device__ bool segment_clear(const uint32_t *__restrict__ bits, int W, int x0, 
     return true;
 }
 
-// One warp per (source u, word w): lanes test targets 32w .. 32w+31.
+// One warp per (source u, word w): lanes test targets 32w .. 32w+31.  The
+// relation is symmetric, so only words at or right of u's own 32-column block
+// are walked (the upper triangle of 32 x 32 blocks, diagonal blocks in full);
+// transpose_blocks_kernel mirrors the rest.
 __global__ void visibility_bits_kernel(const uint32_t *__restrict__ obst_bits, const uint32_t *__restrict__ cells,
                                        uint32_t n, int W, uint32_t words, uint32_t *__restrict__ bitmat) {
     const int lane = threadIdx.x & 31;
     const uint32_t u = blockIdx.x;
     const uint32_t w = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= words) return;
+    if (w >= words || w < u / 32u) return;
     const uint32_t t = w * 32 + lane;
     bool vis = false;
     if (t < n && t != u) {
@@ -113,6 +117,38 @@ __global__ void visibility_bits_kernel(const uint32_t *__restrict__ obst_bits, c
     }
     const uint32_t ballot = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) bitmat[(uint64_t)u * words + w] = ballot;
+}
+
+// Mirror block (bi, bj), bj > bi, of the 32 x 32-bit block matrix into (bj, bi):
+// lane l holds row bi*32 + l's word bj; ballot j collects bit j of every lane,
+// which is row bj*32 + j's word bi.
+__global__ void transpose_blocks_kernel(uint32_t n, uint32_t words, uint32_t *__restrict__ bitmat) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // warp -> (bi, bj) with bi < bj < words, row-major over the strict upper triangle
+    const uint64_t total = (uint64_t)words * (words - 1) / 2;
+    if (warp >= total) return;
+    // bi = largest i with i*words - i*(i+1)/2 <= warp; solved by bisection
+    uint32_t lo = 0, hi = words - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        const uint64_t start = (uint64_t)mid * words - (uint64_t)mid * (mid + 1) / 2;
+        if (start <= warp) lo = mid;
+        else hi = mid - 1;
+    }
+    const uint32_t bi = lo;
+    const uint64_t start = (uint64_t)bi * words - (uint64_t)bi * (bi + 1) / 2;
+    const uint32_t bj = bi + 1 + (uint32_t)(warp - start);
+    const uint32_t row = bi * 32 + lane;
+    const uint32_t word = row < n ? bitmat[(uint64_t)row * words + bj] : 0u;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        const uint32_t col = __ballot_sync(0xffffffffu, (word >> j) & 1u);
+        if (lane == j) mine = col;
+    }
+    const uint32_t out_row = bj * 32 + lane;
+    if (out_row < n) bitmat[(uint64_t)out_row * words + bi] = mine;
 }
 
 __device__ __forceinline__ uint32_t varint_len(uint32_t x) {
@@ -248,6 +284,13 @@ int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_no
                                                                  words, d_mat.as<uint32_t>());
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
+        const uint64_t blocks_upper = (uint64_t)words * (words - 1) / 2;
+        if (blocks_upper) {
+            transpose_blocks_kernel<<<(unsigned)((blocks_upper + warps - 1) / warps), warps * 32, 0, stream>>>(
+                n, words, d_mat.as<uint32_t>());
+            count_launch();
+            VGA_CHECK_CUDA(cudaGetLastError());
+        }
         const unsigned rblocks = (n + warps - 1) / warps;
         encode_rows_kernel<false><<<rblocks, warps * 32, 0, stream>>>(d_mat.as<uint32_t>(), n, words,
                                                                       d_rowbytes.as<uint64_t>(), nullptr, nullptr);
