@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, d=unlimited and CPU baseline")
     ap.add_argument("--slice-bytes", type=int, default=0, help="force the union slice width (0 = automatic)")
     ap.add_argument("--warps", type=int, default=0, help="force union warps per CTA (0 = automatic)")
+    ap.add_argument("--order", choices=["raster", "hilbert"], default="raster", help="node numbering of the graph")
+    ap.add_argument("--register-bits", type=int, default=8, choices=[8, 4],
+                    help="8: uint8 registers; 4: the paper's packed 4-bit registers")
     ap.add_argument("--union-mode", type=int, default=0,
                     help="0 automatic, 1 one gather per neighbour, 2 per run of consecutive ids")
     ap.add_argument("--mode", choices=["metric", "batch", "serve"], default="metric",
@@ -317,7 +320,7 @@ def run_ours(args, dist: Dist):
     dev = torch.device("cuda", dist.local_rank)
     obst = CONFIGS[args.config]["grid"]()
     t0 = time.perf_counter()
-    g = vga.vga_visibility_build(obst)
+    g = vga.vga_visibility_build(obst, order=args.order)
     build_s = time.perf_counter() - t0
     N, E, B = g.n_nodes, g.n_edges, g.n_bytes
     ws = torch.empty(vga.hyperball_workspace_bytes(g, args.p), dtype=torch.uint8, device=dev)
@@ -328,7 +331,8 @@ def run_ours(args, dist: Dist):
     def step(d, union_mode=None):
         return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=ws, stream=stream,
                                      slice_bytes=args.slice_bytes, warps_per_cta=args.warps,
-                                     union_mode=args.union_mode if union_mode is None else union_mode)
+                                     union_mode=args.union_mode if union_mode is None else union_mode,
+                                     register_bits=0 if args.register_bits == 8 else args.register_bits)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -451,7 +455,8 @@ def run_ours(args, dist: Dist):
             "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
-                       "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode,
+                       "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode, "order": args.order,
+                       "register_bits": args.register_bits,
                        "parallelism": f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",
                        "graph_build_seconds": build_s},

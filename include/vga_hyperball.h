@@ -149,6 +149,18 @@ int vga_graph_copy_csr(const vga_graph *g, uint64_t *offsets, uint8_t *bytes, ui
  */
 int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_node, vga_graph **out);
 
+/*
+ * vga_visibility_build_ordered -- as vga_visibility_build, with the node
+ * order chosen: order 0 numbers the main component's cells in row-major
+ * raster order, order 1 along the Hilbert curve of the smallest 2^k x 2^k
+ * square covering the grid (Sec. 3.2, "Optional Hilbert reordering": nearby
+ * cells get nearby ids, which keeps the deltas small; the compressed size
+ * stays within about 1 % of raster order).  Raster order makes visible row
+ * stretches runs of consecutive ids, which the run-aware union exploits.
+ */
+int vga_visibility_build_ordered(int W, int H, const uint8_t *obst, int order, uint64_t *cell_of_node,
+                                 vga_graph **out);
+
 /* Number of nodes (main-component cells) the builder would produce. */
 int vga_visibility_count(int W, int H, const uint8_t *obst, uint32_t *n_nodes);
 
@@ -166,7 +178,11 @@ typedef struct vga_tuning {
                             give the same registers bit for bit.  Mode 2 builds, on a
                             graph's first use, a lookup list held by the graph (~4 bytes
                             per run, about 0.65 byte per edge on city graphs).            */
-    int reserved[4];
+    int register_bits;   /* 0 or 8: uint8 registers; 4: the paper's packed format (Sec. 3.3,
+                            two registers per byte, rho clamped to 15, p >= 5).  4-bit
+                            runs are not bit-comparable with 8-bit ones wherever a rho
+                            above 15 occurs; they match the same clamp applied alone.      */
+    int reserved[3];
 } vga_tuning;
 
 /*

@@ -104,12 +104,20 @@ def lib():
                                         C.c_int, C.c_int, f64p, f64p, C.POINTER(C.c_int), _nullable(u8p),
                                         _nullable(f64p), C.c_int]
             L.orc_hyperball.restype = C.c_int
+            L.orc_hyperball_bits.argtypes = [C.c_int64, u64p, u8p, _nullable(u32p), C.c_int, C.c_int, C.c_uint64,
+                                             C.c_int, C.c_int, C.c_int, f64p, f64p, C.POINTER(C.c_int),
+                                             _nullable(u8p), _nullable(f64p), C.c_int]
+            L.orc_hyperball_bits.restype = C.c_int
+            L.orc_hll_init_bits.argtypes = [C.c_int64, C.c_int, C.c_uint64, C.c_int, u8p]
+            L.orc_hll_init_bits.restype = None
             L.orc_bfs.argtypes = [C.c_int64, u64p, u8p, C.c_int64, i32p]
             L.orc_bfs.restype = C.c_int
             L.orc_dvalue.argtypes = [C.c_double]
             L.orc_dvalue.restype = C.c_double
             L.orc_metrics.argtypes = [C.c_int64, f64p, _nullable(u32p), u32p, f64p]
             L.orc_metrics.restype = None
+            L.orc_hilbert_index.argtypes = [C.c_int, C.c_uint32, C.c_uint32]
+            L.orc_hilbert_index.restype = C.c_uint64
             _lib = L
     return _lib
 
@@ -220,9 +228,27 @@ def decode_csr(offsets: np.ndarray, bytes_: np.ndarray):
     return row_ptr, col
 
 
-def build_graph(obst: np.ndarray, nthreads=None):
-    """Obstacle grid -> (offsets, bytes, cell_of_node) of the main component."""
+def hilbert_index(k: int, x: int, y: int) -> int:
+    """Position of cell (x, y) along the Hilbert curve of a 2^k x 2^k square."""
+    return int(lib().orc_hilbert_index(k, x, y))
+
+
+def hilbert_order(obst: np.ndarray, cell_of_node: np.ndarray) -> np.ndarray:
+    """The main component's cells renumbered along the Hilbert curve of the
+    smallest 2^k square covering the grid (Sec. 3.2 "Optional Hilbert
+    reordering"): returns cell_of_node sorted by Hilbert index."""
+    H, W = obst.shape
+    k = max(1, int(np.ceil(np.log2(max(W, H)))))
+    keys = np.array([hilbert_index(k, int(c % W), int(c // W)) for c in cell_of_node], np.uint64)
+    return cell_of_node[np.argsort(keys, kind="stable")]
+
+
+def build_graph(obst: np.ndarray, nthreads=None, order: str = "raster"):
+    """Obstacle grid -> (offsets, bytes, cell_of_node) of the main component,
+    nodes numbered in raster order or along the Hilbert curve."""
     _, cell_of_node = main_component(obst)
+    if order == "hilbert":
+        cell_of_node = hilbert_order(obst, cell_of_node)
     row_ptr, col = visibility_csr(obst, cell_of_node, nthreads=nthreads)
     offsets, bytes_ = csr_encode(row_ptr, col)
     return offsets, bytes_, cell_of_node
@@ -243,9 +269,9 @@ def hll_hash(v: int, seed: int, p: int):
     return int(j.value), int(rho.value)
 
 
-def hll_init(n: int, p: int, seed: int) -> np.ndarray:
+def hll_init(n: int, p: int, seed: int, reg_bits: int = 8) -> np.ndarray:
     regs = np.zeros(max(n, 1) << p, np.uint8)
-    lib().orc_hll_init(n, p, seed, regs)
+    lib().orc_hll_init_bits(n, p, seed, reg_bits, regs)
     return regs[: n << p].reshape(n, 1 << p)
 
 
@@ -285,8 +311,9 @@ def union_pass(offsets, bytes_, cur: np.ndarray, p: int, nodes=None, nthreads=No
 
 
 def hyperball(offsets, bytes_, p: int, d: int, seed: int = 0, conv_mode: int = 0, comp_size=None,
-              nthreads=None, trace: int = -1):
+              nthreads=None, trace: int = -1, reg_bits: int = 8):
     """Algorithm 1.  Returns dict(mean_depth, ball, iterations[, regs, c]).
+    reg_bits=4: the paper's 4-bit registers (rho clamped to 15).
 
     trace >= 0 also returns the registers (trace+1, N, m) and estimates
     (trace+1, N) after each pass, index 0 being the initial counters."""
@@ -304,8 +331,8 @@ def hyperball(offsets, bytes_, p: int, d: int, seed: int = 0, conv_mode: int = 0
         regs = np.zeros(max((trace + 1) * n * m, 1), np.uint8)
         c = np.zeros(max((trace + 1) * n, 1), np.float64)
     cs = None if comp_size is None else np.ascontiguousarray(comp_size, np.uint32)
-    rc = lib().orc_hyperball(n, offsets, bytes_, cs, p, d, seed, conv_mode, nthreads or default_threads(),
-                             md, ball, C.byref(it), regs, c, trace)
+    rc = lib().orc_hyperball_bits(n, offsets, bytes_, cs, p, d, seed, conv_mode, reg_bits,
+                                  nthreads or default_threads(), md, ball, C.byref(it), regs, c, trace)
     if rc != 0:
         raise ValueError("malformed CSR")
     out = {"mean_depth": md[:n], "ball": ball[:n], "iterations": int(it.value)}

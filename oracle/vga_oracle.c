@@ -325,17 +325,24 @@ void orc_hll_hash(uint64_t v, uint64_t seed, int p, uint32_t *j_out, uint8_t *rh
 }
 
 /* Alg. 1 initialisation: zero the counters, then insert each node into its
- * own counter.  regs is N x m, node-major. */
-void orc_hll_init(int64_t n, int p, uint64_t seed, uint8_t *regs) {
+ * own counter.  regs is N x m, node-major, one byte per register.  reg_bits =
+ * 4 is the paper's packed format (Sec. 3.3, "two 4-bit registers per byte"):
+ * a register holds at most 15, so rho is clamped to 15 (the paper does not say
+ * how larger values are stored; clamping is the reading taken). */
+void orc_hll_init_bits(int64_t n, int p, uint64_t seed, int reg_bits, uint8_t *regs) {
     int64_t m = (int64_t)1 << p;
+    uint8_t cap = (reg_bits == 4) ? 15 : 255;
     memset(regs, 0, (size_t)(n * m));
     for (int64_t v = 0; v < n; v++) {
         uint32_t j;
         uint8_t rho;
         orc_hll_hash((uint64_t)v, seed, p, &j, &rho);
+        if (rho > cap) rho = cap;
         if (rho > regs[v * m + j]) regs[v * m + j] = rho;
     }
 }
+
+void orc_hll_init(int64_t n, int p, uint64_t seed, uint8_t *regs) { orc_hll_init_bits(n, p, seed, 8, regs); }
 
 /* HLL alpha_m (Flajolet et al. 2007). */
 double orc_hll_alpha(int p) {
@@ -467,9 +474,9 @@ int orc_union_pass(int64_t n, int p, const uint64_t *offsets, const uint8_t *byt
 /*   registers (index 0 = initial); trace_c likewise (max_trace+1) x N.      */
 /* Returns 0, or -1 on a malformed CSR.                                       */
 /* ------------------------------------------------------------------------ */
-int orc_hyperball(int64_t n, const uint64_t *offsets, const uint8_t *bytes, const uint32_t *comp_size,
-                  int p, int d, uint64_t seed, int conv_mode, int nthreads, double *mean_depth, double *ball,
-                  int *iters, uint8_t *trace_regs, double *trace_c, int max_trace) {
+int orc_hyperball_bits(int64_t n, const uint64_t *offsets, const uint8_t *bytes, const uint32_t *comp_size,
+                       int p, int d, uint64_t seed, int conv_mode, int reg_bits, int nthreads, double *mean_depth,
+                       double *ball, int *iters, uint8_t *trace_regs, double *trace_c, int max_trace) {
     int64_t m = (int64_t)1 << p;
     uint8_t *cur = (uint8_t *)malloc((size_t)(n * m > 0 ? n * m : 1));
     uint8_t *next = (uint8_t *)malloc((size_t)(n * m > 0 ? n * m : 1));
@@ -478,7 +485,7 @@ int orc_hyperball(int64_t n, const uint64_t *offsets, const uint8_t *bytes, cons
     double *sum_d = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     int rc = 0, t = 0;
 
-    orc_hll_init(n, p, seed, cur);                                   /* Alg. 1 init      */
+    orc_hll_init_bits(n, p, seed, reg_bits, cur);                    /* Alg. 1 init      */
     for (int64_t v = 0; v < n; v++) c_prev[v] = orc_hll_estimate(cur + v * m, p);  /* c_0 */
     if (trace_regs && max_trace >= 0) memcpy(trace_regs, cur, (size_t)(n * m));
     if (trace_c && max_trace >= 0) memcpy(trace_c, c_prev, sizeof(double) * (size_t)n);
@@ -511,6 +518,13 @@ int orc_hyperball(int64_t n, const uint64_t *offsets, const uint8_t *bytes, cons
     }
     free(cur); free(next); free(c_prev); free(c_cur); free(sum_d);
     return rc;
+}
+
+int orc_hyperball(int64_t n, const uint64_t *offsets, const uint8_t *bytes, const uint32_t *comp_size,
+                  int p, int d, uint64_t seed, int conv_mode, int nthreads, double *mean_depth, double *ball,
+                  int *iters, uint8_t *trace_regs, double *trace_c, int max_trace) {
+    return orc_hyperball_bits(n, offsets, bytes, comp_size, p, d, seed, conv_mode, 8, nthreads, mean_depth, ball,
+                              iters, trace_regs, trace_c, max_trace);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -580,4 +594,31 @@ void orc_metrics(int64_t n, const double *md, const uint32_t *comp_size, const u
         out[4 * v + 2] = pv;
         out[4 * v + 3] = m * (double)degree[v];
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hilbert order (Sec. 3.2, "Optional Hilbert reordering").                  */
+/* Index of cell (x, y) along the Hilbert curve filling a 2^k x 2^k square, */
+/* by the classic quadrant-by-quadrant construction: at each level from the */
+/* coarsest, add the quadrant's offset (0, 1, 2, 3 squares of the level in  */
+/* curve order) and rotate/reflect the coordinates into the sub-curve's      */
+/* frame.                                                                    */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_hilbert_index(int k, uint32_t x, uint32_t y) {
+    uint64_t d = 0;
+    for (int64_t s = (int64_t)1 << (k - 1); s > 0; s >>= 1) {
+        uint32_t rx = (x & (uint32_t)s) ? 1u : 0u;
+        uint32_t ry = (y & (uint32_t)s) ? 1u : 0u;
+        d += (uint64_t)s * (uint64_t)s * ((3u * rx) ^ ry);
+        if (ry == 0) {                 /* rotate the quadrant */
+            if (rx == 1) {
+                x = (uint32_t)(s - 1) - (x & (uint32_t)(s - 1)) + (x & ~(uint32_t)(s - 1));
+                y = (uint32_t)(s - 1) - (y & (uint32_t)(s - 1)) + (y & ~(uint32_t)(s - 1));
+            }
+            uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
 }

@@ -31,7 +31,7 @@ vp, i32, u32, u64, i64, f64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_i
 
 class VgaTuning(C.Structure):
     _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
-                ("union_mode", C.c_int), ("reserved", C.c_int * 4)]
+                ("union_mode", C.c_int), ("register_bits", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class VgaJob(C.Structure):
@@ -70,6 +70,7 @@ SIGNATURES = {
     "vga_graph_copy_csr": ([vp, vp, vp, vp], i32),
     "vga_visibility_build": ([i32, i32, vp, vp, C.POINTER(vp)], i32),
     "vga_visibility_count": ([i32, i32, vp, C.POINTER(u32)], i32),
+    "vga_visibility_build_ordered": ([i32, i32, vp, i32, vp, C.POINTER(vp)], i32),
     "hyperball_run": ([vp, i32, i32, u64, vp, vp, C.POINTER(i32)], i32),
     "hyperball_workspace_bytes": ([vp, i32, C.POINTER(u64)], i32),
     "hyperball_run_dev": ([vp, i32, i32, u64, i32, vp, vp, C.POINTER(i32), vp, u64, vp, C.POINTER(VgaTuning)], i32),
@@ -137,11 +138,12 @@ def _ptr(a) -> int | None:
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
-def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0):
-    if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode):
+def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0, register_bits=0):
+    if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode or register_bits):
         return None
     t = VgaTuning()
     t.slice_bytes, t.warps_per_cta, t.l2_budget_mb, t.union_mode = slice_bytes, warps_per_cta, l2_budget_mb, union_mode
+    t.register_bits = register_bits
     return C.pointer(t)
 
 
@@ -249,13 +251,15 @@ def vga_visibility_count(obst: np.ndarray) -> int:
     return n.value
 
 
-def vga_visibility_build(obst: np.ndarray, return_cells: bool = False):
-    """Build the supercover visibility graph of an obstacle grid on the GPU."""
+def vga_visibility_build(obst: np.ndarray, return_cells: bool = False, order: str = "raster"):
+    """Build the supercover visibility graph of an obstacle grid on the GPU,
+    nodes in raster or Hilbert order."""
     obst = np.ascontiguousarray(obst, np.uint8)
     H, W = obst.shape
     cells = np.zeros(max(H * W, 1), np.uint64)
     h = C.c_void_p()
-    _check(lib().vga_visibility_build(W, H, _ptr(obst), _ptr(cells), C.byref(h)))
+    _check(lib().vga_visibility_build_ordered(W, H, _ptr(obst), {"raster": 0, "hilbert": 1}[order], _ptr(cells),
+                                              C.byref(h)))
     g = Graph(h.value)
     if return_cells:
         return g, cells[: g.n_nodes]
@@ -292,13 +296,13 @@ def hyperball_workspace_bytes(g: Graph, p: int) -> int:
 
 def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
                       workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
-                      l2_budget_mb: int = 0, union_mode: int = 0) -> int:
+                      l2_budget_mb: int = 0, union_mode: int = 0, register_bits: int = 0) -> int:
     """Algorithm 1 into device tensors (float64, N each); returns passes run."""
     it = C.c_int()
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
-                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode)))
+                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode, register_bits)))
     return it.value
 
 
@@ -314,7 +318,7 @@ def hyperball_run_noalloc(g: Graph, p: int, d: int, seed: int, mean_depth_dev, b
 
 
 def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0, max_trace: int = 8,
-                        slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0):
+                        slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0):
     """Run with per-pass register and estimate dumps (bit-exact checks).
 
     Returns dict(mean_depth, ball, iterations, regs[(max_trace+1), N, m], c[(max_trace+1), N])."""
@@ -326,7 +330,8 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
     it = C.c_int()
     _check(lib().hyperball_run_trace(g.handle, p, d, seed, conv_mode, _ptr(md), _ptr(ball), C.byref(it),
                                      _ptr(regs), _ptr(cc), max_trace,
-                                     _tuning(slice_bytes, warps_per_cta, union_mode=union_mode)))
+                                     _tuning(slice_bytes, warps_per_cta, union_mode=union_mode,
+                                             register_bits=register_bits)))
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}

@@ -32,33 +32,55 @@ struct GatherShape {
     static constexpr int U = (V4 == 1) ? 4 : 2;
 };
 
-// Bytewise max through 16-bit lanes.  For a register word w = [b3 b2 b1 b0],
-// an unsigned max over u16x2 lanes of w keeps max(b3) and max(b1) in the lanes'
-// high bytes (the high byte decides the comparison; the low byte is whatever
-// came with the winner), and the same over w << 8 keeps max(b2) and max(b0).
-// Two DPX three-way maxima (__vimax3_u16x2) thus fold two gathered words into
-// the running maximum, instead of the multi-instruction __vmaxu4 emulation.
-// SplitAcc holds the two halves for one register word.
-struct SplitAcc {
-    uint32_t hi;  // u16x2 max over w: bytes 3 and 1 in the high byte of each lane
-    uint32_t lo;  // u16x2 max over w << 8: bytes 2 and 0 likewise
+// Register maximum through 16-bit lanes.  For a register word w = [b3 b2 b1 b0]
+// of uint8 registers, an unsigned max over u16x2 lanes of w keeps max(b3) and
+// max(b1) in the lanes' high bytes (the high byte decides the comparison; the
+// low byte is whatever came with the winner), and the same over w << 8 keeps
+// max(b2) and max(b0).  Two DPX three-way maxima (__vimax3_u16x2) thus fold two
+// gathered words into the running maximum, instead of the multi-instruction
+// __vmaxu4 emulation.  With 4-bit registers (two per byte, the paper's packed
+// format) the same holds for the top nibble of each 16-bit lane, so four
+// shifted copies (w, w << 4, w << 8, w << 12) cover the four nibble positions.
+// RegFmt<NIB>::Acc holds the shifted maxima of one register word.
+template <bool NIB>
+struct RegFmt {
+    static constexpr int K = NIB ? 4 : 2;  // shifted copies per word
+    static constexpr int SHIFT = NIB ? 4 : 8;
+    struct Acc {
+        uint32_t h[K];
+    };
+    static __device__ __forceinline__ void fold2(Acc &a, uint32_t w0, uint32_t w1) {
+#pragma unroll
+        for (int k = 0; k < K; k++) a.h[k] = __vimax3_u16x2(a.h[k], w0 << (SHIFT * k), w1 << (SHIFT * k));
+    }
+    // register values of the word: copy k holds, in each lane's top field, the
+    // field that sat k positions lower
+    static __device__ __forceinline__ uint32_t word(const Acc &a) {
+        uint32_t r = 0;
+        const uint32_t top = NIB ? 0xF000F000u : 0xFF00FF00u;
+#pragma unroll
+        for (int k = 0; k < K; k++) r |= (a.h[k] & top) >> (SHIFT * k);
+        return r;
+    }
+    // field-wise max of two register words
+    static __device__ __forceinline__ uint32_t max_word(uint32_t a, uint32_t b) {
+        if (!NIB) return __vmaxu4(a, b);
+        const uint32_t lo = __vmaxu4(a & 0x0F0F0F0Fu, b & 0x0F0F0F0Fu);
+        const uint32_t hi = __vmaxu4((a >> 4) & 0x0F0F0F0Fu, (b >> 4) & 0x0F0F0F0Fu);
+        return lo | (hi << 4);
+    }
+    static __device__ __forceinline__ uint4 max4(uint4 a, uint4 b) {
+        return make_uint4(max_word(a.x, b.x), max_word(a.y, b.y), max_word(a.z, b.z), max_word(a.w, b.w));
+    }
 };
-
-__device__ __forceinline__ void split_fold2(SplitAcc &a, uint32_t w0, uint32_t w1) {
-    a.hi = __vimax3_u16x2(a.hi, w0, w1);
-    a.lo = __vimax3_u16x2(a.lo, w0 << 8, w1 << 8);
-}
-
-__device__ __forceinline__ uint32_t split_bytes(const SplitAcc &a) {
-    return (a.hi & 0xFF00FF00u) | ((a.lo >> 8) & 0x00FF00FFu);
-}
 
 // Fold the S-byte rows row(ids[0..cnt)) into acc (4 * V4 words per lane, split
 // form).  Loads for U rows per lane are issued before any is folded.
-template <int S, class Row>
+template <int S, bool NIB, class Row>
 __device__ __forceinline__ void gather_fold(const Row &row, const uint32_t *ids, int cnt, int g, int sub,
-                                            SplitAcc (&acc)[4 * GatherShape<S>::V4]) {
+                                            typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4]) {
     using Sh = GatherShape<S>;
+    using F = RegFmt<NIB>;
     static_assert(Sh::U % 2 == 0, "loads are folded in pairs");
     for (int k0 = 0; k0 < cnt; k0 += Sh::P * Sh::U) {
         uint4 x[Sh::U][Sh::V4];
@@ -78,10 +100,10 @@ __device__ __forceinline__ void gather_fold(const Row &row, const uint32_t *ids,
         for (int u = 0; u < Sh::U; u += 2)
 #pragma unroll
             for (int q = 0; q < Sh::V4; q++) {
-                split_fold2(acc[4 * q + 0], x[u][q].x, x[u + 1][q].x);
-                split_fold2(acc[4 * q + 1], x[u][q].y, x[u + 1][q].y);
-                split_fold2(acc[4 * q + 2], x[u][q].z, x[u + 1][q].z);
-                split_fold2(acc[4 * q + 3], x[u][q].w, x[u + 1][q].w);
+                F::fold2(acc[4 * q + 0], x[u][q].x, x[u + 1][q].x);
+                F::fold2(acc[4 * q + 1], x[u][q].y, x[u + 1][q].y);
+                F::fold2(acc[4 * q + 2], x[u][q].z, x[u + 1][q].z);
+                F::fold2(acc[4 * q + 3], x[u][q].w, x[u + 1][q].w);
             }
     }
 }
@@ -108,14 +130,15 @@ struct TableRow {
 
 // Convert the split accumulators to register bytes and fold the P lane groups
 // of a warp together (every lane ends with the group maximum).
-template <int S>
-__device__ __forceinline__ void finish_groups(const SplitAcc (&acc)[4 * GatherShape<S>::V4],
+template <int S, bool NIB>
+__device__ __forceinline__ void finish_groups(const typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4],
                                               uint4 (&out)[GatherShape<S>::V4]) {
     using Sh = GatherShape<S>;
+    using F = RegFmt<NIB>;
 #pragma unroll
     for (int q = 0; q < Sh::V4; q++)
-        out[q] = make_uint4(split_bytes(acc[4 * q + 0]), split_bytes(acc[4 * q + 1]), split_bytes(acc[4 * q + 2]),
-                            split_bytes(acc[4 * q + 3]));
+        out[q] = make_uint4(F::word(acc[4 * q + 0]), F::word(acc[4 * q + 1]), F::word(acc[4 * q + 2]),
+                            F::word(acc[4 * q + 3]));
 #pragma unroll
     for (int o = Sh::G; o < 32; o <<= 1)
 #pragma unroll
@@ -125,33 +148,41 @@ __device__ __forceinline__ void finish_groups(const SplitAcc (&acc)[4 * GatherSh
             y.y = __shfl_xor_sync(0xffffffffu, out[q].y, o);
             y.z = __shfl_xor_sync(0xffffffffu, out[q].z, o);
             y.w = __shfl_xor_sync(0xffffffffu, out[q].w, o);
-            out[q] = vmax4(out[q], y);
+            out[q] = F::max4(out[q], y);
         }
 }
 
 // Alg. 1 initialisation of node v: its counter gets rho in register j, where j
 // is the top p bits of the hash and rho the position of the first set bit of
 // the remaining 64-p bits (65-p if none).  The registers were zeroed before.
+// With 4-bit registers (nib) rho is clamped to 15 and register j is nibble
+// j % 2 of byte j / 2 (the low nibble first).
 __device__ __forceinline__ void init_node(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed,
-                                          uint32_t v) {
+                                          uint32_t v, bool nib = false) {
     const uint64_t h = splitmix64((uint64_t)v ^ seed);
     const uint32_t j = (uint32_t)(h >> (64 - p));
     const uint64_t w = h << p;
-    const uint32_t rho = w ? (uint32_t)__clzll((long long)w) + 1u : (uint32_t)(65 - p);
-    const uint32_t s = j / (uint32_t)S, o = j % (uint32_t)S;
-    regs[((uint64_t)s * n + v) * (uint64_t)S + o] = (uint8_t)rho;
+    uint32_t rho = w ? (uint32_t)__clzll((long long)w) + 1u : (uint32_t)(65 - p);
+    uint32_t byte = j, val = rho;
+    if (nib) {
+        rho = rho < 15u ? rho : 15u;
+        byte = j >> 1;
+        val = rho << (4u * (j & 1u));
+    }
+    const uint32_t s = byte / (uint32_t)S, o = byte % (uint32_t)S;
+    regs[((uint64_t)s * n + v) * (uint64_t)S + o] = (uint8_t)val;
 }
 
 // Fold the node's own slice into the gathered maximum, store it, and set
 // *flag if any register changed (one atomic per warp at most).
-template <int S>
-__device__ __forceinline__ void union_store(const SplitAcc (&acc)[4 * GatherShape<S>::V4],
+template <int S, bool NIB>
+__device__ __forceinline__ void union_store(const typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4],
                                             const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, uint32_t v,
                                             int lane, uint32_t *flag) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
     uint4 nb[Sh::V4];
-    finish_groups<S>(acc, nb);
+    finish_groups<S, NIB>(acc, nb);
     bool changed = false;
     if (g == 0) {
         const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
@@ -159,7 +190,7 @@ __device__ __forceinline__ void union_store(const SplitAcc (&acc)[4 * GatherShap
 #pragma unroll
         for (int q = 0; q < Sh::V4; q++) {
             const uint4 o4 = __ldg(own + q);
-            const uint4 res = vmax4(nb[q], o4);
+            const uint4 res = RegFmt<NIB>::max4(nb[q], o4);
             dst[q] = res;
             changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
         }
@@ -173,16 +204,14 @@ __device__ __forceinline__ void union_store(const SplitAcc (&acc)[4 * GatherShap
 // max_{w in N(v)} cur[w]) bytewise.  The warp decodes the node's LEB128 list
 // 32 bytes at a time (decode_window), stages the decoded ids in `ids` (32
 // entries of shared memory) and gathers each neighbour's S-byte slice.
-template <int S>
+template <int S, bool NIB = false>
 __device__ __forceinline__ void union_node_edges(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes,
                                                  const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
                                                  uint32_t v, uint32_t *ids, int lane, uint32_t *flag) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    SplitAcc acc[4 * Sh::V4];
-#pragma unroll
-    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
+    typename RegFmt<NIB>::Acc acc[4 * Sh::V4] = {};
     uint64_t pos = off[v];
     const uint64_t end = off[v + 1];
     uint32_t base = 0;
@@ -192,12 +221,12 @@ __device__ __forceinline__ void union_node_edges(const uint64_t *__restrict__ of
         if (T == 0) break;  // cannot happen on a validated graph; guarantees progress
         if ((T >> lane) & 1u) ids[__popc(T & lt_mask)] = r.id;
         __syncwarp();
-        gather_fold<S>(SliceRow<S>{cur}, ids, __popc(T), g, sub, acc);
+        gather_fold<S, NIB>(SliceRow<S>{cur}, ids, __popc(T), g, sub, acc);
         __syncwarp();
         base = r.next_base;
         pos += (uint64_t)r.advance;
     }
-    union_store<S>(acc, cur, nxt, v, lane, flag);
+    union_store<S, NIB>(acc, cur, nxt, v, lane, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,16 +286,14 @@ __device__ __forceinline__ bool lk_wait(LkStage &st, int slot, uint32_t parity) 
 // node's lookups stream through the warp's TMA stage (`st`, with its barrier
 // phases in `phase`) and each chunk's rows are gathered like the
 // per-neighbour union.
-template <int S>
+template <int S, bool NIB = false>
 __device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_off, const uint32_t *__restrict__ lk,
                                                 const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab,
                                                 uint8_t *__restrict__ nxt, uint32_t n, uint32_t v, LkStage &st,
                                                 uint32_t &phase, int lane, uint32_t *flag, int *err) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
-    SplitAcc acc[4 * Sh::V4];
-#pragma unroll
-    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
+    typename RegFmt<NIB>::Acc acc[4 * Sh::V4] = {};
     const TableRow<S> row{cur, tab, n};
     const uint64_t b = lk_off[v], e = lk_off[v + 1];
     if (b < e) {
@@ -290,7 +317,7 @@ __device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_
             const uint64_t s0 = a0 + (uint64_t)c * kLkChunk;
             const uint64_t lo = b > s0 ? b : s0;
             const uint64_t hi = (e < s0 + kLkChunk) ? e : s0 + kLkChunk;
-            if (hi > lo) gather_fold<S>(row, st.buf[slot] + (lo - s0), (int)(hi - lo), g, sub, acc);
+            if (hi > lo) gather_fold<S, NIB>(row, st.buf[slot] + (lo - s0), (int)(hi - lo), g, sub, acc);
             __syncwarp();
             if (lane == 0 && c + 2 < chunks) {
                 const uint64_t s2 = a0 + (uint64_t)(c + 2) * kLkChunk;
@@ -299,7 +326,7 @@ __device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_
             }
         }
     }
-    union_store<S>(acc, cur, nxt, v, lane, flag);
+    union_store<S, NIB>(acc, cur, nxt, v, lane, flag);
 }
 
 // Rows of one slice's sparse table built by one CTA (`table_item`), and the
@@ -319,7 +346,7 @@ constexpr int kTableSmemBytes = (16 + 15) * 1024;  // largest (B + 15) * S
 // the 16 rows of its widest window, writing T_1, T_2, T_3, T_4 as the window
 // reaches 2, 4, 8 and 16 rows (tab + (k-1) * n * S for level k).  All threads
 // of the CTA (256) take part.
-template <int S>
+template <int S, bool NIB = false>
 __device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict__ tab, uint32_t n, uint32_t r0,
                            uint8_t *buf) {
     using T = TableShape<S>;
@@ -337,7 +364,7 @@ __device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict_
         uint4 acc = b4[x];
 #pragma unroll
         for (int j = 1; j < 16; j++) {
-            acc = vmax4(acc, b4[x + j * T::C16]);
+            acc = RegFmt<NIB>::max4(acc, b4[x + j * T::C16]);
             if ((j & (j + 1)) == 0) {  // window of j + 1 = 2^k rows complete
                 const int k = 31 - __clz(j + 1);
                 if (i + (1u << k) <= n)
@@ -377,21 +404,24 @@ __device__ __forceinline__ void estimate_node(const uint8_t *__restrict__ regs, 
                                               double alpha_mm, const double *__restrict__ lc,
                                               const double *__restrict__ c_prev, double *__restrict__ c_cur,
                                               double *__restrict__ sum_d, uint32_t *__restrict__ inc_flag, uint32_t v,
-                                              int lane) {
+                                              int lane, bool nib = false) {
     const uint32_t m = 1u << p;
+    const uint32_t node_bytes = nib ? m / 2u : m;  // 4-bit registers: two per byte
     const int K = 65 - p;
     uint64_t lo = 0, hi = 0;
     uint32_t zeros = 0;
-    for (uint32_t q = lane; q * 16u < m; q += 32) {
+    const int fields = nib ? 8 : 4;  // registers per 32-bit word
+    const int width = nib ? 4 : 8;
+    const uint32_t fmask = nib ? 0xFu : 0xFFu;
+    for (uint32_t q = lane; q * 16u < node_bytes; q += 32) {
         const uint32_t r0 = q * 16u;
         const uint32_t s = r0 / (uint32_t)S, o = r0 % (uint32_t)S;
         const uint4 x = *reinterpret_cast<const uint4 *>(regs + ((uint64_t)s * n + v) * (uint64_t)S + o);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) {
-                const uint32_t M = (wv[i] >> (8 * b)) & 0xFFu;
+            for (int b = 0; b < fields; b++) {
+                const uint32_t M = (wv[i] >> (width * b)) & fmask;
                 if (M == 0) {
                     zeros++;
                 } else {

@@ -45,14 +45,14 @@ const std::vector<double> &lc_table(int p) {
 
 namespace {
 
-__global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed) {
+__global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed, int nib) {
     const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    init_node(regs, n, p, S, seed, (uint32_t)v);
+    init_node(regs, n, p, S, seed, (uint32_t)v, nib != 0);
 }
 
 // Eq. hll-union for one register slice, one warp per node (union_node_edges).
-template <int S>
+template <int S, bool NIB>
 __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restrict__ off,
                                                        const uint8_t *__restrict__ bytes,
                                                        const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
@@ -62,13 +62,13 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     const int wib = threadIdx.x >> 5;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
-    union_node_edges<S>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags);
+    union_node_edges<S, NIB>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags);
 }
 
 // Run-aware Eq. hll-union for one register slice, one warp per node
 // (union_node_runs, lookups staged by TMA), after the slice's sparse table has
 // been built.  flags[2] records a bounded wait that ran out.
-template <int S>
+template <int S, bool NIB>
 __global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__restrict__ lk_off,
                                                             const uint32_t *__restrict__ lk,
                                                             const uint8_t *__restrict__ cur,
@@ -83,22 +83,22 @@ __global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__re
     LkStage &st = stages[wib];
     lk_stage_init(st, lane);
     uint32_t phase = 0;
-    union_node_runs<S>(lk_off, lk, cur, tab, nxt, n, (uint32_t)warp, st, phase, lane, flags,
-                       reinterpret_cast<int *>(flags + 2));
+    union_node_runs<S, NIB>(lk_off, lk, cur, tab, nxt, n, (uint32_t)warp, st, phase, lane, flags,
+                            reinterpret_cast<int *>(flags + 2));
 }
 
 // One sparse-table level for a slice: out[i] = max(prev[i], prev[i + half]) for
 // i = 0 .. rows-1 (rows = N - 2*half + 1; later rows are never looked up).
 // One thread per 16-byte chunk.
 __global__ void hb_table_level_kernel(const uint8_t *__restrict__ prev, uint8_t *__restrict__ out, uint32_t rows,
-                                      uint32_t half, int S) {
+                                      uint32_t half, int S, int nib) {
     const uint32_t chunks = (uint32_t)S / 16u;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (uint64_t)rows * chunks) return;
     const uint64_t i = t / chunks, c = t % chunks;
     const uint4 a = __ldg(reinterpret_cast<const uint4 *>(prev + i * S) + c);
     const uint4 b = __ldg(reinterpret_cast<const uint4 *>(prev + (i + half) * S) + c);
-    reinterpret_cast<uint4 *>(out + i * S)[c] = vmax4(a, b);
+    reinterpret_cast<uint4 *>(out + i * S)[c] = nib ? RegFmt<true>::max4(a, b) : RegFmt<false>::max4(a, b);
 }
 
 // Microbenchmark twin of hb_union_kernel: rows drawn from a hash instead of
@@ -115,9 +115,7 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
     uint32_t *ids = s_ids + wib * 32;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     const int g = lane / Sh::G, sub = lane % Sh::G;
-    SplitAcc acc[4 * Sh::V4];
-#pragma unroll
-    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = SplitAcc{0u, 0u};
+    RegFmt<false>::Acc acc[4 * Sh::V4] = {};
     uint32_t x_acc = 0;
     for (uint32_t w = 0; w < windows; w++) {
         ids[lane] = (uint32_t)(splitmix64((warp * windows + w) * 32 + lane) % rows);
@@ -143,13 +141,13 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
                     for (int q = 0; q < Sh::V4; q++) x_acc ^= x[u][q].x ^ x[u][q].y ^ x[u][q].z ^ x[u][q].w;
             }
         } else {
-            gather_fold<S>(SliceRow<S>{buf}, ids, 32, g, sub, acc);
+            gather_fold<S, false>(SliceRow<S>{buf}, ids, 32, g, sub, acc);
         }
         __syncwarp();
     }
     if (!XOR) {
         uint4 r[Sh::V4];
-        finish_groups<S>(acc, r);
+        finish_groups<S, false>(acc, r);
         x_acc = r[0].x ^ r[0].y ^ r[0].z ^ r[0].w;
     }
     if (lane == 0) out[warp] = x_acc;
@@ -160,11 +158,11 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
 __global__ void hb_estimate_kernel(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, int t,
                                    double alpha_mm, const double *__restrict__ lc, const double *__restrict__ c_prev,
                                    double *__restrict__ c_cur, double *__restrict__ sum_d,
-                                   uint32_t *__restrict__ flags) {
+                                   uint32_t *__restrict__ flags, int nib) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= n) return;
-    estimate_node(regs, n, p, S, t, alpha_mm, lc, c_prev, c_cur, sum_d, flags + 1, (uint32_t)warp, lane);
+    estimate_node(regs, n, p, S, t, alpha_mm, lc, c_prev, c_cur, sum_d, flags + 1, (uint32_t)warp, lane, nib != 0);
 }
 
 // MD(v) = sum_d[v] / (N_v - 1) (Sec. 3.3), NaN when N_v <= 1; ball = c_t.
@@ -186,6 +184,8 @@ constexpr int kModeRuns = 2;     // one or two gathers per run of consecutive id
 struct Plan {
     int p = 10;
     uint32_t m = 1024;
+    int nib = 0;           // 4-bit registers, two per byte (the paper's packed format)
+    uint32_t node_bytes = 1024;  // register bytes per node: m, or m / 2 with 4-bit registers
     int S = 1024;          // slice bytes
     int slices = 1;
     int warps = 8;         // union kernel warps per CTA
@@ -206,6 +206,17 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->p = p;
     P->m = 1u << p;
     P->n = g->n;
+    const int bits = tune && tune->register_bits ? tune->register_bits : 8;
+    if (bits != 8 && bits != 4) {
+        set_error("register_bits = %d must be 8 or 4", bits);
+        return VGA_EINVAL;
+    }
+    if (bits == 4 && p < 5) {
+        set_error("4-bit registers need p >= 5 (got %d)", p);
+        return VGA_EINVAL;
+    }
+    P->nib = bits == 4;
+    P->node_bytes = P->nib ? P->m / 2 : P->m;
     const int req_mode = tune ? tune->union_mode : 0;
     if (req_mode < 0 || req_mode > kModeRuns) {
         set_error("union_mode = %d must be 0 (auto), 1 (per neighbour) or 2 (per run)", req_mode);
@@ -220,8 +231,8 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     const uint64_t rows_per_node = P->mode == kModeRuns ? (uint64_t)kRunLevels + 1 : 1;
     int S = tune ? tune->slice_bytes : 0;
     if (S != 0) {
-        if (S < 16 || S > 1024 || (S & (S - 1)) || (uint32_t)S > P->m) {
-            set_error("slice_bytes = %d must be a power of two in [16, min(2^p, 1024)]", S);
+        if (S < 16 || S > 1024 || (S & (S - 1)) || (uint32_t)S > P->node_bytes) {
+            set_error("slice_bytes = %d must be a power of two in [16, min(register bytes per node, 1024)]", S);
             return VGA_EINVAL;
         }
     } else {
@@ -229,17 +240,17 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device);
         uint64_t budget = (tune && tune->l2_budget_mb > 0) ? (uint64_t)tune->l2_budget_mb << 20
                                                            : (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
-        S = (int)std::min<uint32_t>(P->m, 1024u);
+        S = (int)std::min<uint32_t>(P->node_bytes, 1024u);
         while (S > 16 && (uint64_t)S * P->n * rows_per_node > budget) S >>= 1;
     }
     P->S = S;
-    P->slices = (int)(P->m / (uint32_t)S);
+    P->slices = (int)(P->node_bytes / (uint32_t)S);
     P->warps = (tune && tune->warps_per_cta > 0) ? tune->warps_per_cta : 8;
     if (P->warps > 16) {
         set_error("warps_per_cta = %d exceeds 16", P->warps);
         return VGA_EINVAL;
     }
-    const uint64_t regs = (uint64_t)P->n * P->m;
+    const uint64_t regs = (uint64_t)P->n * P->node_bytes;
     uint64_t o = 0;
     P->off_cur = o;   o = align256(o + regs);
     P->off_next = o;  o = align256(o + regs);
@@ -276,7 +287,7 @@ struct PendingTiming {
     int S, mode;
 };
 
-template <int SS>
+template <int SS, bool NIB>
 static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t *c, uint8_t *x, uint8_t *tab,
                                uint32_t *flags, cudaStream_t stream) {
     const unsigned blocks = (unsigned)((P.n + P.warps - 1) / P.warps);
@@ -290,14 +301,14 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
             uint8_t *out = tab + (uint64_t)(k - 1) * P.n * SS;
             const uint64_t threads = (uint64_t)rows * (SS / 16);
             hb_table_level_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(prev, out, rows,
-                                                                                         (uint32_t)(w >> 1), SS);
+                                                                                         (uint32_t)(w >> 1), SS, NIB);
             count_launch();
             prev = out;
         }
-        hb_union_runs_kernel<SS><<<blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
+        hb_union_runs_kernel<SS, NIB><<<blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
             g->d_lk_off, g->d_lk, c, tab, x, (uint32_t)P.n, flags);
     } else {
-        hb_union_kernel<SS><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
+        hb_union_kernel<SS, NIB><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
                                                                     flags);
     }
     count_launch();
@@ -316,13 +327,20 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
         }
         switch (P.S) {
-            case 16: launch_union_slice<16>(P, g, c, x, tab, flags, stream); break;
-            case 32: launch_union_slice<32>(P, g, c, x, tab, flags, stream); break;
-            case 64: launch_union_slice<64>(P, g, c, x, tab, flags, stream); break;
-            case 128: launch_union_slice<128>(P, g, c, x, tab, flags, stream); break;
-            case 256: launch_union_slice<256>(P, g, c, x, tab, flags, stream); break;
-            case 512: launch_union_slice<512>(P, g, c, x, tab, flags, stream); break;
-            case 1024: launch_union_slice<1024>(P, g, c, x, tab, flags, stream); break;
+            case 16: P.nib ? launch_union_slice<16, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<16, false>(P, g, c, x, tab, flags, stream); break;
+            case 32: P.nib ? launch_union_slice<32, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<32, false>(P, g, c, x, tab, flags, stream); break;
+            case 64: P.nib ? launch_union_slice<64, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<64, false>(P, g, c, x, tab, flags, stream); break;
+            case 128: P.nib ? launch_union_slice<128, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<128, false>(P, g, c, x, tab, flags, stream); break;
+            case 256: P.nib ? launch_union_slice<256, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<256, false>(P, g, c, x, tab, flags, stream); break;
+            case 512: P.nib ? launch_union_slice<512, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<512, false>(P, g, c, x, tab, flags, stream); break;
+            case 1024: P.nib ? launch_union_slice<1024, true>(P, g, c, x, tab, flags, stream)
+                             : launch_union_slice<1024, false>(P, g, c, x, tab, flags, stream); break;
             default:
                 set_error("internal: slice width %d", P.S);
                 return VGA_EINVAL;
@@ -372,19 +390,37 @@ static int launch_estimate(const Plan &P, const uint8_t *regs, int t, const doub
     const unsigned blocks = (unsigned)((P.n + warps - 1) / warps);
     const double alpha_mm = hll_alpha_host(P.p) * (double)P.m * (double)P.m;
     hb_estimate_kernel<<<blocks, warps * 32, 0, stream>>>(regs, (uint32_t)P.n, P.p, P.S, t, alpha_mm, lc, c_prev,
-                                                          c_cur, sum_d, flags);
+                                                          c_cur, sum_d, flags, P.nib);
     count_launch();
     VGA_CHECK_CUDA(cudaGetLastError());
     return VGA_OK;
 }
 
+// Registers of one pass into the caller's node-major uint8 trace slot.  With
+// 4-bit registers the packed slices are copied to a host buffer and unpacked
+// (register j of a node is nibble j % 2 of byte j / 2, low nibble first).
 static int copy_trace(const Plan &P, const uint8_t *regs, const double *c, int slot, uint8_t *trace_regs,
                       double *trace_c, cudaStream_t stream) {
     if (trace_regs) {
         uint8_t *dst = trace_regs + (uint64_t)slot * P.n * P.m;
-        for (int s = 0; s < P.slices; s++)
-            VGA_CHECK_CUDA(cudaMemcpy2DAsync(dst + (uint64_t)s * P.S, P.m, regs + (uint64_t)s * P.n * P.S, P.S, P.S,
-                                             P.n, cudaMemcpyDeviceToHost, stream));
+        if (!P.nib) {
+            for (int s = 0; s < P.slices; s++)
+                VGA_CHECK_CUDA(cudaMemcpy2DAsync(dst + (uint64_t)s * P.S, P.m, regs + (uint64_t)s * P.n * P.S, P.S,
+                                                 P.S, P.n, cudaMemcpyDeviceToHost, stream));
+        } else {
+            std::vector<uint8_t> packed((size_t)P.n * P.node_bytes);
+            for (int s = 0; s < P.slices; s++)
+                VGA_CHECK_CUDA(cudaMemcpy2DAsync(packed.data() + (uint64_t)s * P.S, P.node_bytes,
+                                                 regs + (uint64_t)s * P.n * P.S, P.S, P.S, P.n,
+                                                 cudaMemcpyDeviceToHost, stream));
+            VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+            for (uint64_t v = 0; v < P.n; v++)
+                for (uint32_t b = 0; b < P.node_bytes; b++) {
+                    const uint8_t x = packed[v * P.node_bytes + b];
+                    dst[v * P.m + 2 * b] = x & 0x0Fu;
+                    dst[v * P.m + 2 * b + 1] = x >> 4;
+                }
+        }
     }
     if (trace_c)
         VGA_CHECK_CUDA(cudaMemcpyAsync(trace_c + (uint64_t)slot * P.n, c, 8 * P.n, cudaMemcpyDeviceToHost, stream));
@@ -438,9 +474,9 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     VGA_CHECK_CUDA(cudaMemcpyAsync(lc, table.data(), 8 * table.size(), cudaMemcpyHostToDevice, stream));
     int t = 0;
     if (P.n > 0) {
-        VGA_CHECK_CUDA(cudaMemsetAsync(cur, 0, P.n * P.m, stream));
+        VGA_CHECK_CUDA(cudaMemsetAsync(cur, 0, P.n * P.node_bytes, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
-        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed);
+        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed, P.nib);
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
         VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0

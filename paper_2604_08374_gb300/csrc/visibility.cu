@@ -13,6 +13,7 @@
 // (device) one warp per source writes the bytes; then the ordinary load path
 // validates the stream and derives degrees.
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "vga_common.cuh"
@@ -59,6 +60,34 @@ std::vector<uint32_t> main_component_cells(int W, int H, const uint8_t *obst) {
     for (size_t c = 0; c < C; c++)
         if (best >= 0 && label[c] == best) cells.push_back((uint32_t)c);
     return cells;
+}
+
+// Hilbert-curve position of (x, y) in a 2^k x 2^k square (Sec. 3.2, optional
+// Hilbert reordering): walk the levels from the coarsest; each level adds its
+// quadrant's rank in curve order (0, 1, 2, 3 for lower-left, upper-left,
+// upper-right, lower-right in the current frame) times the quadrant size, then
+// maps the point into that quadrant's own frame (the lower quadrants are
+// transposed, the lower-right one also mirrored).
+uint64_t hilbert_position(int k, uint32_t x, uint32_t y) {
+    uint64_t d = 0;
+    for (int lvl = k - 1; lvl >= 0; lvl--) {
+        const uint32_t half = 1u << lvl;
+        const uint32_t qx = (x >> lvl) & 1u, qy = (y >> lvl) & 1u;
+        const uint32_t rank = qx ? (qy ? 2u : 3u) : (qy ? 1u : 0u);
+        d += (uint64_t)rank << (2 * lvl);
+        x &= half - 1u;
+        y &= half - 1u;
+        if (!qy) {
+            if (qx) {
+                x = half - 1u - x;
+                y = half - 1u - y;
+            }
+            const uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
 }
 
 __device__ __forceinline__ bool blocked_at(const uint32_t *__restrict__ bits, uint32_t idx) {
@@ -240,13 +269,23 @@ int vga_visibility_count(int W, int H, const uint8_t *obst, uint32_t *n_nodes) {
     return VGA_OK;
 }
 
-int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_node, vga_graph **out) {
+int vga_visibility_build_ordered(int W, int H, const uint8_t *obst, int order, uint64_t *cell_of_node,
+                                 vga_graph **out) {
     clear_error();
-    if (!obst || !out || W < 1 || H < 1 || W > kMaxSide || H > kMaxSide) {
-        set_error("vga_visibility_build: bad arguments (W=%d, H=%d, limit %d)", W, H, kMaxSide);
+    if (!obst || !out || W < 1 || H < 1 || W > kMaxSide || H > kMaxSide || (order != 0 && order != 1)) {
+        set_error("vga_visibility_build: bad arguments (W=%d, H=%d, order=%d, limit %d)", W, H, order, kMaxSide);
         return VGA_EINVAL;
     }
-    const std::vector<uint32_t> cells = main_component_cells(W, H, obst);
+    std::vector<uint32_t> cells = main_component_cells(W, H, obst);
+    if (order == 1) {
+        int k = 1;
+        while ((1 << k) < std::max(W, H)) k++;
+        std::vector<std::pair<uint64_t, uint32_t>> keyed(cells.size());
+        for (size_t i = 0; i < cells.size(); i++)
+            keyed[i] = {hilbert_position(k, cells[i] % (uint32_t)W, cells[i] / (uint32_t)W), cells[i]};
+        std::sort(keyed.begin(), keyed.end());
+        for (size_t i = 0; i < cells.size(); i++) cells[i] = keyed[i].second;
+    }
     const uint32_t n = (uint32_t)cells.size();
     if (cell_of_node)
         for (uint32_t v = 0; v < n; v++) cell_of_node[v] = cells[v];
@@ -322,6 +361,10 @@ int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_no
     d_off.release();
     d_bytes.release();
     return finish_graph_load(n, n_bytes, po, pb, nullptr, stream, out);
+}
+
+int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_node, vga_graph **out) {
+    return vga_visibility_build_ordered(W, H, obst, 0, cell_of_node, out);
 }
 
 }  // extern "C"

@@ -312,3 +312,63 @@ def test_metrics_match_oracle(vga):
     ref_run = oracle.metrics(ref_md, deg, comp_size=comp)
     fin = np.isfinite(ref_run)
     np.testing.assert_allclose(got_run[fin], ref_run[fin], rtol=MD_RTOL, atol=0)
+
+
+# ----------------------------------------------------------------------------
+# Hilbert node order (Sec. 3.2, optional Hilbert reordering)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("grid", ["tiny2", "rect40x23", "open9x7"])
+def test_hilbert_builder_and_hyperball(vga, grid):
+    if grid == "tiny2":
+        obst = workloads.tiny(2)
+    elif grid == "rect40x23":
+        obst = workloads.random_rectangles(40, 23, 9, (1, 7), seed=11)
+    else:
+        obst = workloads.open_grid(9, 7)
+    off, b, cells = oracle.build_graph(obst, order="hilbert")
+    g, gcells = vga.vga_visibility_build(obst, return_cells=True, order="hilbert")
+    with g:
+        o2, b2, _ = g.copy_csr()
+        assert np.array_equal(gcells.astype(np.int64), cells)
+        assert np.array_equal(o2, off) and np.array_equal(b2, b)
+        ref = oracle.hyperball(off, b, 10, 0, seed=2, trace=10)
+        for mode in (1, 2):
+            got = vga.hyperball_run_trace(g, 10, 0, seed=2, max_trace=10, union_mode=mode)
+            assert_same_run(got, ref)
+
+
+# ----------------------------------------------------------------------------
+# 4-bit registers (the paper's packed format, Sec. 3.3)
+# ----------------------------------------------------------------------------
+
+def _seed_with_clamp(n, p):
+    """A hash seed for which some node's rho exceeds 15 (the 4-bit clamp bites)."""
+    # the hash input is v ^ seed: seeds must reach above the node ids, or every
+    # seed only permutes the same few inputs
+    for k in range(1, 5000):
+        seed = k * 0x9E3779B97F4A7C15 % (1 << 63)
+        if any(oracle.hll_hash(v, seed, p)[1] > 15 for v in range(n)):
+            return seed
+    raise AssertionError("no seed found")
+
+
+@pytest.mark.parametrize("p,S,mode", [(10, 0, 1), (10, 0, 2), (8, 16, 2), (12, 256, 1), (5, 16, 1), (10, 64, 2)])
+def test_four_bit_registers_bit_exact(vga, p, S, mode):
+    _, off, b, cells = tiny_graph(3)
+    seed = _seed_with_clamp(len(cells), p)
+    ref = oracle.hyperball(off, b, p, 0, seed=seed, trace=12, reg_bits=4)
+    assert ref["regs"][0].max() == 15
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, p, 0, seed=seed, max_trace=12, slice_bytes=S, union_mode=mode,
+                                      register_bits=4)
+    assert_same_run(got, ref)
+
+
+def test_four_bit_rejects_small_p(vga):
+    _, off, b, _ = tiny_graph(1)
+    with vga.vga_graph_load(off, b) as g:
+        with pytest.raises(vga.VgaError):
+            vga.hyperball_run_trace(g, 4, 1, max_trace=1, register_bits=4)
+        with pytest.raises(vga.VgaError):
+            vga.hyperball_run_trace(g, 10, 1, max_trace=1, register_bits=6)

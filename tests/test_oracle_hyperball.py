@@ -153,3 +153,36 @@ def test_degenerate_graphs():
     # empty graph
     out = oracle.hyperball(np.zeros(1, np.uint64), np.zeros(0, np.uint8), 10, d=3)
     assert out["iterations"] == 0 and len(out["mean_depth"]) == 0
+
+
+@pytest.mark.parametrize("p", [5, 8, 10])
+def test_four_bit_registers_are_the_clamped_eight_bit_ones(tiny1, p):
+    # The 4-bit format (Sec. 3.3) clamps rho to 15.  Clamping commutes with
+    # the register-wise max, so after every pass the 4-bit registers must be
+    # the 8-bit ones clamped to 15 -- as long as the clamp never changes
+    # whether a pass changed anything, which the pass counts also check.
+    offsets, b, n, dist = tiny1
+    seed = 11
+    r8 = oracle.hyperball(offsets, b, p, 3, seed=seed, trace=3)
+    r4 = oracle.hyperball(offsets, b, p, 3, seed=seed, trace=3, reg_bits=4)
+    for t in range(r4["iterations"] + 1):
+        assert np.array_equal(r4["regs"][t], np.minimum(r8["regs"][t], 15))
+        assert r4["regs"][t].max() <= 15
+    # BFS closed form with clamped initial counters
+    R0 = oracle.hll_init(n, p, seed, reg_bits=4)
+    for v in range(0, n, 11):
+        ball = np.flatnonzero((dist[v] >= 0) & (dist[v] <= 2))
+        assert np.array_equal(r4["regs"][2][v], R0[ball].max(axis=0))
+
+
+def test_four_bit_clamp_is_hit_with_large_ids():
+    # a node whose rho exceeds 15 must come out as 15
+    import itertools
+    p = 10
+    for v in itertools.count():
+        j, rho = oracle.hll_hash(v, 0, p)
+        if rho > 15:
+            break
+    regs = oracle.hll_init(v + 1, p, 0, reg_bits=4)
+    assert regs[v, j] == 15
+    assert oracle.hll_init(v + 1, p, 0)[v, j] == rho
