@@ -85,6 +85,9 @@ def parse_args():
     ap.add_argument("--lane-priority", type=int, default=0, help="server: 1 favours the solo lane, -1 the batched")
     ap.add_argument("--solo-nodes", type=int, default=0, help="server: solo-lane threshold (0 = library default)")
     ap.add_argument("--backend", default="nccl")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the per-degree-bucket autotuner on the workload's graphs before timing")
+    ap.add_argument("--hub-lookups", type=int, default=0, help="force the run-aware hub threshold (0 = automatic)")
     return ap.parse_args()
 
 
@@ -323,6 +326,11 @@ def run_ours(args, dist: Dist):
     g = vga.vga_visibility_build(obst, order=args.order)
     build_s = time.perf_counter() - t0
     N, E, B = g.n_nodes, g.n_edges, g.n_bytes
+    tuned = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        tuned = vga.vga_autotune([g], p=args.p)
+        tuned = {"entries": tuned, "seconds": round(time.perf_counter() - t0, 2)}
     ws = torch.empty(vga.hyperball_workspace_bytes(g, args.p), dtype=torch.uint8, device=dev)
     md = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
     ball = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
@@ -332,7 +340,8 @@ def run_ours(args, dist: Dist):
         return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=ws, stream=stream,
                                      slice_bytes=args.slice_bytes, warps_per_cta=args.warps,
                                      union_mode=args.union_mode if union_mode is None else union_mode,
-                                     register_bits=0 if args.register_bits == 8 else args.register_bits)
+                                     register_bits=0 if args.register_bits == 8 else args.register_bits,
+                                     hub_lookups=args.hub_lookups)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -456,7 +465,7 @@ def run_ours(args, dist: Dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
                        "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode, "order": args.order,
-                       "register_bits": args.register_bits,
+                       "register_bits": args.register_bits, "autotune": tuned,
                        "parallelism": f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",
                        "graph_build_seconds": build_s},
@@ -498,6 +507,10 @@ def run_batch_mode(args, dist):
             for k, (g, sp) in enumerate(zip(graphs, specs))]
     nodes = [g.n_nodes for g in graphs]
     edges = [g.n_edges for g in graphs]
+    tuned = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        tuned = {"entries": vga.vga_autotune(graphs, p=10), "seconds": round(time.perf_counter() - t0, 2)}
     # one at a time (each with a reused workspace); first round warms caches and lookup lists
     ws_single = torch.empty(max(vga.hyperball_workspace_bytes(j["graph"], j["p"]) for j in jobs), dtype=torch.uint8,
                             device="cuda")
@@ -535,7 +548,7 @@ def run_batch_mode(args, dist):
             "data": "synthetic", "dtype": "u8",
             "config": {"workload": f"{n} medium-style grids, free cells log-uniform 1k-30k, per-graph seeds",
                        "nodes_total": int(sum(nodes)), "edges_total": int(sum(edges)),
-                       "graph_build_seconds": build_s},
+                       "graph_build_seconds": build_s, "autotune": tuned},
             "batched_seconds": timings["graph"], "batched_host_loop_seconds": timings["host"],
             "batched_host_loop_analyses_per_s": n / timings["host"],
             "one_at_a_time_seconds": single_s, "one_at_a_time_analyses_per_s": n / single_s,

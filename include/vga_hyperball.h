@@ -182,7 +182,11 @@ typedef struct vga_tuning {
                             two registers per byte, rho clamped to 15, p >= 5).  4-bit
                             runs are not bit-comparable with 8-bit ones wherever a rho
                             above 15 occurs; they match the same clamp applied alone.      */
-    int reserved[3];
+    int hub_lookups;     /* mode 2: a node with more range lookups than this is split into
+                            chunks of at most this many, each folded by its own warp and
+                            merged by a word-wise atomic max (0 = automatic: half of one
+                            warp's even share of the lookups, at least 2048)              */
+    int reserved[2];
 } vga_tuning;
 
 /*
@@ -444,6 +448,64 @@ int vga_profile_read(vga_profile *out);
  */
 int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, int consumer, void *stream,
                      double *gb_per_s);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuner (the paper tunes nothing; its kernel uses one fixed launch      */
+/* shape, Sec. 3.4).  Launch choices of the union are picked per degree      */
+/* bucket by timing the candidates on the caller's own graphs.               */
+/* ---------------------------------------------------------------------- */
+
+/* Tuned launch choices for one degree bucket. */
+typedef struct vga_tune_entry {
+    int degree_log2;     /* bucket: graphs whose average degree E/N has floor(log2) = this  */
+    int union_mode;      /* 1 per neighbour, 2 per run                                       */
+    int slice_bytes;     /* slice width; applied as an upper bound, lowered when the slice
+                            (and in mode 2 its four sparse-table levels) would not fit the
+                            whole L2 for a larger graph of the bucket                        */
+    int warps_per_cta;   /* union CTA size in warps                                          */
+    int hub_lookups;     /* mode 2 hub threshold (0 = automatic)                             */
+    int p;               /* precision the entry was tuned at                                 */
+    double geu_per_s;    /* winner's union throughput on the tuning graph, 1e9 edges/s       */
+    uint64_t tuned_edges;/* E of the tuning graph                                            */
+    int reserved[2];
+} vga_tune_entry;
+
+/*
+ * vga_autotune -- time the union's launch choices on the given graphs and
+ * return one entry per degree bucket present.
+ *   graphs, n_graphs  graphs on the current device (n_graphs >= 1).  Each
+ *                     bucket is tuned on its graph with the most edges.
+ *   p                 precision to tune at (4..16).
+ *   stream            cudaStream_t or NULL.
+ *   out, max_out      caller-owned array of entries; *n_out gets the count
+ *                     (at most max_out; VGA_EINVAL if more buckets are present).
+ *   install           1: also install the result as the process-wide table
+ *                     (vga_tune_table_set), 0: only return it.
+ * Search per bucket: every union variant and power-of-two slice width that fits
+ * the L2 at 8 warps per CTA with the automatic hub threshold; then CTA sizes 4
+ * and 16 for the best pair; then, in mode 2, hub thresholds of 1/2 and 1/4 of
+ * the automatic one.  Each candidate runs two union passes (d = 2) twice and
+ * keeps its faster run; a run of each variant first builds any lookup list.
+ * Every candidate computes the same registers (they differ only in launch shape).
+ */
+int vga_autotune(const vga_graph *const *graphs, int n_graphs, int p, void *stream, vga_tune_entry *out,
+                 int max_out, int *n_out, int install);
+
+/*
+ * vga_tune_table_set -- install entries as the process-wide tuning table
+ * (copied; n = 0 clears it).  While a table is installed, every analysis whose
+ * graph falls in a tabled bucket takes that entry's choices for each tuning
+ * field the caller leaves at 0 (hyperball_run, hyperball_run_dev with NULL or
+ * partial tuning, hyperball_run_batch and the server; the batched engine uses
+ * union_mode and slice_bytes).  hyperball_workspace_bytes follows the table
+ * too: query it after the table is set.  Entries with union_mode outside 1..2,
+ * slice_bytes not a power of two in [16, 1024] or warps_per_cta outside 0..16
+ * give VGA_EINVAL.
+ */
+int vga_tune_table_set(const vga_tune_entry *entries, int n);
+
+/* Copy the installed table into out (at most max_out entries); *n_out gets its size. */
+int vga_tune_table_get(vga_tune_entry *out, int max_out, int *n_out);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,8 @@ vp, i32, u32, u64, i64, f64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_i
 
 class VgaTuning(C.Structure):
     _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
-                ("union_mode", C.c_int), ("register_bits", C.c_int), ("reserved", C.c_int * 3)]
+                ("union_mode", C.c_int), ("register_bits", C.c_int), ("hub_lookups", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class VgaJob(C.Structure):
@@ -55,6 +56,16 @@ class VgaProfile(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("union_launches", C.c_uint64), ("union_ms", C.c_double),
                 ("union_edges", C.c_uint64), ("union_gather_bytes", C.c_uint64), ("union_hbm_bytes", C.c_uint64),
                 ("slice_bytes", C.c_int), ("union_mode", C.c_int), ("reserved", C.c_int * 2)]
+
+
+class VgaTuneEntry(C.Structure):
+    _fields_ = [("degree_log2", C.c_int), ("union_mode", C.c_int), ("slice_bytes", C.c_int),
+                ("warps_per_cta", C.c_int), ("hub_lookups", C.c_int), ("p", C.c_int), ("geu_per_s", C.c_double),
+                ("tuned_edges", C.c_uint64), ("reserved", C.c_int * 2)]
+
+
+TUNE_FIELDS = ("degree_log2", "union_mode", "slice_bytes", "warps_per_cta", "hub_lookups", "p", "geu_per_s",
+               "tuned_edges")
 
 
 SIGNATURES = {
@@ -89,6 +100,9 @@ SIGNATURES = {
     "vga_profile_reset": ([], i32),
     "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
     "vga_bench_gather": ([u64, i32, u64, i32, vp, C.POINTER(f64)], i32),
+    "vga_autotune": ([C.POINTER(vp), i32, i32, vp, C.POINTER(VgaTuneEntry), i32, C.POINTER(i32), i32], i32),
+    "vga_tune_table_set": ([C.POINTER(VgaTuneEntry), i32], i32),
+    "vga_tune_table_get": ([C.POINTER(VgaTuneEntry), i32, C.POINTER(i32)], i32),
 }
 
 _lock = threading.Lock()
@@ -138,12 +152,12 @@ def _ptr(a) -> int | None:
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
-def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0, register_bits=0):
-    if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode or register_bits):
+def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0, register_bits=0, hub_lookups=0):
+    if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode or register_bits or hub_lookups):
         return None
     t = VgaTuning()
     t.slice_bytes, t.warps_per_cta, t.l2_budget_mb, t.union_mode = slice_bytes, warps_per_cta, l2_budget_mb, union_mode
-    t.register_bits = register_bits
+    t.register_bits, t.hub_lookups = register_bits, hub_lookups
     return C.pointer(t)
 
 
@@ -296,13 +310,15 @@ def hyperball_workspace_bytes(g: Graph, p: int) -> int:
 
 def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
                       workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
-                      l2_budget_mb: int = 0, union_mode: int = 0, register_bits: int = 0) -> int:
+                      l2_budget_mb: int = 0, union_mode: int = 0, register_bits: int = 0,
+                      hub_lookups: int = 0) -> int:
     """Algorithm 1 into device tensors (float64, N each); returns passes run."""
     it = C.c_int()
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
-                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode, register_bits)))
+                                   _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode, register_bits,
+                                           hub_lookups)))
     return it.value
 
 
@@ -318,7 +334,8 @@ def hyperball_run_noalloc(g: Graph, p: int, d: int, seed: int, mean_depth_dev, b
 
 
 def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0, max_trace: int = 8,
-                        slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0):
+                        slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
+                        hub_lookups: int = 0):
     """Run with per-pass register and estimate dumps (bit-exact checks).
 
     Returns dict(mean_depth, ball, iterations, regs[(max_trace+1), N, m], c[(max_trace+1), N])."""
@@ -331,7 +348,7 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
     _check(lib().hyperball_run_trace(g.handle, p, d, seed, conv_mode, _ptr(md), _ptr(ball), C.byref(it),
                                      _ptr(regs), _ptr(cc), max_trace,
                                      _tuning(slice_bytes, warps_per_cta, union_mode=union_mode,
-                                             register_bits=register_bits)))
+                                             register_bits=register_bits, hub_lookups=hub_lookups)))
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}
@@ -459,3 +476,37 @@ def vga_bench_gather(resident_bytes: int, chunk_bytes: int, gathers: int, consum
     _check(lib().vga_bench_gather(resident_bytes, chunk_bytes, gathers, consumer, _stream_ptr(stream),
                                   C.byref(out)))
     return out.value
+
+
+def _entries_out(arr, n):
+    return [{f: getattr(arr[k], f) for f in TUNE_FIELDS} for k in range(n)]
+
+
+def vga_autotune(graphs, p: int = 10, stream=None, install: bool = True):
+    """Time the union's launch choices on `graphs` and return one entry (dict)
+    per degree bucket; with install=True they also become the process-wide
+    table consulted by every analysis that leaves its tuning fields at 0."""
+    gs = list(graphs)
+    handles = (C.c_void_p * max(len(gs), 1))(*[g.handle.value for g in gs])
+    out = (VgaTuneEntry * 64)()
+    n = C.c_int()
+    _check(lib().vga_autotune(handles, len(gs), p, _stream_ptr(stream), out, 64, C.byref(n), int(install)))
+    return _entries_out(out, n.value)
+
+
+def vga_tune_table_set(entries):
+    """Install tuning entries (dicts with TUNE_FIELDS keys); [] clears the table."""
+    arr = (VgaTuneEntry * max(len(entries), 1))()
+    for k, e in enumerate(entries):
+        for f in TUNE_FIELDS:
+            if f in e:
+                setattr(arr[k], f, e[f])
+    _check(lib().vga_tune_table_set(arr, len(entries)))
+
+
+def vga_tune_table_get():
+    """The installed tuning table as a list of dicts."""
+    out = (VgaTuneEntry * 64)()
+    n = C.c_int()
+    _check(lib().vga_tune_table_get(out, 64, C.byref(n)))
+    return _entries_out(out, min(n.value, 64))

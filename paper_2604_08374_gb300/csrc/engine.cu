@@ -508,7 +508,13 @@ int plan_batch(const vga_job *jobs, int n_jobs, int slice_cap, BatchPlan *B) {
             return VGA_EINVAL;
         }
         if (jb.graph->n == 0) continue;
-        const JobLayout L = job_layout(jb.graph->n, jb.p, slice_cap, budget, jb.union_mode);
+        // a job that leaves the variant (and the call the width) automatic takes
+        // the autotuner's entry for its degree bucket, if one is installed
+        vga_tune_entry te{};
+        const bool tabled = tune_table_lookup(jb.graph, &te);
+        const int mode = jb.union_mode ? jb.union_mode : (tabled ? te.union_mode : 0);
+        const int cap = slice_cap ? slice_cap : (tabled ? te.slice_bytes : 0);
+        const JobLayout L = job_layout(jb.graph->n, jb.p, cap, budget, mode);
         B->idx.push_back(i);
         B->lay.push_back(L);
         B->job_off.push_back(o);

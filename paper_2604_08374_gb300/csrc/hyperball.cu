@@ -65,11 +65,12 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     union_node_edges<S, NIB>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags);
 }
 
-// Run-aware Eq. hll-union for one register slice, one warp per node
-// (union_node_runs, lookups staged by TMA), after the slice's sparse table has
-// been built.  flags[2] records a bounded wait that ran out.
+// Run-aware Eq. hll-union for one register slice, one warp per work item
+// (RunItem: a whole node, or one chunk of a split hub), lookups staged by TMA,
+// after the slice's sparse table has been built.  flags[2] records a bounded
+// wait that ran out.
 template <int S, bool NIB>
-__global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__restrict__ lk_off,
+__global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__restrict__ items, uint64_t n_items,
                                                             const uint32_t *__restrict__ lk,
                                                             const uint8_t *__restrict__ cur,
                                                             const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt,
@@ -79,12 +80,18 @@ __global__ void __launch_bounds__(512) hb_union_runs_kernel(const uint64_t *__re
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    if (warp >= n) return;
+    if (warp >= n_items) return;
+    const RunItem it = items[warp];
     LkStage &st = stages[wib];
     lk_stage_init(st, lane);
     uint32_t phase = 0;
-    union_node_runs<S, NIB>(lk_off, lk, cur, tab, nxt, n, (uint32_t)warp, st, phase, lane, flags,
-                            reinterpret_cast<int *>(flags + 2));
+    int *err = reinterpret_cast<int *>(flags + 2);
+    typename RegFmt<NIB>::Acc acc[4 * GatherShape<S>::V4] = {};
+    union_range_runs<S, NIB>(lk, cur, tab, n, it.b, it.b + it.cnt, st, phase, lane, acc, err);
+    if (it.v & kHubChunk)
+        union_store_hub<S, NIB>(acc, cur, nxt, it.v & ~kHubChunk, lane, flags, err);
+    else
+        union_store<S, NIB>(acc, cur, nxt, it.v, lane, flags);
 }
 
 // One sparse-table level for a slice: out[i] = max(prev[i], prev[i + half]) for
@@ -190,6 +197,9 @@ struct Plan {
     int slices = 1;
     int warps = 8;         // union kernel warps per CTA
     int mode = kModeRuns;  // union variant
+    uint32_t hub_req = 0;  // runs mode: requested hub threshold (0 = automatic)
+    uint32_t hub = 0;      // runs mode: nodes with more lookups than this are split across warps
+    RunItemList items;     // runs mode: the union's work list for `hub`
     uint64_t n = 0;
     // workspace layout (byte offsets, 256-aligned)
     uint64_t off_cur = 0, off_next = 0, off_c0 = 0, off_c1 = 0, off_sum = 0, off_lc = 0, off_flags = 0, off_tab = 0,
@@ -197,6 +207,18 @@ struct Plan {
 };
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Hub threshold of the run-aware union (lookups per work item).  Automatic:
+// half of one warp's even share of the slice's lookups when every SM holds 64
+// warps, and at least 2048, so only nodes that would outlast the rest of the
+// launch are split.
+static uint32_t hub_threshold(const vga_graph *g, uint32_t requested) {
+    if (requested > 0) return requested;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    const uint64_t share = g->lk_total / ((uint64_t)(sms > 0 ? sms : 1) * 64);
+    return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(share / 2, 2048), 0x7fffffffull);
+}
 
 static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P) {
     if (p < 4 || p > 16) {
@@ -217,7 +239,11 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     }
     P->nib = bits == 4;
     P->node_bytes = P->nib ? P->m / 2 : P->m;
-    const int req_mode = tune ? tune->union_mode : 0;
+    // fields left at 0 come from the autotuner's table entry for the graph's
+    // degree bucket, if one is installed, else from the built-in defaults
+    vga_tune_entry te{};
+    const bool tabled = tune_table_lookup(g, &te);
+    const int req_mode = (tune && tune->union_mode) ? tune->union_mode : 0;
     if (req_mode < 0 || req_mode > kModeRuns) {
         set_error("union_mode = %d must be 0 (auto), 1 (per neighbour) or 2 (per run)", req_mode);
         return VGA_EINVAL;
@@ -226,7 +252,9 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         set_error("union_mode 2 supports at most 2^29 nodes (graph has %u)", g->n);
         return VGA_EINVAL;
     }
-    P->mode = req_mode ? req_mode : ((uint64_t)g->n <= kRunMaxNodes ? kModeRuns : kModePerEdge);
+    const bool runs_ok = (uint64_t)g->n <= kRunMaxNodes;
+    P->mode = req_mode ? req_mode
+                       : (tabled && te.union_mode == kModePerEdge) || !runs_ok ? kModePerEdge : kModeRuns;
     // rows of counters the union reads per slice: the slice, plus the sparse-table levels in runs mode
     const uint64_t rows_per_node = P->mode == kModeRuns ? (uint64_t)kRunLevels + 1 : 1;
     int S = tune ? tune->slice_bytes : 0;
@@ -238,18 +266,31 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     } else {
         int l2 = 0;
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device);
+        const uint64_t l2_bytes = (uint64_t)(l2 > 0 ? l2 : (64 << 20));
+        // a tabled width is an upper bound; the slice must still fit the whole L2
+        const bool tabled_S = tabled && te.slice_bytes > 0 && !(tune && tune->l2_budget_mb > 0);
         uint64_t budget = (tune && tune->l2_budget_mb > 0) ? (uint64_t)tune->l2_budget_mb << 20
-                                                           : (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
-        S = (int)std::min<uint32_t>(P->node_bytes, 1024u);
+                          : tabled_S                       ? l2_bytes
+                                                           : l2_bytes * 6 / 10;
+        S = (int)std::min<uint32_t>(P->node_bytes, tabled_S ? (uint32_t)std::min(te.slice_bytes, 1024) : 1024u);
         while (S > 16 && (uint64_t)S * P->n * rows_per_node > budget) S >>= 1;
     }
     P->S = S;
     P->slices = (int)(P->node_bytes / (uint32_t)S);
-    P->warps = (tune && tune->warps_per_cta > 0) ? tune->warps_per_cta : 8;
+    P->warps = (tune && tune->warps_per_cta > 0) ? tune->warps_per_cta
+               : (tabled && te.warps_per_cta > 0)     ? te.warps_per_cta
+                                                      : 8;
     if (P->warps > 16) {
         set_error("warps_per_cta = %d exceeds 16", P->warps);
         return VGA_EINVAL;
     }
+    if (tune && tune->hub_lookups < 0) {
+        set_error("hub_lookups = %d must be >= 0", tune->hub_lookups);
+        return VGA_EINVAL;
+    }
+    P->hub_req = (tune && tune->hub_lookups > 0) ? (uint32_t)tune->hub_lookups
+                 : (tabled && te.hub_lookups > 0) ? (uint32_t)te.hub_lookups
+                                                  : 0u;
     const uint64_t regs = (uint64_t)P->n * P->node_bytes;
     uint64_t o = 0;
     P->off_cur = o;   o = align256(o + regs);
@@ -293,6 +334,7 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
     const unsigned blocks = (unsigned)((P.n + P.warps - 1) / P.warps);
     const size_t smem = (size_t)P.warps * 32 * sizeof(uint32_t);
     if (P.mode == kModeRuns) {
+        const unsigned item_blocks = (unsigned)((P.items.count + P.warps - 1) / P.warps);
         const uint8_t *prev = c;
         for (int k = 1; k <= kRunLevels; k++) {
             const uint64_t w = 1ull << k;
@@ -305,8 +347,8 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
             count_launch();
             prev = out;
         }
-        hb_union_runs_kernel<SS, NIB><<<blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
-            g->d_lk_off, g->d_lk, c, tab, x, (uint32_t)P.n, flags);
+        hb_union_runs_kernel<SS, NIB><<<item_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
+            P.items.items, P.items.count, g->d_lk, c, tab, x, (uint32_t)P.n, flags);
     } else {
         hb_union_kernel<SS, NIB><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
                                                                     flags);
@@ -364,12 +406,17 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
     return VGA_OK;
 }
 
-static void settle_timings(std::vector<PendingTiming> &timings) {
+// Read the union timings of a run: into the profile counters when profiling is
+// on, and summed into *sum_ms when it is given.
+static void settle_timings(std::vector<PendingTiming> &timings, bool to_profile, double *sum_ms) {
     ProfileState &ps = prof();
     std::lock_guard<std::mutex> lock(ps.mu);
     for (PendingTiming &pt : timings) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pt.start, pt.stop) == cudaSuccess) {
+        const bool ok = cudaEventElapsedTime(&ms, pt.start, pt.stop) == cudaSuccess;
+        if (sum_ms && !ok) *sum_ms = -1.0;
+        if (sum_ms && ok && *sum_ms >= 0.0) *sum_ms += ms;
+        if (to_profile && ok) {
             ps.acc.union_launches++;
             ps.acc.union_ms += ms;
             ps.acc.union_edges += pt.edges;
@@ -429,7 +476,7 @@ static int copy_trace(const Plan &P, const uint8_t *regs, const double *c, int s
 
 static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *md_dev, double *ball_dev,
                     int *iterations, void *ws, uint64_t ws_bytes, cudaStream_t stream, const vga_tuning *tune,
-                    uint8_t *trace_regs, double *trace_c, int max_trace) {
+                    uint8_t *trace_regs, double *trace_c, int max_trace, double *union_ms = nullptr) {
     if (!g) {
         set_error("null graph");
         return VGA_EINVAL;
@@ -458,23 +505,33 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     double *lc = reinterpret_cast<double *>(base + P.off_lc);
     uint32_t *flags = reinterpret_cast<uint32_t *>(base + P.off_flags);
     uint8_t *tab = base + P.off_tab;
-    if (P.mode == kModeRuns && P.n > 0) VGA_TRY(ensure_run_lookups(g, stream));
+    if (P.mode == kModeRuns && P.n > 0) {
+        VGA_TRY(ensure_run_lookups(g, stream));
+        P.hub = hub_threshold(g, P.hub_req);
+        VGA_TRY(ensure_run_items(g, P.hub, stream, &P.items));
+    }
 
     bool profiling;
     {
         std::lock_guard<std::mutex> lock(prof().mu);
         profiling = prof().enabled;
     }
+    if (union_ms) *union_ms = 0.0;
+    const bool timed = profiling || union_ms;
     std::vector<PendingTiming> timings;
     struct Settle {
         std::vector<PendingTiming> &t;
-        ~Settle() { settle_timings(t); }
-    } settle{timings};
+        bool to_profile;
+        double *sum;
+        ~Settle() { settle_timings(t, to_profile, sum); }
+    } settle{timings, profiling, union_ms};
     const std::vector<double> &table = lc_table(p);
     VGA_CHECK_CUDA(cudaMemcpyAsync(lc, table.data(), 8 * table.size(), cudaMemcpyHostToDevice, stream));
     int t = 0;
     if (P.n > 0) {
         VGA_CHECK_CUDA(cudaMemsetAsync(cur, 0, P.n * P.node_bytes, stream));
+        // split hubs merge into next[v] by atomic max: it must start below the result
+        if (P.items.hubs) VGA_CHECK_CUDA(cudaMemsetAsync(nxt, 0, P.n * P.node_bytes, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
         hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed, P.nib);
         count_launch();
@@ -485,7 +542,7 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 12, stream));
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
-            VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, profiling ? &timings : nullptr));
+            VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, timed ? &timings : nullptr));
             VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
             if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
             VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 12, cudaMemcpyDeviceToHost, stream));
@@ -508,6 +565,22 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     if (iterations) *iterations = t;
     return VGA_OK;
 }
+
+}  // namespace
+
+// One run with the union launches timed (the autotuner's measurement):
+// outputs go to library-owned buffers, *union_ms gets the summed device time
+// of the union slices (sparse tables included).
+int run_timed(const vga_graph *g, int p, int d, uint64_t seed, const vga_tuning *tune, cudaStream_t stream,
+              double *union_ms, int *iterations) {
+    DeviceBuffer out;
+    VGA_TRY(out.alloc(16 * (size_t)(g->n ? g->n : 1)));
+    double *md = out.as<double>();
+    return run_impl(g, p, d, seed, 0, md, md + g->n, iterations, nullptr, 0, stream, tune, nullptr, nullptr, -1,
+                    union_ms);
+}
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // Fixed scratch for callers that must not allocate device memory

@@ -155,7 +155,48 @@ int ensure_run_lookups(const vga_graph *g, cudaStream_t stream) {
     g->d_lk_off = static_cast<uint64_t *>(d_off.release());
     g->d_lk = static_cast<uint32_t *>(d_lk.release());
     g->lk_total = total;
+    g->h_lk_off = std::move(h_off);
     g->lk_ready = true;
+    return VGA_OK;
+}
+
+int ensure_run_items(const vga_graph *g, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out) {
+    VGA_TRY(ensure_run_lookups(g, stream));
+    std::lock_guard<std::mutex> lock(g->lk_mu);
+    if (hub_lookups == 0) hub_lookups = 1;
+    for (const vga_graph::RunItemSet &r : g->lk_items)
+        if (r.hub_lookups == hub_lookups) {
+            *out = RunItemList{static_cast<const RunItem *>(r.d_items), r.count, r.hub_items, r.hubs};
+            return VGA_OK;
+        }
+    const std::vector<uint64_t> &off = g->h_lk_off;
+    std::vector<RunItem> items;
+    items.reserve((size_t)g->n);
+    uint32_t hubs = 0;
+    for (uint32_t v = 0; v < g->n; v++) {
+        const uint64_t cnt = off[v + 1] - off[v];
+        if (cnt <= hub_lookups) continue;
+        const uint64_t k = (cnt + hub_lookups - 1) / hub_lookups;  // chunks of at most hub_lookups
+        for (uint64_t c = 0; c < k; c++) {
+            const uint64_t lo = off[v] + cnt * c / k, hi = off[v] + cnt * (c + 1) / k;
+            items.push_back(RunItem{v | kHubChunk, (uint32_t)(hi - lo), lo});
+        }
+        hubs++;
+    }
+    const uint64_t hub_items = items.size();
+    for (uint32_t v = 0; v < g->n; v++) {
+        const uint64_t cnt = off[v + 1] - off[v];
+        if (cnt <= hub_lookups) items.push_back(RunItem{v, (uint32_t)cnt, off[v]});
+    }
+    DeviceBuffer d;
+    VGA_TRY(d.alloc(sizeof(RunItem) * (items.empty() ? 1 : items.size())));
+    if (!items.empty())
+        VGA_CHECK_CUDA(cudaMemcpyAsync(d.ptr, items.data(), sizeof(RunItem) * items.size(), cudaMemcpyHostToDevice,
+                                       stream));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));  // the host vector goes out of scope
+    g->lk_items.push_back(vga_graph::RunItemSet{hub_lookups, (uint64_t)items.size(), hub_items, hubs, d.release()});
+    const vga_graph::RunItemSet &r = g->lk_items.back();
+    *out = RunItemList{static_cast<const RunItem *>(r.d_items), r.count, r.hub_items, r.hubs};
     return VGA_OK;
 }
 

@@ -33,6 +33,15 @@ struct vga_graph {
     mutable uint32_t *d_lk = nullptr;      // lk_total
     mutable uint64_t lk_total = 0;
     mutable bool lk_ready = false;
+    mutable std::vector<uint64_t> h_lk_off;  // host copy of d_lk_off
+    // Work lists of the run-aware union, one per hub threshold (ensure_run_items).
+    struct RunItemSet {
+        uint32_t hub_lookups;
+        uint64_t count, hub_items;
+        uint32_t hubs;
+        void *d_items;
+    };
+    mutable std::vector<RunItemSet> lk_items;
 };
 
 namespace vga {
@@ -131,6 +140,34 @@ constexpr int kRunLevels = 4;        // windows of 1, 2, 4, 8, 16 rows
 constexpr uint32_t kLkIndexBits = 29;
 constexpr uint32_t kLkIndexMask = (1u << kLkIndexBits) - 1u;
 constexpr uint64_t kRunMaxNodes = 1ull << kLkIndexBits;
+
+// One warp's work in the run-aware union: the lookups lk[b .. b + cnt) of node
+// v & ~kHubChunk.  A node with more lookups than the hub threshold is split
+// into several items flagged kHubChunk, each folding part of the node's
+// lookups; they merge into next[v] with a word-wise atomic max.
+struct RunItem {
+    uint32_t v;
+    uint32_t cnt;
+    uint64_t b;
+};
+constexpr uint32_t kHubChunk = 1u << 31;
+
+// Work list of the run-aware union for hub threshold `hub_lookups` (> 0),
+// built on first use and held by the graph: the hub chunks first (so that the
+// longest work starts first), then every other node in id order.
+struct RunItemList {
+    const RunItem *items = nullptr;
+    uint64_t count = 0, hub_items = 0;
+    uint32_t hubs = 0;
+};
+int ensure_run_items(const vga_graph *g, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out);
+
+// Autotuner table (autotune.cu): the installed entry for g's degree bucket.
+bool tune_table_lookup(const vga_graph *g, vga_tune_entry *out);
+
+// One run with the union launches timed (hyperball.cu), for the autotuner.
+int run_timed(const vga_graph *g, int p, int d, uint64_t seed, const vga_tuning *tune, cudaStream_t stream,
+              double *union_ms, int *iterations);
 
 // Build the graph's lookup list on first use (thread-safe); no-op afterwards.
 int ensure_run_lookups(const vga_graph *g, cudaStream_t stream);

@@ -252,6 +252,7 @@ void vga_graph_free(vga_graph *g) {
     if (g->d_comp) cudaFree(g->d_comp);
     if (g->d_lk_off) cudaFree(g->d_lk_off);
     if (g->d_lk) cudaFree(g->d_lk);
+    for (const vga_graph::RunItemSet &r : g->lk_items) cudaFree(r.d_items);
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     delete g;
 }

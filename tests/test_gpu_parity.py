@@ -372,3 +372,59 @@ def test_four_bit_rejects_small_p(vga):
             vga.hyperball_run_trace(g, 4, 1, max_trace=1, register_bits=4)
         with pytest.raises(vga.VgaError):
             vga.hyperball_run_trace(g, 10, 1, max_trace=1, register_bits=6)
+
+
+# ----------------------------------------------------------------------------
+# split hubs in the run-aware union
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("hub,S,bits", [(1, 0, 8), (3, 64, 8), (17, 16, 8), (64, 0, 8), (2, 32, 4), (9, 0, 4)])
+def test_hub_split_bit_exact(vga, hub, S, bits):
+    # a small threshold splits most nodes into chunks that merge by atomic max
+    _, off, b, _ = tiny_graph(2)
+    p = 8
+    ref = oracle.hyperball(off, b, p, 0, seed=5, trace=12, reg_bits=bits)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, p, 0, seed=5, max_trace=12, slice_bytes=S, union_mode=2,
+                                      register_bits=0 if bits == 8 else bits, hub_lookups=hub)
+    assert_same_run(got, ref)
+
+
+def _skewed_csr(n=12000, seed=0):
+    """Directed CSR with a few hubs far above the rest: hub h sees every other
+    node of a long range (single-id runs, so one lookup per neighbour); the
+    other nodes see a few short runs."""
+    rng = np.random.default_rng(seed)
+    lists = []
+    hubs = {0: 2, 5000: 3, 11999: 2}
+    for v in range(n):
+        if v in hubs:
+            ids = np.arange(1 if v == 0 else 0, n, hubs[v])
+        else:
+            starts = rng.integers(0, n - 8, size=4)
+            ids = np.unique(np.concatenate([np.arange(s, s + rng.integers(1, 8)) for s in starts]))
+        ids = ids[ids != v]
+        lists.append(ids.astype(np.uint32))
+    row_ptr = np.zeros(n + 1, np.uint64)
+    row_ptr[1:] = np.cumsum([len(x) for x in lists])
+    return oracle.csr_encode(row_ptr, np.concatenate(lists))
+
+
+@pytest.mark.parametrize("hub", [0, 1000, 2500])
+def test_hub_split_skewed_graph(vga, hub):
+    # hub = 0: the automatic threshold (>= 2048 lookups) splits the 4000- and
+    # 6000-lookup hubs; explicit thresholds split them into more chunks
+    off, b = _skewed_csr()
+    ref = oracle.hyperball(off, b, 8, 3, seed=9, trace=3)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, 8, 3, seed=9, max_trace=3, union_mode=2, hub_lookups=hub)
+        got1 = vga.hyperball_run_trace(g, 8, 3, seed=9, max_trace=3, union_mode=1)
+    assert_same_run(got, ref)
+    assert_same_run(got1, ref)
+
+
+def test_hub_lookups_rejects_negative(vga):
+    _, off, b, _ = tiny_graph(1)
+    with vga.vga_graph_load(off, b) as g:
+        with pytest.raises(vga.VgaError):
+            vga.hyperball_run_trace(g, 8, 1, max_trace=1, union_mode=2, hub_lookups=-3)
