@@ -450,6 +450,64 @@ int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers,
                      double *gb_per_s);
 
 /* ---------------------------------------------------------------------- */
+/* Register-range shards: one analysis split over several GPUs (or streams)  */
+/* by register index.  Eq. hll-union acts on each register independently,   */
+/* so shard k keeps only the register slices [s0, s1) of every node's        */
+/* counter and runs the union on them alone.  The estimator (Sec. 2.3) needs */
+/* all m registers of a node, but only through two sums: the exact integer   */
+/* harmonic sum and the zero count.  Each shard writes its part of both for  */
+/* every node (its "partial block"); the blocks of all shards, gathered in   */
+/* shard order (an all-gather of n_shards x partial_bytes), give every shard */
+/* the same c_t, Eq. sumD and mean depth, bit for bit equal to an unsharded  */
+/* run.  The stop decision needs the OR of the shards' changed flags.        */
+/*                                                                           */
+/* Per analysis, on every shard, in lockstep:                                */
+/*   vga_shard_start(own) ; all-gather ; vga_shard_estimate(all)   (c_0)     */
+/*   repeat: vga_shard_union(own, &changed) ; all-gather ;                   */
+/*           vga_shard_estimate(all, &increase) ; OR-reduce changed ;        */
+/*           stop as hyperball_run_dev would (changed == 0, or increase == 0 */
+/*           under the paper's rule, or t == d)                              */
+/*   vga_shard_finalize                                                      */
+/* The calls synchronise their stream before returning.  No shard waits on  */
+/* another inside a kernel: the exchange is the caller's collective.         */
+/* ---------------------------------------------------------------------- */
+
+typedef struct vga_shard vga_shard;
+
+/*
+ * vga_shard_create -- shard `shard` of `n_shards` (2 <= n_shards <= the
+ * number of register slices, 0 <= shard < n_shards) of the analysis (g, p,
+ * seed).  Slices are split as evenly as possible, in order.  `tuning` as for
+ * hyperball_run_dev (NULL = automatic; every shard must pass the same).
+ * Allocates the shard's device state on the current device; the graph must
+ * outlive the shard.
+ */
+int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_shards, const vga_tuning *tuning,
+                     vga_shard **out);
+
+/* Slices held, slice width, and the size of one partial block (256-byte multiple). */
+int vga_shard_info(const vga_shard *s, int *slice_first, int *slice_count, int *slice_bytes,
+                   uint64_t *partial_bytes);
+
+/* Insert every node into its own counter (Alg. 1) and write this shard's
+ * partial block of the initial counters to partial_dev (device, 256-byte aligned). */
+int vga_shard_start(vga_shard *s, void *partial_dev, void *stream);
+
+/* One Eq. hll-union pass over this shard's slices, then its partial block of
+ * the new counters; *changed (host) = 1 if any of its registers changed. */
+int vga_shard_union(vga_shard *s, void *partial_dev, uint32_t *changed, void *stream);
+
+/* c_t of every node from all shards' partial blocks (n_shards consecutive
+ * blocks, shard order, device), then Eq. sumD for t >= 1; *increase_flag
+ * (host) = 1 if some c_t - c_{t-1} > 0.5 (the paper's rule). */
+int vga_shard_estimate(vga_shard *s, const void *all_partials_dev, uint32_t *increase_flag, void *stream);
+
+/* Mean depth and ball size (device, N doubles each, may be NULL), as hyperball_run_dev. */
+int vga_shard_finalize(vga_shard *s, double *mean_depth_dev, double *ball_size_dev, void *stream);
+
+void vga_shard_free(vga_shard *s);
+
+/* ---------------------------------------------------------------------- */
 /* Autotuner (the paper tunes nothing; its kernel uses one fixed launch      */
 /* shape, Sec. 3.4).  Launch choices of the union are picked per degree      */
 /* bucket by timing the candidates on the caller's own graphs.               */

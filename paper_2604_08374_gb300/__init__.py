@@ -100,6 +100,13 @@ SIGNATURES = {
     "vga_profile_reset": ([], i32),
     "vga_profile_read": ([C.POINTER(VgaProfile)], i32),
     "vga_bench_gather": ([u64, i32, u64, i32, vp, C.POINTER(f64)], i32),
+    "vga_shard_create": ([vp, i32, u64, i32, i32, C.POINTER(VgaTuning), C.POINTER(vp)], i32),
+    "vga_shard_info": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(u64)], i32),
+    "vga_shard_start": ([vp, vp, vp], i32),
+    "vga_shard_union": ([vp, vp, C.POINTER(u32), vp], i32),
+    "vga_shard_estimate": ([vp, vp, C.POINTER(u32), vp], i32),
+    "vga_shard_finalize": ([vp, vp, vp, vp], i32),
+    "vga_shard_free": ([vp], None),
     "vga_autotune": ([C.POINTER(vp), i32, i32, vp, C.POINTER(VgaTuneEntry), i32, C.POINTER(i32), i32], i32),
     "vga_tune_table_set": ([C.POINTER(VgaTuneEntry), i32], i32),
     "vga_tune_table_get": ([C.POINTER(VgaTuneEntry), i32, C.POINTER(i32)], i32),
@@ -510,3 +517,53 @@ def vga_tune_table_get():
     n = C.c_int()
     _check(lib().vga_tune_table_get(out, 64, C.byref(n)))
     return _entries_out(out, min(n.value, 64))
+
+
+class Shard:
+    """Register-range shard of one analysis (vga_shard_*): slices
+    [slice_first, slice_first + slice_count) of every node's counter."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        first, count, width, pb = C.c_int(), C.c_int(), C.c_int(), C.c_uint64()
+        _check(lib().vga_shard_info(handle, C.byref(first), C.byref(count), C.byref(width), C.byref(pb)))
+        self.slice_first, self.slice_count, self.slice_bytes = first.value, count.value, width.value
+        self.partial_bytes = pb.value
+
+    def start(self, partial, stream=None):
+        _check(lib().vga_shard_start(self.handle, _ptr(partial), _stream_ptr(stream)))
+
+    def union(self, partial, stream=None) -> int:
+        changed = C.c_uint32()
+        _check(lib().vga_shard_union(self.handle, _ptr(partial), C.byref(changed), _stream_ptr(stream)))
+        return changed.value
+
+    def estimate(self, all_partials, stream=None) -> int:
+        inc = C.c_uint32()
+        _check(lib().vga_shard_estimate(self.handle, _ptr(all_partials), C.byref(inc), _stream_ptr(stream)))
+        return inc.value
+
+    def finalize(self, mean_depth_dev, ball_size_dev, stream=None):
+        _check(lib().vga_shard_finalize(self.handle, _ptr(mean_depth_dev), _ptr(ball_size_dev),
+                                        _stream_ptr(stream)))
+
+    def free(self):
+        if self.handle:
+            lib().vga_shard_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, slice_bytes: int = 0,
+                     warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
+                     hub_lookups: int = 0) -> Shard:
+    h = C.c_void_p()
+    _check(lib().vga_shard_create(g.handle, p, seed, shard, n_shards,
+                                  _tuning(slice_bytes, warps_per_cta, 0, union_mode, register_bits, hub_lookups),
+                                  C.byref(h)))
+    return Shard(h)

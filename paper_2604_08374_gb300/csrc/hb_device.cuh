@@ -156,9 +156,11 @@ __device__ __forceinline__ void finish_groups(const typename RegFmt<NIB>::Acc (&
 // is the top p bits of the hash and rho the position of the first set bit of
 // the remaining 64-p bits (65-p if none).  The registers were zeroed before.
 // With 4-bit registers (nib) rho is clamped to 15 and register j is nibble
-// j % 2 of byte j / 2 (the low nibble first).
+// j % 2 of byte j / 2 (the low nibble first).  A shard stores only slices
+// [s0, s1), its slice s0 first.
 __device__ __forceinline__ void init_node(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed,
-                                          uint32_t v, bool nib = false) {
+                                          uint32_t v, bool nib = false, uint32_t s0 = 0u,
+                                          uint32_t s1 = 0xffffffffu) {
     const uint64_t h = splitmix64((uint64_t)v ^ seed);
     const uint32_t j = (uint32_t)(h >> (64 - p));
     const uint64_t w = h << p;
@@ -170,7 +172,8 @@ __device__ __forceinline__ void init_node(uint8_t *__restrict__ regs, uint32_t n
         val = rho << (4u * (j & 1u));
     }
     const uint32_t s = byte / (uint32_t)S, o = byte % (uint32_t)S;
-    regs[((uint64_t)s * n + v) * (uint64_t)S + o] = (uint8_t)val;
+    if (s < s0 || s >= s1) return;  // a register-range shard holds slices [s0, s1) only
+    regs[((uint64_t)(s - s0) * n + v) * (uint64_t)S + o] = (uint8_t)val;
 }
 
 // Fold the node's own slice into the gathered maximum, store it, and set
@@ -451,30 +454,24 @@ __device__ __forceinline__ double u128_to_double(uint64_t hi, uint64_t lo) {
     return __dmul_rn(__ull2double_rn(y | sticky), scale);
 }
 
-// HLL estimator (Sec. 2.3, Sec. 3.3) for every node, then Eq. sumD.
-// The harmonic sum Z = sum_j 2^-M[j] is formed exactly as the integer
-// Z * 2^(65-p) (zero registers V * 2^(65-p) plus 2^(65-p-M) for M >= 1) and
-// rounded once, so the result does not depend on summation order.
-// E = alpha_m m^2 / Z; c = lc[V] = m ln(m/V) if E <= 2.5m and V > 0, else E.
-// For t >= 1: sum_d += t * (c - c_prev), and flags[1] records
-// max_v(c - c_prev) > 0.5 (the paper's convergence test).
-// The whole warp reads node v's m registers; lane 0 writes the results.
-__device__ __forceinline__ void estimate_node(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, int t,
-                                              double alpha_mm, const double *__restrict__ lc,
-                                              const double *__restrict__ c_prev, double *__restrict__ c_cur,
-                                              double *__restrict__ sum_d, uint32_t *__restrict__ inc_flag, uint32_t v,
-                                              int lane, bool nib = false) {
-    const uint32_t m = 1u << p;
-    const uint32_t node_bytes = nib ? m / 2u : m;  // 4-bit registers: two per byte
+// Exact integer part of the HLL harmonic sum over register bytes
+// [b0, b1) of node v (slice-major storage whose slice 0 holds byte b0 ... of
+// every node): lo/hi accumulate sum of 2^(K - M) over the registers M >= 1,
+// zeros counts M = 0 (K = 65 - p).  Warp-cooperative; every lane ends with the
+// warp's totals.
+__device__ __forceinline__ void harmonic_partial(const uint8_t *__restrict__ regs, uint32_t n, int p, int S,
+                                                 uint32_t b0, uint32_t b1, uint32_t v, int lane, bool nib,
+                                                 uint64_t &lo, uint64_t &hi, uint32_t &zeros) {
     const int K = 65 - p;
-    uint64_t lo = 0, hi = 0;
-    uint32_t zeros = 0;
+    lo = 0;
+    hi = 0;
+    zeros = 0;
     const int fields = nib ? 8 : 4;  // registers per 32-bit word
     const int width = nib ? 4 : 8;
     const uint32_t fmask = nib ? 0xFu : 0xFFu;
-    for (uint32_t q = lane; q * 16u < node_bytes; q += 32) {
-        const uint32_t r0 = q * 16u;
-        const uint32_t s = r0 / (uint32_t)S, o = r0 % (uint32_t)S;
+    for (uint32_t r0 = b0 + (uint32_t)lane * 16u; r0 < b1; r0 += 32u * 16u) {
+        const uint32_t rel = r0 - b0;
+        const uint32_t s = rel / (uint32_t)S, o = rel % (uint32_t)S;
         const uint4 x = *reinterpret_cast<const uint4 *>(regs + ((uint64_t)s * n + v) * (uint64_t)S + o);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -498,7 +495,22 @@ __device__ __forceinline__ void estimate_node(const uint8_t *__restrict__ regs, 
         lo += olo;
         hi += ohi + (lo < olo);
     }
-    if (lane != 0) return;
+}
+
+// HLL estimator (Sec. 2.3, Sec. 3.3) from the exact harmonic sum, then
+// Eq. sumD.  Z = sum_j 2^-M[j] is formed exactly as the integer Z * 2^(65-p)
+// (the zero registers' V * 2^(65-p) plus the partial sum lo/hi of
+// harmonic_partial) and rounded once, so the result does not depend on
+// summation order.  E = alpha_m m^2 / Z; c = lc[V] = m ln(m/V) if E <= 2.5m
+// and V > 0, else E.  For t >= 1: sum_d += t * (c - c_prev), and inc_flag
+// records max_v(c - c_prev) > 0.5 (the paper's convergence test).
+__device__ __forceinline__ void estimate_finish(uint64_t lo, uint64_t hi, uint32_t zeros, int p, int t,
+                                                double alpha_mm, const double *__restrict__ lc,
+                                                const double *__restrict__ c_prev, double *__restrict__ c_cur,
+                                                double *__restrict__ sum_d, uint32_t *__restrict__ inc_flag,
+                                                uint32_t v) {
+    const uint32_t m = 1u << p;
+    const int K = 65 - p;
     // add V * 2^K (V <= 2^16, K <= 61: fits in 128 bits)
     const uint64_t zlo = (uint64_t)zeros << K;
     const uint64_t zhi = (uint64_t)zeros >> (64 - K);
@@ -514,6 +526,21 @@ __device__ __forceinline__ void estimate_node(const uint8_t *__restrict__ regs, 
         if (diff > 0.5 && *reinterpret_cast<volatile uint32_t *>(inc_flag) == 0u) atomicOr(inc_flag, 1u);
     }
     c_cur[v] = c;
+}
+
+// Estimator and Eq. sumD for node v over all its registers (one warp; lane 0
+// writes the results).
+__device__ __forceinline__ void estimate_node(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, int t,
+                                              double alpha_mm, const double *__restrict__ lc,
+                                              const double *__restrict__ c_prev, double *__restrict__ c_cur,
+                                              double *__restrict__ sum_d, uint32_t *__restrict__ inc_flag, uint32_t v,
+                                              int lane, bool nib = false) {
+    const uint32_t node_bytes = nib ? (1u << p) / 2u : (1u << p);  // 4-bit registers: two per byte
+    uint64_t lo, hi;
+    uint32_t zeros;
+    harmonic_partial(regs, n, p, S, 0u, node_bytes, v, lane, nib, lo, hi, zeros);
+    if (lane != 0) return;
+    estimate_finish(lo, hi, zeros, p, t, alpha_mm, lc, c_prev, c_cur, sum_d, inc_flag, v);
 }
 
 // MD(v) = sum_d[v] / (N_v - 1) (Sec. 3.3), NaN when N_v <= 1; ball = c_t.

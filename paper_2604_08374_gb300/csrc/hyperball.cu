@@ -45,10 +45,11 @@ const std::vector<double> &lc_table(int p) {
 
 namespace {
 
-__global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed, int nib) {
+__global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed, int nib,
+                               uint32_t s0, uint32_t s1) {
     const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    init_node(regs, n, p, S, seed, (uint32_t)v, nib != 0);
+    init_node(regs, n, p, S, seed, (uint32_t)v, nib != 0, s0, s1);
 }
 
 // Eq. hll-union for one register slice, one warp per node (union_node_edges).
@@ -170,6 +171,49 @@ __global__ void hb_estimate_kernel(const uint8_t *__restrict__ regs, uint32_t n,
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= n) return;
     estimate_node(regs, n, p, S, t, alpha_mm, lc, c_prev, c_cur, sum_d, flags + 1, (uint32_t)warp, lane, nib != 0);
+}
+
+// Register-range shard: node v's exact partial harmonic sum over the shard's
+// slices (relative slice 0 = register byte s0 * S) and its zero count, into
+// the shard's partial block (u64 sums, then u32 counts).  A shard holds fewer
+// than m registers, so the sum stays below 2^64; flags[2] would record
+// otherwise.
+__global__ void hb_shard_partial_kernel(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint32_t b0,
+                                        uint32_t b1, int nib, uint64_t *__restrict__ part_sum,
+                                        uint32_t *__restrict__ part_zeros, uint32_t *__restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= n) return;
+    uint64_t lo, hi;
+    uint32_t zeros;
+    harmonic_partial(regs, n, p, S, b0, b1, (uint32_t)warp, lane, nib != 0, lo, hi, zeros);
+    if (lane != 0) return;
+    if (hi) atomicOr(flags + 2, 2u);
+    part_sum[warp] = lo;
+    part_zeros[warp] = zeros;
+}
+
+// Estimator and Eq. sumD from all shards' partial blocks (`blocks` of
+// `block_bytes` each, in shard order): the partial sums are added exactly in
+// 128 bits, the zero counts as integers, so every shard count gives the
+// unsharded result bit for bit.  One thread per node.
+__global__ void hb_shard_estimate_kernel(const uint8_t *__restrict__ parts, int blocks, uint64_t block_bytes,
+                                         uint64_t zeros_off, uint32_t n, int p, int t, double alpha_mm,
+                                         const double *__restrict__ lc, const double *__restrict__ c_prev,
+                                         double *__restrict__ c_cur, double *__restrict__ sum_d,
+                                         uint32_t *__restrict__ flags) {
+    const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    uint64_t lo = 0, hi = 0;
+    uint32_t zeros = 0;
+    for (int b = 0; b < blocks; b++) {
+        const uint8_t *blk = parts + (uint64_t)b * block_bytes;
+        const uint64_t x = reinterpret_cast<const uint64_t *>(blk)[v];
+        lo += x;
+        hi += (lo < x);
+        zeros += reinterpret_cast<const uint32_t *>(blk + zeros_off)[v];
+    }
+    estimate_finish(lo, hi, zeros, p, t, alpha_mm, lc, c_prev, c_cur, sum_d, flags + 1, (uint32_t)v);
 }
 
 // MD(v) = sum_d[v] / (N_v - 1) (Sec. 3.3), NaN when N_v <= 1; ball = c_t.
@@ -533,7 +577,8 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         // split hubs merge into next[v] by atomic max: it must start below the result
         if (P.items.hubs) VGA_CHECK_CUDA(cudaMemsetAsync(nxt, 0, P.n * P.node_bytes, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
-        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed, P.nib);
+        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed, P.nib, 0u,
+                                                                          (uint32_t)P.slices);
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
         VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0
@@ -625,9 +670,239 @@ void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
 
 }  // namespace vga
 
+// Register-range shard (vga_shard_*): slices [s0, s1) of every node's
+// counter, with its own union buffers and a full copy of the per-node
+// estimator state (identical on every shard).
+struct vga_shard {
+    const vga_graph *g = nullptr;
+    vga::Plan P;  // the graph's plan, with `slices` cut down to this shard's count
+    int p = 10;
+    uint64_t seed = 0;
+    int shard = 0, n_shards = 1;
+    uint32_t s0 = 0, s1 = 0, all_slices = 0;
+    uint64_t block_bytes = 0, zeros_off = 0;
+    vga::DeviceBuffer ws;
+    uint8_t *cur = nullptr, *nxt = nullptr, *tab = nullptr;
+    double *c_prev = nullptr, *c_cur = nullptr, *sum_d = nullptr, *lc = nullptr;
+    uint32_t *flags = nullptr;
+    int t = -1;  // passes run; -1 before vga_shard_start
+};
+
 using namespace vga;
 
 extern "C" {
+
+int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_shards, const vga_tuning *tuning,
+                     vga_shard **out) {
+    clear_error();
+    if (!g || !out || n_shards < 2 || shard < 0 || shard >= n_shards) {
+        set_error("vga_shard_create: need a graph, an output pointer, n_shards >= 2 and 0 <= shard < n_shards");
+        return VGA_EINVAL;
+    }
+    *out = nullptr;
+    Plan P;
+    VGA_TRY(make_plan(g, p, tuning, &P));
+    if (n_shards > P.slices) {
+        set_error("vga_shard_create: %d shards but only %d register slices of %d bytes (lower slice_bytes)",
+                  n_shards, P.slices, P.S);
+        return VGA_EINVAL;
+    }
+    vga_shard *s = new vga_shard;
+    s->g = g;
+    s->p = p;
+    s->seed = seed;
+    s->shard = shard;
+    s->n_shards = n_shards;
+    s->all_slices = (uint32_t)P.slices;
+    s->s0 = (uint32_t)((uint64_t)shard * P.slices / n_shards);
+    s->s1 = (uint32_t)((uint64_t)(shard + 1) * P.slices / n_shards);
+    P.slices = (int)(s->s1 - s->s0);
+    const uint64_t n = P.n, regs = n * P.S * (uint64_t)P.slices;
+    uint64_t o = 0;
+    const uint64_t off_cur = o;   o = align256(o + regs);
+    const uint64_t off_next = o;  o = align256(o + regs);
+    const uint64_t off_c0 = o;    o = align256(o + 8 * n);
+    const uint64_t off_c1 = o;    o = align256(o + 8 * n);
+    const uint64_t off_sum = o;   o = align256(o + 8 * n);
+    const uint64_t off_lc = o;    o = align256(o + 8 * ((uint64_t)P.m + 1));
+    const uint64_t off_flags = o; o = align256(o + 64);
+    const uint64_t off_tab = o;
+    if (P.mode == kModeRuns) o = align256(o + (uint64_t)kRunLevels * n * (uint64_t)P.S);
+    const int rc = s->ws.alloc(o);
+    if (rc != VGA_OK) {
+        delete s;
+        return rc;
+    }
+    uint8_t *base = s->ws.as<uint8_t>();
+    s->cur = base + off_cur;
+    s->nxt = base + off_next;
+    s->c_prev = reinterpret_cast<double *>(base + off_c0);
+    s->c_cur = reinterpret_cast<double *>(base + off_c1);
+    s->sum_d = reinterpret_cast<double *>(base + off_sum);
+    s->lc = reinterpret_cast<double *>(base + off_lc);
+    s->flags = reinterpret_cast<uint32_t *>(base + off_flags);
+    s->tab = base + off_tab;
+    s->zeros_off = align256(8 * n);
+    s->block_bytes = s->zeros_off + align256(4 * n);
+    if (P.mode == kModeRuns && n > 0) {
+        int r = ensure_run_lookups(g, 0);
+        if (r == VGA_OK) {
+            P.hub = hub_threshold(g, P.hub_req);
+            r = ensure_run_items(g, P.hub, 0, &P.items);
+        }
+        if (r != VGA_OK) {
+            delete s;
+            return r;
+        }
+    }
+    s->P = P;
+    *out = s;
+    return VGA_OK;
+}
+
+int vga_shard_info(const vga_shard *s, int *slice_first, int *slice_count, int *slice_bytes,
+                   uint64_t *partial_bytes) {
+    clear_error();
+    if (!s) {
+        set_error("vga_shard_info: null shard");
+        return VGA_EINVAL;
+    }
+    if (slice_first) *slice_first = (int)s->s0;
+    if (slice_count) *slice_count = (int)(s->s1 - s->s0);
+    if (slice_bytes) *slice_bytes = s->P.S;
+    if (partial_bytes) *partial_bytes = s->block_bytes;
+    return VGA_OK;
+}
+
+static int shard_partials(vga_shard *s, const uint8_t *regs, void *partial_dev, cudaStream_t stream) {
+    const Plan &P = s->P;
+    if (!partial_dev || (reinterpret_cast<uintptr_t>(partial_dev) & 255u)) {
+        set_error("vga_shard: partial block must be a 256-byte aligned device buffer of vga_shard_info bytes");
+        return VGA_EINVAL;
+    }
+    if (P.n == 0) return VGA_OK;
+    uint8_t *blk = static_cast<uint8_t *>(partial_dev);
+    const unsigned blocks = (unsigned)((P.n + 7) / 8);
+    hb_shard_partial_kernel<<<blocks, 256, 0, stream>>>(regs, (uint32_t)P.n, s->p, P.S, 0u,
+                                                        (uint32_t)P.S * (uint32_t)P.slices, P.nib,
+                                                        reinterpret_cast<uint64_t *>(blk),
+                                                        reinterpret_cast<uint32_t *>(blk + s->zeros_off), s->flags);
+    count_launch();
+    VGA_CHECK_CUDA(cudaGetLastError());
+    return VGA_OK;
+}
+
+int vga_shard_start(vga_shard *s, void *partial_dev, void *stream_ptr) {
+    clear_error();
+    if (!s) {
+        set_error("vga_shard_start: null shard");
+        return VGA_EINVAL;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const Plan &P = s->P;
+    const uint64_t regs = P.n * P.S * (uint64_t)P.slices;
+    const std::vector<double> &table = lc_table(s->p);
+    VGA_CHECK_CUDA(cudaMemcpyAsync(s->lc, table.data(), 8 * table.size(), cudaMemcpyHostToDevice, stream));
+    VGA_CHECK_CUDA(cudaMemsetAsync(s->flags, 0, 64, stream));
+    if (P.n > 0) {
+        VGA_CHECK_CUDA(cudaMemsetAsync(s->cur, 0, regs, stream));
+        if (P.items.hubs) VGA_CHECK_CUDA(cudaMemsetAsync(s->nxt, 0, regs, stream));
+        VGA_CHECK_CUDA(cudaMemsetAsync(s->sum_d, 0, 8 * P.n, stream));
+        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(s->cur, (uint32_t)P.n, s->p, P.S, s->seed,
+                                                                          P.nib, s->s0, s->s1);
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+    }
+    VGA_TRY(shard_partials(s, s->cur, partial_dev, stream));
+    s->t = 0;
+    return VGA_OK;
+}
+
+int vga_shard_union(vga_shard *s, void *partial_dev, uint32_t *changed, void *stream_ptr) {
+    clear_error();
+    if (!s || s->t < 0) {
+        set_error("vga_shard_union: null shard, or vga_shard_start not called");
+        return VGA_EINVAL;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const Plan &P = s->P;
+    uint32_t h[3] = {0, 0, 0};
+    bool profiling;
+    {
+        std::lock_guard<std::mutex> lock(prof().mu);
+        profiling = prof().enabled;
+    }
+    std::vector<PendingTiming> timings;
+    struct Settle {
+        std::vector<PendingTiming> &t;
+        ~Settle() { settle_timings(t, true, nullptr); }
+    } settle{timings};
+    if (P.n > 0) {
+        VGA_CHECK_CUDA(cudaMemsetAsync(s->flags, 0, 4, stream));
+        VGA_TRY(launch_union(P, s->g, s->cur, s->nxt, s->tab, s->flags, stream, profiling ? &timings : nullptr));
+    }
+    VGA_TRY(shard_partials(s, s->nxt, partial_dev, stream));
+    VGA_CHECK_CUDA(cudaMemcpyAsync(h, s->flags, 12, cudaMemcpyDeviceToHost, stream));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    if (h[2] & 1u) {
+        set_error("vga_shard_union: a bounded wait for a TMA copy ran out in pass %d", s->t + 1);
+        return VGA_ETIMEOUT;
+    }
+    if (h[2] & 2u) {
+        set_error("vga_shard_union: a partial harmonic sum overflowed 64 bits");
+        return VGA_ECORRUPT;
+    }
+    std::swap(s->cur, s->nxt);
+    s->t++;
+    if (changed) *changed = h[0] ? 1u : 0u;
+    return VGA_OK;
+}
+
+int vga_shard_estimate(vga_shard *s, const void *all_partials_dev, uint32_t *increase_flag, void *stream_ptr) {
+    clear_error();
+    if (!s || s->t < 0 || !all_partials_dev) {
+        set_error("vga_shard_estimate: null shard or partials, or vga_shard_start not called");
+        return VGA_EINVAL;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const Plan &P = s->P;
+    uint32_t inc = 0;
+    if (P.n > 0) {
+        VGA_CHECK_CUDA(cudaMemsetAsync(s->flags + 1, 0, 4, stream));
+        const double alpha_mm = hll_alpha_host(s->p) * (double)P.m * (double)P.m;
+        double *out = s->t == 0 ? s->c_prev : s->c_cur;  // c_0 is written where c_{t-1} is read next
+        hb_shard_estimate_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(
+            static_cast<const uint8_t *>(all_partials_dev), s->n_shards, s->block_bytes, s->zeros_off,
+            (uint32_t)P.n, s->p, s->t, alpha_mm, s->lc, s->c_prev, out, s->sum_d, s->flags);
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+        VGA_CHECK_CUDA(cudaMemcpyAsync(&inc, s->flags + 1, 4, cudaMemcpyDeviceToHost, stream));
+        VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+        if (s->t > 0) std::swap(s->c_prev, s->c_cur);
+    }
+    if (increase_flag) *increase_flag = inc ? 1u : 0u;
+    return VGA_OK;
+}
+
+int vga_shard_finalize(vga_shard *s, double *mean_depth_dev, double *ball_size_dev, void *stream_ptr) {
+    clear_error();
+    if (!s || s->t < 0) {
+        set_error("vga_shard_finalize: null shard, or vga_shard_start not called");
+        return VGA_EINVAL;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    const Plan &P = s->P;
+    if (P.n > 0) {
+        hb_finalize_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(
+            (uint32_t)P.n, s->g->d_comp, s->sum_d, s->c_prev, mean_depth_dev, ball_size_dev);
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+    }
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    return VGA_OK;
+}
+
+void vga_shard_free(vga_shard *s) { delete s; }
 
 int vga_profile_enable(int on) {
     std::lock_guard<std::mutex> lock(prof().mu);
