@@ -412,8 +412,11 @@ def run_ours(args, dist: Dist):
         "frac": achieved / l2_peak if l2_peak else None,
         "traffic": traffic,
         "peak_source": (f"in-run L2 gather microbenchmark: {S}-byte rows of an L2-resident {N * S / 2**20:.0f} MiB "
-                        "buffer, same lane mapping and loads in flight as the union kernel, xor consumer "
-                        "(vga_bench_gather consumer=1); MEASURED_PEAKS.json has no L2 figure"),
+                        "buffer, same lane mapping, load width and loads in flight as the union kernel, xor "
+                        "consumer (vga_bench_gather consumer=1); MEASURED_PEAKS.json has no L2 figure.  Its rows "
+                        "are hashed, so none hit L1; the union's rows hit L1 about 45 % of the time (warps of one "
+                        "CTA take neighbouring nodes, whose visible runs overlap), which lets the union read "
+                        "slightly above this L2 figure"),
         "union_loop_ceiling": {"value": loop_ceiling, "unit": "GB/s",
                                "what": "same microbenchmark folding with the union's bytewise max (no decode)"},
         "algorithmic_bytes_per_launch": gather_per_launch,

@@ -171,7 +171,7 @@ int vga_visibility_count(int W, int H, const uint8_t *obst, uint32_t *n_nodes);
 /* Tuning knobs (all 0 = choose automatically). */
 typedef struct vga_tuning {
     int slice_bytes;     /* registers per union slice: power of two in [16, min(m, 1024)] */
-    int warps_per_cta;   /* union kernel CTA size in warps: 1..16                         */
+    int warps_per_cta;   /* union kernel CTA size in warps: 1..16 (0: 4 in mode 2, 8 in 1) */
     int l2_budget_mb;    /* L2 share the auto slice width aims at (default: 60 % of L2)   */
     int union_mode;      /* 0 auto (= 2), 1 one gather per neighbour, 2 per run of
                             consecutive ids through a sparse table of range maxima; both

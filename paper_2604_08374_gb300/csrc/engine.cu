@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         const int t = J.t + 1;
         const uint64_t slice = (uint64_t)s * J.n * S;
         const uint8_t *cur = J.regs[(t - 1) & 1] + slice;
-        uint8_t *tab = RUNS ? J.tab + (uint64_t)s * kRunLevels * J.n * S : nullptr;
+        uint8_t *tab = RUNS ? J.tab + (uint64_t)s * (kRunLevels + 1) * J.n * S : nullptr;
         if (RUNS) {
             if (q < (uint64_t)J.tblocks) {
                 table_item<S>(cur, tab, J.n, (uint32_t)q * (uint32_t)TableShape<S>::B, s_tab);
@@ -214,7 +214,7 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
     o = align256(o + 8ull * n);
     o = align256(o + 8ull * n);
     if (L.mode == 2) {
-        o = align256(o + (uint64_t)kRunLevels * n * m);
+        o = align256(o + (uint64_t)(kRunLevels + 1) * n * m);
         o = align256(o + 4ull * L.slices);
     }
     L.bytes = o;
@@ -232,7 +232,7 @@ JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, co
     J.c[1] = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
     J.sum_d = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
     if (L.mode == 2) {
-        J.tab = ws + o; o = align256(o + (uint64_t)kRunLevels * n * m);
+        J.tab = ws + o; o = align256(o + (uint64_t)(kRunLevels + 1) * n * m);
         J.tab_done = reinterpret_cast<uint32_t *>(ws + o);
         J.lk_off = g->d_lk_off;
         J.lk = g->d_lk;

@@ -18,7 +18,7 @@ struct JobDev {
     const uint32_t *comp;
     const uint64_t *lk_off;  // run-aware union: the graph's range lookups
     const uint32_t *lk;
-    uint8_t *tab;            // sparse tables, slice s at tab + s * kRunLevels * N * S
+    uint8_t *tab;            // table regions T_0..T_4, slice s at tab + s * (kRunLevels + 1) * N * S
     uint32_t *tab_done;      // per slice: table items finished, over all passes
     uint8_t *regs[2];   // slice-major [m/S][N][S]; pass t reads regs[(t-1)&1], writes regs[t&1]
     double *c[2];       // c_t lives in c[t&1]

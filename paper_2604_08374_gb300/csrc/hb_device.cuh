@@ -21,16 +21,34 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 
 // Lane mapping of a slice gather: each lane moves CH bytes of a neighbour's
-// S-byte slice, G lanes cover one neighbour, P neighbours share one warp-wide
-// load instruction, U loads per lane are in flight.
+// S-byte slice (32 bytes, one 256-bit load, from S = 32 on), G lanes cover one
+// neighbour, P neighbours share one warp-wide load instruction, U loads per
+// lane are in flight.
 template <int S>
 struct GatherShape {
-    static constexpr int CH = (S > 512) ? S / 32 : 16;
+    static constexpr int CH = (S >= 1024) ? S / 32 : (S >= 32 ? 32 : 16);
     static constexpr int G = S / CH;
     static constexpr int P = 32 / G;
     static constexpr int V4 = CH / 16;
     static constexpr int U = (V4 == 1) ? 4 : 2;
 };
+
+// One lane's CH bytes of a register row (16-byte aligned; 32-byte aligned when
+// V4 == 2, where a single 256-bit read-only load moves them).  The rows are
+// not written while the loading kernel reads them (or, in the batched engine,
+// are published before the lookups that address them are read).
+template <int V4>
+__device__ __forceinline__ void load_row_chunk(const uint8_t *p, uint4 (&x)[V4]) {
+    if constexpr (V4 == 2) {
+        asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(x[0].x), "=r"(x[0].y), "=r"(x[0].z), "=r"(x[0].w), "=r"(x[1].x), "=r"(x[1].y), "=r"(x[1].z),
+              "=r"(x[1].w)
+            : "l"(p));
+    } else {
+#pragma unroll
+        for (int q = 0; q < V4; q++) x[q] = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+    }
+}
 
 // Register maximum through 16-bit lanes.  For a register word w = [b3 b2 b1 b0]
 // of uint8 registers, an unsigned max over u16x2 lanes of w keeps max(b3) and
@@ -88,9 +106,7 @@ __device__ __forceinline__ void gather_fold(const Row &row, const uint32_t *ids,
         for (int u = 0; u < Sh::U; u++) {
             const int k = k0 + u * Sh::P + g;
             if (k < cnt) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(row(ids[k]) + sub * Sh::CH);
-#pragma unroll
-                for (int q = 0; q < Sh::V4; q++) x[u][q] = __ldg(src + q);
+                load_row_chunk<Sh::V4>(row(ids[k]) + sub * Sh::CH, x[u]);
             } else {
 #pragma unroll
                 for (int q = 0; q < Sh::V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
@@ -115,17 +131,13 @@ struct SliceRow {
     __device__ __forceinline__ const uint8_t *operator()(uint32_t id) const { return cur + (uint64_t)id * S; }
 };
 
-// Row of a range lookup (level k, index i): T_0 is the slice itself, T_1..T_K
-// follow each other in `tab`, N rows each.
+// Row of a range lookup: the lookup is the row index r = k * N + i of window
+// T_k[i] in the slice's table region (T_0 = the slice's own rows, then
+// T_1..T_K, N rows each).
 template <int S>
 struct TableRow {
-    const uint8_t *__restrict__ cur;
     const uint8_t *__restrict__ tab;
-    uint32_t n;
-    __device__ __forceinline__ const uint8_t *operator()(uint32_t lk) const {
-        const uint32_t lvl = lk >> kLkIndexBits, i = lk & kLkIndexMask;
-        return lvl ? tab + ((uint64_t)(lvl - 1) * n + i) * S : cur + (uint64_t)i * S;
-    }
+    __device__ __forceinline__ const uint8_t *operator()(uint32_t r) const { return tab + (uint64_t)r * S; }
 };
 
 // Convert the split accumulators to register bytes and fold the P lane groups
@@ -284,18 +296,19 @@ __device__ __forceinline__ bool lk_wait(LkStage &st, int slot, uint32_t parity) 
 }
 
 // Run-aware Eq. hll-union for one register slice (runs.cu explains the
-// lookups): fold into acc the rows T_k[i] of the range lookups lk[b .. e),
-// where T_k[i] = max(cur[i .. i + 2^k)) has been built for this slice.  The
+// lookups): fold into acc the table rows of the range lookups lk[b .. e),
+// where the slice's table region tab (T_0 .. T_4, T_k[i] = max(cur[i .. i +
+// 2^k))) has been built.  The
 // lookups stream through the warp's TMA stage (`st`, with its barrier phases
 // in `phase`) and each chunk's rows are gathered like the per-neighbour union.
 template <int S, bool NIB = false>
-__device__ __forceinline__ void union_range_runs(const uint32_t *__restrict__ lk, const uint8_t *__restrict__ cur,
-                                                 const uint8_t *__restrict__ tab, uint32_t n, uint64_t b, uint64_t e,
+__device__ __forceinline__ void union_range_runs(const uint32_t *__restrict__ lk, const uint8_t *__restrict__ tab,
+                                                 uint64_t b, uint64_t e,
                                                  LkStage &st, uint32_t &phase, int lane,
                                                  typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4], int *err) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
-    const TableRow<S> row{cur, tab, n};
+    const TableRow<S> row{tab};
     if (b >= e) return;
     const uint64_t a0 = b & ~3ull, e4 = (e + 3) & ~3ull;
     const uint32_t chunks = (uint32_t)((e4 - a0 + kLkChunk - 1) / kLkChunk);
@@ -335,7 +348,7 @@ __device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_
                                                 uint8_t *__restrict__ nxt, uint32_t n, uint32_t v, LkStage &st,
                                                 uint32_t &phase, int lane, uint32_t *flag, int *err) {
     typename RegFmt<NIB>::Acc acc[4 * GatherShape<S>::V4] = {};
-    union_range_runs<S, NIB>(lk, cur, tab, n, lk_off[v], lk_off[v + 1], st, phase, lane, acc, err);
+    union_range_runs<S, NIB>(lk, tab, lk_off[v], lk_off[v + 1], st, phase, lane, acc, err);
     union_store<S, NIB>(acc, cur, nxt, v, lane, flag);
 }
 
@@ -402,12 +415,12 @@ struct TableShape {
 constexpr int kTableSmemBytes = (16 + 15) * 1024;  // largest (B + 15) * S
 
 // Sparse-table rows [r0, r0 + B) of one slice, all levels, straight from the
-// slice's counters: T_k[i] = max(cur[i .. i + 2^k)) for k = 1..kRunLevels and
-// the rows with i + 2^k <= n.  The rows and their halo are staged once in
-// `buf`; each thread then owns one 16-byte chunk of one output row and folds
-// the 16 rows of its widest window, writing T_1, T_2, T_3, T_4 as the window
-// reaches 2, 4, 8 and 16 rows (tab + (k-1) * n * S for level k).  All threads
-// of the CTA (256) take part.
+// slice's counters: T_0[i] = cur[i] and T_k[i] = max(cur[i .. i + 2^k)) for
+// k = 1..kRunLevels and the rows with i + 2^k <= n.  The rows and their halo
+// are staged once in `buf`; each thread then owns one 16-byte chunk of one
+// output row, copies it to T_0 and folds the 16 rows of its widest window,
+// writing T_1, T_2, T_3, T_4 as the window reaches 2, 4, 8 and 16 rows
+// (tab + k * n * S for level k).  All threads of the CTA (256) take part.
 template <int S, bool NIB = false>
 __device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict__ tab, uint32_t n, uint32_t r0,
                            uint8_t *buf) {
@@ -424,13 +437,13 @@ __device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict_
         const uint32_t row = x / T::C16, c = x % T::C16;
         const uint64_t i = (uint64_t)r0 + row;
         uint4 acc = b4[x];
+        if (i < n) reinterpret_cast<uint4 *>(tab + i * S)[c] = acc;
 #pragma unroll
         for (int j = 1; j < 16; j++) {
             acc = RegFmt<NIB>::max4(acc, b4[x + j * T::C16]);
             if ((j & (j + 1)) == 0) {  // window of j + 1 = 2^k rows complete
                 const int k = 31 - __clz(j + 1);
-                if (i + (1u << k) <= n)
-                    reinterpret_cast<uint4 *>(tab + ((uint64_t)(k - 1) * n + i) * S)[c] = acc;
+                if (i + (1u << k) <= n) reinterpret_cast<uint4 *>(tab + ((uint64_t)k * n + i) * S)[c] = acc;
             }
         }
     }

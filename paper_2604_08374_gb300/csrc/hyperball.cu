@@ -88,25 +88,20 @@ __global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__res
     uint32_t phase = 0;
     int *err = reinterpret_cast<int *>(flags + 2);
     typename RegFmt<NIB>::Acc acc[4 * GatherShape<S>::V4] = {};
-    union_range_runs<S, NIB>(lk, cur, tab, n, it.b, it.b + it.cnt, st, phase, lane, acc, err);
+    union_range_runs<S, NIB>(lk, tab, it.b, it.b + it.cnt, st, phase, lane, acc, err);
     if (it.v & kHubChunk)
         union_store_hub<S, NIB>(acc, cur, nxt, it.v & ~kHubChunk, lane, flags, err);
     else
         union_store<S, NIB>(acc, cur, nxt, it.v, lane, flags);
 }
 
-// One sparse-table level for a slice: out[i] = max(prev[i], prev[i + half]) for
-// i = 0 .. rows-1 (rows = N - 2*half + 1; later rows are never looked up).
-// One thread per 16-byte chunk.
-__global__ void hb_table_level_kernel(const uint8_t *__restrict__ prev, uint8_t *__restrict__ out, uint32_t rows,
-                                      uint32_t half, int S, int nib) {
-    const uint32_t chunks = (uint32_t)S / 16u;
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (uint64_t)rows * chunks) return;
-    const uint64_t i = t / chunks, c = t % chunks;
-    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(prev + i * S) + c);
-    const uint4 b = __ldg(reinterpret_cast<const uint4 *>(prev + (i + half) * S) + c);
-    reinterpret_cast<uint4 *>(out + i * S)[c] = nib ? RegFmt<true>::max4(a, b) : RegFmt<false>::max4(a, b);
+// The slice's table region T_0 .. T_4 (table_item), B rows per CTA of 256
+// threads, in one launch.
+template <int S, bool NIB>
+__global__ void __launch_bounds__(256) hb_table_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ tab,
+                                                       uint32_t n) {
+    __shared__ __align__(16) uint8_t buf[TableShape<S>::R * S];
+    table_item<S, NIB>(cur, tab, n, blockIdx.x * (uint32_t)TableShape<S>::B, buf);
 }
 
 // Microbenchmark twin of hb_union_kernel: rows drawn from a hash instead of
@@ -135,9 +130,7 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
                 for (int u = 0; u < Sh::U; u++) {
                     const int k = k0 + u * Sh::P + g;
                     if (k < 32) {
-                        const uint4 *src = reinterpret_cast<const uint4 *>(buf + (uint64_t)ids[k] * S + sub * Sh::CH);
-#pragma unroll
-                        for (int q = 0; q < Sh::V4; q++) x[u][q] = __ldg(src + q);
+                        load_row_chunk<Sh::V4>(buf + (uint64_t)ids[k] * S + sub * Sh::CH, x[u]);
                     } else {
 #pragma unroll
                         for (int q = 0; q < Sh::V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
@@ -321,8 +314,11 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     }
     P->S = S;
     P->slices = (int)(P->node_bytes / (uint32_t)S);
+    // default CTA size: 4 warps for the run-aware union (measured fastest on
+    // the city workload), 8 for the per-neighbour one
     P->warps = (tune && tune->warps_per_cta > 0) ? tune->warps_per_cta
                : (tabled && te.warps_per_cta > 0)     ? te.warps_per_cta
+               : P->mode == kModeRuns                 ? 4
                                                       : 8;
     if (P->warps > 16) {
         set_error("warps_per_cta = %d exceeds 16", P->warps);
@@ -345,7 +341,7 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->off_lc = o;    o = align256(o + 8 * ((uint64_t)P->m + 1));
     P->off_flags = o; o = align256(o + 64);
     P->off_tab = o;
-    if (P->mode == kModeRuns) o = align256(o + (uint64_t)kRunLevels * P->n * (uint64_t)S);
+    if (P->mode == kModeRuns) o = align256(o + (uint64_t)(kRunLevels + 1) * P->n * (uint64_t)S);
     P->total = o;
     return VGA_OK;
 }
@@ -379,18 +375,9 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
     const size_t smem = (size_t)P.warps * 32 * sizeof(uint32_t);
     if (P.mode == kModeRuns) {
         const unsigned item_blocks = (unsigned)((P.items.count + P.warps - 1) / P.warps);
-        const uint8_t *prev = c;
-        for (int k = 1; k <= kRunLevels; k++) {
-            const uint64_t w = 1ull << k;
-            if (P.n < w) break;  // no run can be this long
-            const uint32_t rows = (uint32_t)(P.n - w + 1);
-            uint8_t *out = tab + (uint64_t)(k - 1) * P.n * SS;
-            const uint64_t threads = (uint64_t)rows * (SS / 16);
-            hb_table_level_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(prev, out, rows,
-                                                                                         (uint32_t)(w >> 1), SS, NIB);
-            count_launch();
-            prev = out;
-        }
+        const unsigned table_blocks = (unsigned)((P.n + TableShape<SS>::B - 1) / TableShape<SS>::B);
+        hb_table_kernel<SS, NIB><<<table_blocks, 256, 0, stream>>>(c, tab, (uint32_t)P.n);
+        count_launch();
         hb_union_runs_kernel<SS, NIB><<<item_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
             P.items.items, P.items.count, g->d_lk, c, tab, x, (uint32_t)P.n, flags);
     } else {
@@ -436,7 +423,7 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             pt.edges = g->n_edges;
             if (P.mode == kModeRuns) {
                 pt.gather_bytes = g->lk_total * (uint64_t)P.S;
-                pt.hbm_bytes = 4 * g->lk_total + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
+                pt.hbm_bytes = 4 * g->lk_total + 16 * P.items.count + 2 * P.n * (uint64_t)P.S;
             } else {
                 pt.gather_bytes = g->n_edges * (uint64_t)P.S;
                 pt.hbm_bytes = g->n_bytes + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
@@ -727,7 +714,7 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     const uint64_t off_lc = o;    o = align256(o + 8 * ((uint64_t)P.m + 1));
     const uint64_t off_flags = o; o = align256(o + 64);
     const uint64_t off_tab = o;
-    if (P.mode == kModeRuns) o = align256(o + (uint64_t)kRunLevels * n * (uint64_t)P.S);
+    if (P.mode == kModeRuns) o = align256(o + (uint64_t)(kRunLevels + 1) * n * (uint64_t)P.S);
     const int rc = s->ws.alloc(o);
     if (rc != VGA_OK) {
         delete s;

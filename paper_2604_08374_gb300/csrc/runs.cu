@@ -11,10 +11,11 @@
 // 16.  Max is associative, commutative and idempotent, so the result is the
 // same register array, bit for bit.
 //
-// This file turns the LEB128 CSR into the list of (level, row) lookups of
-// every node, once per graph: one warp per node decodes its list with the
-// warp window decoder, finds run boundaries across windows, and emits each
-// completed run's lookups.
+// This file turns the LEB128 CSR into the list of lookups of every node, once
+// per graph: one warp per node decodes its list with the warp window decoder,
+// finds run boundaries across windows, and emits each completed run's lookups
+// as row indices k * N + i of a slice's table region (T_0 = the slice, then
+// T_1..T_4), so that the union addresses a row with one multiply-add.
 #include <vector>
 
 #include "vga_common.cuh"
@@ -22,7 +23,7 @@
 namespace vga {
 namespace {
 
-// Lookups covering the run [a, a + L).
+// Number of lookups covering the run [a, a + L).
 __device__ __forceinline__ uint32_t run_lookup_count(uint32_t L) {
     if (L < 32u) {
         const uint32_t k = 31u - __clz(L);
@@ -31,16 +32,17 @@ __device__ __forceinline__ uint32_t run_lookup_count(uint32_t L) {
     return (L >> 4) + ((L & 15u) ? 1u : 0u);
 }
 
-__device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_t *out) {
+// Lookups covering the run [a, a + L) as table row indices k * n + i.
+__device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_t n, uint32_t *out) {
     if (L < 32u) {
         const uint32_t k = 31u - __clz(L);
-        out[0] = (k << kLkIndexBits) | a;
-        if (L != (1u << k)) out[1] = (k << kLkIndexBits) | (a + L - (1u << k));
+        out[0] = k * n + a;
+        if (L != (1u << k)) out[1] = k * n + (a + L - (1u << k));
         return;
     }
     const uint32_t full = L >> 4;
-    for (uint32_t j = 0; j < full; j++) out[j] = (4u << kLkIndexBits) | (a + 16u * j);
-    if (L & 15u) out[full] = (4u << kLkIndexBits) | (a + L - 16u);
+    for (uint32_t j = 0; j < full; j++) out[j] = 4u * n + (a + 16u * j);
+    if (L & 15u) out[full] = 4u * n + (a + L - 16u);
 }
 
 // One warp per node.  WRITE = false stores the node's lookup count in cnt[v];
@@ -78,7 +80,7 @@ __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8
         if (run_len > 0) {
             if (starts) {
                 run_len += (uint32_t)(__ffs(starts) - 1);
-                if (WRITE && lane == 0) run_lookup_write(run_a, run_len, lk + out);
+                if (WRITE && lane == 0) run_lookup_write(run_a, run_len, n, lk + out);
                 out += run_lookup_count(run_len);
                 run_len = 0;
             } else {
@@ -96,7 +98,7 @@ __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        if (WRITE && complete) run_lookup_write(id, L, lk + out + (incl - my));
+        if (WRITE && complete) run_lookup_write(id, L, n, lk + out + (incl - my));
         out += __shfl_sync(0xffffffffu, incl, 31);
         // 3. the last start of the window opens a run that may continue
         if (starts) {
@@ -109,7 +111,7 @@ __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8
         pos += (uint64_t)r.advance;
     }
     if (run_len > 0) {
-        if (WRITE && lane == 0) run_lookup_write(run_a, run_len, lk + out);
+        if (WRITE && lane == 0) run_lookup_write(run_a, run_len, n, lk + out);
         out += run_lookup_count(run_len);
     }
     if (!WRITE && lane == 0) cnt[v] = out;

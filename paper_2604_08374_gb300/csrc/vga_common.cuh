@@ -135,11 +135,11 @@ struct PinnedBuffer {
 // Range lookups of the run-aware union.  A neighbour list in raster order is a
 // sequence of runs of consecutive ids; the maximum over a run [a, a+L) is read
 // from a sparse table T_k[i] = max(cur[i .. i + 2^k)) for k = 0..kRunLevels.
-// Each lookup is one u32: level k in the top 3 bits, row i in the low 29.
-constexpr int kRunLevels = 4;        // windows of 1, 2, 4, 8, 16 rows
-constexpr uint32_t kLkIndexBits = 29;
-constexpr uint32_t kLkIndexMask = (1u << kLkIndexBits) - 1u;
-constexpr uint64_t kRunMaxNodes = 1ull << kLkIndexBits;
+constexpr int kRunLevels = 4;  // sparse-table levels T_1..T_4: windows of 2, 4, 8, 16 rows
+// A lookup is the row index r = k * N + i of window T_k[i] in a slice's table
+// region, where T_0 (a copy of the slice) and T_1..T_4 lie one after another
+// (kRunLevels + 1 rows per node); r < 5 N must fit in 32 bits.
+constexpr uint64_t kRunMaxNodes = 1ull << 29;
 
 // One warp's work in the run-aware union: the lookups lk[b .. b + cnt) of node
 // v & ~kHubChunk.  A node with more lookups than the hub threshold is split

@@ -96,7 +96,10 @@ def test_mixed_requests_match_solo_runs(vga, pool, solo_nodes):
 def test_tight_budget_queues_requests(vga, pool):
     reqs = _requests(pool, 24, seed=5)
     budget = 24 << 20
-    reqs = [r for r in reqs if r["g"].n_nodes * (2 << r["p"]) + 40 * r["g"].n_nodes < budget // 2]
+    # a run-aware job holds two register copies and five table rows per node
+    # and slice (N x m bytes each) plus 56 bytes of per-node doubles
+    reqs = [r for r in reqs if r["g"].n_nodes * (7 << r["p"]) + 64 * r["g"].n_nodes + 4096 < budget // 2]
+    assert len(reqs) >= 6
     with vga.Server(hbm_budget_bytes=budget, max_batch=8, solo_nodes=1 << 30) as srv:
         ids = [srv.submit(r["g"], r["p"], r["d"], r["seed"], r["conv"]) for r in reqs]
         results = [srv.wait(i, timeout_s=120) for i in ids]
