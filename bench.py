@@ -297,7 +297,7 @@ def kernel_source_sha() -> str:
     with open(os.path.join(ROOT, "paper_2604_08374_gb300/csrc/hyperball.cu"), "rb") as f:
         src = f.read()
     a = src.find(b"// Eq. hll-union for one register slice, one warp per node")
-    b = src.find(b"// One sparse-table level for a slice")
+    b = src.find(b"// Microbenchmark twin of hb_union_kernel")
     h.update(src[a:b] if 0 <= a < b else src)
     return h.hexdigest()[:16]
 

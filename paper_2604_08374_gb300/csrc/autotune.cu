@@ -88,10 +88,7 @@ int tune_graph(const vga_graph *g, int p, cudaStream_t stream, vga_tune_entry *e
     }
     // 3. hub threshold (mode 2): the automatic one, then smaller
     if (best.union_mode == 2) {
-        int sms = 1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const uint64_t share = g->lk_total / ((uint64_t)std::max(sms, 1) * 64);
-        const uint32_t autoh = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(share / 2, 2048), 0x7fffffffull);
+        const uint32_t autoh = hub_lookups_auto(g);
         const vga_tuning base2 = best;
         for (uint32_t div : {2u, 4u}) {
             vga_tuning t = base2;

@@ -83,10 +83,14 @@ __device__ __forceinline__ bool wait_tables(const uint32_t *done, uint32_t targe
 
 // Persistent union over the running jobs of one group (same union variant,
 // same slice width S).  CTAs claim items from the group's queue.  Per job and
-// slice the queue holds, in run-aware jobs (RUNS), first the sparse-table items
-// and then the union items (one node per warp); a union item starts once its
-// slice's table items are done.  Table items never wait, and every table item
-// of a slice is claimed before any of its union items, so each wait ends.
+// slice the queue holds, in run-aware jobs (RUNS), first the sparse-table
+// items (TableShape<S>::B rows each, built by the whole CTA) and then the
+// union blocks of kEngineBlock work items (work-list entries: a node, or a
+// chunk of a split hub; in per-neighbour jobs, nodes), whose warps take the
+// block's items one at a time from a shared counter, so that a long item does
+// not hold the others back.  A union block starts once its slice's table
+// items are done.  Table items never wait, and every table item of a slice is
+// claimed before any of its union blocks, so each wait ends.
 template <int S, bool RUNS>
 __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *jobs,
                                                                         const uint32_t *__restrict__ gjobs,
@@ -97,27 +101,33 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
     __shared__ __align__(16) uint8_t s_tab[RUNS ? TableShape<S>::R * S : 16];
     __shared__ __align__(128) LkStage s_stage[RUNS ? kEngineWarps : 1];
     __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_next;
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint32_t phase = 0;  // barrier phases of this warp's TMA stage
     if (RUNS) lk_stage_init(s_stage[wib], lane);
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+        __syncthreads();  // every warp is done with the previous item (and its s_next)
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(counter, 1ull);
+            s_next = 0;
+        }
         __syncthreads();
         const uint64_t item = s_item;
-        __syncthreads();
         if (item >= total_items) break;
         const int k = find_job(item_start, n_jobs, item);
         JobDev &J = jobs[gjobs[k]];
         if (J.state != 0) continue;
-        const uint64_t per_slice = (uint64_t)J.blocks + (RUNS ? (uint64_t)J.tblocks : 0);
+        const uint32_t ublocks = (J.units + kEngineBlock - 1) / kEngineBlock;
+        const uint64_t per_slice = (uint64_t)ublocks + (RUNS ? (uint64_t)J.tblocks : 0);
         const uint64_t r = item - item_start[k];
         const uint32_t s = (uint32_t)(r / per_slice);
         uint64_t q = r % per_slice;
         const int t = J.t + 1;
         const uint64_t slice = (uint64_t)s * J.n * S;
         const uint8_t *cur = J.regs[(t - 1) & 1] + slice;
+        uint8_t *nxt = J.regs[t & 1] + slice;
         uint8_t *tab = RUNS ? J.tab + (uint64_t)s * (kRunLevels + 1) * J.n * S : nullptr;
         if (RUNS) {
             if (q < (uint64_t)J.tblocks) {
@@ -135,13 +145,25 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
             __syncthreads();
             if (!s_ok) continue;
         }
-        const uint32_t v = (uint32_t)q * kEngineWarps + wib;
-        if (v >= J.n) continue;
-        uint8_t *nxt = J.regs[t & 1] + slice;
-        if (RUNS)
-            union_node_runs<S>(J.lk_off, J.lk, cur, tab, nxt, J.n, v, s_stage[wib], phase, lane, &J.changed, error);
-        else
-            union_node_edges<S>(J.off, J.bytes, cur, nxt, v, s_ids[wib], lane, &J.changed);
+        const uint32_t u0 = (uint32_t)q * kEngineBlock;
+        const uint32_t u1 = min(u0 + kEngineBlock, J.units);
+        for (;;) {
+            uint32_t x = 0;
+            if (lane == 0) x = atomicAdd(&s_next, 1u);
+            x = u0 + __shfl_sync(0xffffffffu, x, 0);
+            if (x >= u1) break;
+            if (RUNS) {
+                const RunItem it = J.items[x];
+                typename RegFmt<false>::Acc acc[4 * GatherShape<S>::V4] = {};
+                union_range_runs<S>(J.lk, tab, it.b, it.b + it.cnt, s_stage[wib], phase, lane, acc, error);
+                if (it.v & kHubChunk)
+                    union_store_hub<S, false>(acc, cur, nxt, it.v & ~kHubChunk, lane, &J.changed, error);
+                else
+                    union_store<S, false>(acc, cur, nxt, it.v, lane, &J.changed);
+            } else {
+                union_node_edges<S>(J.off, J.bytes, cur, nxt, x, s_ids[wib], lane, &J.changed);
+            }
+        }
     }
 }
 
@@ -204,7 +226,6 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
     while (S > 16 && (uint64_t)S * n * rows > budget) S >>= 1;
     L.S = S;
     L.slices = (int)(m / (uint32_t)S);
-    L.blocks = (int)((n + kEngineWarps - 1) / kEngineWarps);
     const int B = S >= 1024 ? 16 : 32;  // rows of a table item (TableShape)
     L.tblocks = L.mode == 2 ? (int)((n + B - 1) / B) : 0;
     uint64_t o = 0;
@@ -221,8 +242,8 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
     return L;
 }
 
-JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
-                   const double *lc, double *md, double *ball) {
+int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
+                const double *lc, double *md, double *ball, uint32_t hub_lookups, cudaStream_t stream, JobDev *out) {
     JobDev J{};
     const uint64_t n = g->n, m = 1ull << p;
     uint64_t o = 0;
@@ -234,8 +255,13 @@ JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, co
     if (L.mode == 2) {
         J.tab = ws + o; o = align256(o + (uint64_t)(kRunLevels + 1) * n * m);
         J.tab_done = reinterpret_cast<uint32_t *>(ws + o);
-        J.lk_off = g->d_lk_off;
+        RunItemList list;
+        VGA_TRY(ensure_run_items(g, hub_lookups ? hub_lookups : hub_lookups_auto(g), stream, &list));
         J.lk = g->d_lk;
+        J.items = list.items;
+        J.units = (uint32_t)list.count;
+    } else {
+        J.units = g->n;
     }
     J.off = g->d_offsets;
     J.bytes = g->d_bytes;
@@ -251,10 +277,10 @@ JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, co
     J.slices = L.slices;
     J.d = d;
     J.conv = conv;
-    J.blocks = L.blocks;
     J.mode = L.mode;
     J.tblocks = L.tblocks;
-    return J;
+    *out = J;
+    return VGA_OK;
 }
 
 // Linear-counting tables of p = 4..16 side by side (8 (2^p + 1) bytes each).
@@ -350,7 +376,8 @@ int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, Engine
             gj.push_back(k);
             is.push_back(items);
             const JobDev &J = jobs[k];
-            items += (uint64_t)J.slices * ((uint64_t)J.blocks + (J.mode == 2 ? (uint64_t)J.tblocks : 0));
+            items += (uint64_t)J.slices * ((uint64_t)((J.units + kEngineBlock - 1) / kEngineBlock) +
+                                           (J.mode == 2 ? (uint64_t)J.tblocks : 0));
         }
         is.push_back(items);
         G.total_items = items;
@@ -378,6 +405,8 @@ int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, Engine
 int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const EngineSet &E, cudaStream_t stream) {
     for (const JobDev &J : jobs) {
         VGA_CHECK_CUDA(cudaMemsetAsync(J.regs[0], 0, (uint64_t)J.n << J.p, stream));
+        // split hubs merge into the pass's output by atomic max: it must start below the result
+        if (J.mode == 2) VGA_CHECK_CUDA(cudaMemsetAsync(J.regs[1], 0, (uint64_t)J.n << J.p, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(J.sum_d, 0, 8ull * J.n, stream));
         if (J.mode == 2) VGA_CHECK_CUDA(cudaMemsetAsync(J.tab_done, 0, 4ull * J.slices, stream));
     }
@@ -548,15 +577,15 @@ int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaSt
         jobs[i].status = VGA_OK;
     }
     if (B.idx.empty()) return VGA_OK;
-    for (size_t k = 0; k < B.idx.size(); k++)
-        if (B.lay[k].mode == 2) VGA_TRY(ensure_run_lookups(jobs[B.idx[k]].graph, stream));
     VGA_TRY(upload_lc_tables(ws + B.off_lc, B.lc_used, stream));
     std::vector<JobDev> host(B.idx.size());
     for (size_t k = 0; k < B.idx.size(); k++) {
         const vga_job &jb = jobs[B.idx[k]];
-        host[k] = make_jobdev(jb.graph, jb.p, jb.d, jb.seed, jb.conv_mode, B.lay[k], ws + B.job_off[k],
-                              reinterpret_cast<const double *>(ws + B.off_lc + lc_offset(jb.p)), jb.mean_depth_dev,
-                              jb.ball_size_dev);
+        vga_tune_entry te{};
+        const uint32_t hub = tune_table_lookup(jb.graph, &te) ? (uint32_t)te.hub_lookups : 0u;
+        VGA_TRY(make_jobdev(jb.graph, jb.p, jb.d, jb.seed, jb.conv_mode, B.lay[k], ws + B.job_off[k],
+                            reinterpret_cast<const double *>(ws + B.off_lc + lc_offset(jb.p)), jb.mean_depth_dev,
+                            jb.ball_size_dev, hub, stream, &host[k]));
     }
     const EngineArrays A = engine_arrays_at(ws + B.off_arrays, (int)host.size());
     EngineSet E;

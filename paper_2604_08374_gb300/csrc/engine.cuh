@@ -8,7 +8,8 @@
 
 namespace vga {
 
-constexpr int kEngineWarps = 8;
+constexpr int kEngineWarps = 16;
+constexpr uint32_t kEngineBlock = 64;  // work items per union block of the queue
 constexpr int kGroups = 14;  // union kernels: (per neighbour | per run) x slice width 16..1024
 
 // One analysis as the batched kernels see it (device memory).
@@ -16,8 +17,8 @@ struct JobDev {
     const uint64_t *off;
     const uint8_t *bytes;
     const uint32_t *comp;
-    const uint64_t *lk_off;  // run-aware union: the graph's range lookups
-    const uint32_t *lk;
+    const uint32_t *lk;      // run-aware union: the graph's range lookups
+    const RunItem *items;    // and its work list (nodes, split hubs' chunks)
     uint8_t *tab;            // table regions T_0..T_4, slice s at tab + s * (kRunLevels + 1) * N * S
     uint32_t *tab_done;      // per slice: table items finished, over all passes
     uint8_t *regs[2];   // slice-major [m/S][N][S]; pass t reads regs[(t-1)&1], writes regs[t&1]
@@ -28,9 +29,10 @@ struct JobDev {
     double alpha_mm;
     uint64_t seed;
     uint32_t n;
-    int p, S, slices, d, conv, blocks;
+    int p, S, slices, d, conv;
+    uint32_t units;         // union items per slice: work-list entries (mode 2) or nodes (mode 1)
     int mode;               // 1 one gather per neighbour, 2 per run (sparse tables)
-    int tblocks;            // table items per slice (mode 2)
+    int tblocks;            // table items per slice (mode 2), TableShape<S>::B rows each
     uint32_t changed, inc;  // flags of the pass in progress
     int t;                  // passes completed
     int state;              // 0 running, 1 stopped at this step (finalize), 2 done
@@ -39,7 +41,7 @@ struct JobDev {
 // Per-job union variant, slice width and workspace size (regs0, regs1, c0,
 // c1, sum_d, and in mode 2 the sparse tables of every slice and their counters).
 struct JobLayout {
-    int mode = 2, S = 0, slices = 0, blocks = 0, tblocks = 0;
+    int mode = 2, S = 0, slices = 0, tblocks = 0;
     uint64_t bytes = 0;
 };
 
@@ -74,8 +76,11 @@ struct EngineSet {
 uint64_t align256(uint64_t x);
 uint64_t l2_budget_bytes(int dev);
 JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode);
-JobDev make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
-                   const double *lc, double *md, double *ball);
+// Device view of one analysis in workspace ws; in mode 2 it builds (on first
+// use) the graph's lookups and its work list for hub threshold hub_lookups
+// (0 = automatic).
+int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
+                const double *lc, double *md, double *ball, uint32_t hub_lookups, cudaStream_t stream, JobDev *out);
 uint64_t lc_offset(int p);
 uint64_t lc_all_bytes();
 int upload_lc_tables(uint8_t *dst, const bool *used, cudaStream_t stream);

@@ -245,16 +245,9 @@ struct Plan {
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
-// Hub threshold of the run-aware union (lookups per work item).  Automatic:
-// half of one warp's even share of the slice's lookups when every SM holds 64
-// warps, and at least 2048, so only nodes that would outlast the rest of the
-// launch are split.
+// Hub threshold of the run-aware union (lookups per work item).
 static uint32_t hub_threshold(const vga_graph *g, uint32_t requested) {
-    if (requested > 0) return requested;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    const uint64_t share = g->lk_total / ((uint64_t)(sms > 0 ? sms : 1) * 64);
-    return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(share / 2, 2048), 0x7fffffffull);
+    return requested > 0 ? requested : hub_lookups_auto(g);
 }
 
 static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P) {

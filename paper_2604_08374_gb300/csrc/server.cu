@@ -150,13 +150,6 @@ void batched_lane(vga_server *S) {
         std::vector<JobDev> start;
         std::vector<std::shared_ptr<Request>> started;
         for (const auto &r : fresh) {
-            if (r->L.mode == 2) {
-                const int rc = ensure_run_lookups(r->g, stream);
-                if (rc != VGA_OK) {
-                    fail(S, r, rc, vga_last_error(), stream);
-                    continue;
-                }
-            }
             void *mem = nullptr;
             if (cudaMallocAsync(&mem, r->bytes, stream) != cudaSuccess) {
                 cudaGetLastError();
@@ -165,8 +158,16 @@ void batched_lane(vga_server *S) {
             }
             r->ws = static_cast<uint8_t *>(mem);
             double *md = reinterpret_cast<double *>(r->ws + r->L.bytes);
-            start.push_back(make_jobdev(r->g, r->p, r->d, r->seed, r->conv, r->L, r->ws, lc_base + lc_offset(r->p) / 8,
-                                        md, md + r->g->n));
+            JobDev J{};
+            vga_tune_entry te{};
+            const uint32_t hub = tune_table_lookup(r->g, &te) ? (uint32_t)te.hub_lookups : 0u;
+            const int rc = make_jobdev(r->g, r->p, r->d, r->seed, r->conv, r->L, r->ws, lc_base + lc_offset(r->p) / 8,
+                                       md, md + r->g->n, hub, stream, &J);
+            if (rc != VGA_OK) {
+                fail(S, r, rc, vga_last_error(), stream);
+                continue;
+            }
+            start.push_back(J);
             started.push_back(r);
         }
         if (!start.empty()) {

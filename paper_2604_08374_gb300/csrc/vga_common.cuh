@@ -162,6 +162,11 @@ struct RunItemList {
 };
 int ensure_run_items(const vga_graph *g, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out);
 
+// Automatic hub threshold (lookups per work item): half of one warp's even
+// share of a slice's lookups when every SM holds 64 warps, and at least 2048,
+// so only nodes that would outlast the rest of a launch are split.
+uint32_t hub_lookups_auto(const vga_graph *g);
+
 // Autotuner table (autotune.cu): the installed entry for g's degree bucket.
 bool tune_table_lookup(const vga_graph *g, vga_tune_entry *out);
 
@@ -172,11 +177,15 @@ int run_timed(const vga_graph *g, int p, int d, uint64_t seed, const vga_tuning 
 // Build the graph's lookup list on first use (thread-safe); no-op afterwards.
 int ensure_run_lookups(const vga_graph *g, cudaStream_t stream);
 
-// Creates a graph object around already-copied device offsets and bytes:
-// validates the stream on the device, derives degrees and E.  Takes
-// ownership of the device pointers on success (and frees them on failure).
+// Creates a graph object around device offsets and bytes: validates the
+// stream on the device, derives degrees, E and the run-aware union's lookup
+// counts.  Takes ownership of the device pointers on success (and frees them
+// on failure).  With h_bytes (and h_offsets) given, d_bytes is still empty
+// apart from its zeroed padding, and the bytes are copied from the host here,
+// in chunks overlapped with the validation of the nodes already complete.
 int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t *d_bytes, const uint32_t *comp_host,
-                      cudaStream_t stream, vga_graph **out);
+                      cudaStream_t stream, vga_graph **out, const uint64_t *h_offsets = nullptr,
+                      const uint8_t *h_bytes = nullptr);
 
 // ---------------------------------------------------------------------------
 // Warp LEB128 window decoder (Sec. 3.2 encoding; the paper decodes each list
@@ -237,6 +246,104 @@ __device__ __forceinline__ WindowDecode<Id> decode_window(const uint8_t *__restr
     r.id = base + s;
     r.next_base = T ? __shfl_sync(0xffffffffu, r.id, r.advance - 1) : base;
     return r;
+}
+
+// Wide variant of decode_window for the passes that only need the ids (graph
+// validation, lookup building): each lane takes 4 bytes, so a warp decodes
+// 128 bytes per step.  The window starts at a varint boundary `pos`; lane L
+// holds window bytes 4L .. 4L+3 (two aligned 32-bit loads per lane shared
+// through a shuffle, then a funnel shift; the byte buffer carries 256 bytes
+// of padding).  Every varint that ends in the window is assembled from at
+// most 5 bytes (its own lane and the one before), the deltas are prefix-
+// summed across the warp, and the ids are written in order to ids[0 ..
+// count).  Returns count; advance = bytes consumed up to the window's last
+// complete varint (0 if none); next_base = its id.  CHECK also tests every
+// rule of the format (varint of at most 5 bytes and 32 bits, no zero delta
+// after a list's first entry, id < n, id != self) and sets fail on any
+// break; list_start says the window begins the node's list.
+template <class Id, bool CHECK>
+__device__ __forceinline__ int decode_window4(const uint8_t *__restrict__ bytes, uint64_t pos, uint64_t end,
+                                              Id base, int lane, uint32_t *ids, int &advance, Id &next_base,
+                                              bool list_start, uint64_t n, uint64_t self, bool &fail) {
+    const uint64_t a0 = pos & ~3ull;
+    const uint32_t *aw = reinterpret_cast<const uint32_t *>(bytes + a0);
+    const uint32_t w = __ldg(aw + lane);
+    uint32_t wn = __shfl_down_sync(0xffffffffu, w, 1);
+    if (lane == 31) wn = __ldg(aw + 32);
+    const uint32_t word = __funnelshift_r(w, wn, (uint32_t)(pos & 3ull) * 8u);
+    const uint32_t prev_word = __shfl_up_sync(0xffffffffu, word, 1);
+    const uint64_t dw = ((uint64_t)word << 32) | (lane ? prev_word : 0u);  // window bytes 4L-4 .. 4L+3
+    const uint64_t p0 = pos + 4u * (uint32_t)lane;
+    uint32_t tm = 0;  // terminator bits of this lane's bytes
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (p0 + (uint64_t)k < end && !((word >> (8 * k)) & 0x80u)) tm |= 1u << k;
+    // last terminator before this lane's bytes (window position), -1 if none
+    int pt = tm ? 4 * lane + (31 - __clz(tm)) : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pt, o);
+        if (lane >= o) pt = max(pt, t);
+    }
+    const int last_all = __shfl_sync(0xffffffffu, pt, 31);
+    int prev = __shfl_up_sync(0xffffffffu, pt, 1);
+    if (lane == 0) prev = -1;
+    // assemble this lane's varints
+    uint32_t val[4];
+    Id lane_sum = 0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        val[k] = 0;
+        if ((tm >> k) & 1u) {
+            const int q = 4 * lane + k;  // terminator position
+            const int len = q - prev;    // bytes prev+1 .. q
+            uint64_t v = 0;
+            if (len <= 5) {
+                // the varint's bytes, first (least significant group) lowest, then
+                // the 7-bit groups packed together
+                const uint64_t x = (dw >> (8 * (prev + 1 - 4 * lane + 4))) & ((1ull << (8 * len)) - 1ull);
+                v = (x & 0x7Full) | ((x >> 1) & (0x7Full << 7)) | ((x >> 2) & (0x7Full << 14)) |
+                    ((x >> 3) & (0x7Full << 21)) | ((x >> 4) & (0x7Full << 28));
+            } else {
+                bad = true;
+            }
+            if (v > 0xFFFFFFFFull) bad = true;
+            val[k] = (uint32_t)v;
+            lane_sum += (Id)(uint32_t)v;
+            prev = q;
+        }
+    }
+    // prefix sums of the deltas and of the varint counts across lanes
+    Id incl = lane_sum;
+    int cnt_incl = __popc(tm);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Id t = __shfl_up_sync(0xffffffffu, incl, o);
+        const int c = __shfl_up_sync(0xffffffffu, cnt_incl, o);
+        if (lane >= o) {
+            incl += t;
+            cnt_incl += c;
+        }
+    }
+    Id id = base + incl - lane_sum;
+    int idx = cnt_incl - __popc(tm);
+    bool f = bad;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if ((tm >> k) & 1u) {
+            id += (Id)val[k];
+            if (CHECK) {
+                if (val[k] == 0u && !(list_start && idx == 0)) f = true;  // duplicate neighbour
+                if ((uint64_t)id >= n || (uint64_t)id == self) f = true;
+            }
+            ids[idx++] = (uint32_t)id;
+        }
+    }
+    if (CHECK) fail = __any_sync(0xffffffffu, f);
+    advance = last_all + 1;
+    next_base = base + __shfl_sync(0xffffffffu, incl, 31);
+    return __shfl_sync(0xffffffffu, cnt_incl, 31);
 }
 
 __device__ __forceinline__ uint4 vmax4(uint4 a, uint4 b) {

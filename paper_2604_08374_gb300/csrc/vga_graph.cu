@@ -1,11 +1,12 @@
 // vga_graph.cu -- graph residency: the delta-compressed LEB128 CSR of Sec. 3.2
 // kept in device memory, its on-device validation, the host encoder and the
 // library's file format.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
 
-#include "vga_common.cuh"
+#include "runs.cuh"
 
 namespace vga {
 
@@ -20,58 +21,77 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
-// One warp per node: decode its byte range with the warp window decoder and
-// check every rule of the format.  Writes the degree and folds E, the maximum
+// One warp per node v0 .. v1-1: decode its byte range with the wide window
+// decoder and check every rule of the format.  Writes the degree and the number of range
+// lookups the run-aware union will need (runs.cuh), and folds E, the maximum
 // degree and the lowest bad node id into global counters.
 __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes, uint32_t n,
-                                uint32_t *__restrict__ degree, unsigned long long *__restrict__ edge_total,
+                                uint32_t v0, uint32_t v1, uint32_t *__restrict__ degree,
+                                uint32_t *__restrict__ lk_count, unsigned long long *__restrict__ edge_total,
                                 uint32_t *__restrict__ max_degree, uint32_t *__restrict__ bad_node) {
+    __shared__ uint32_t s_ids[8][128];
     const int lane = threadIdx.x & 31;
-    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (warp >= n) return;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *ids = s_ids[wib];
+    const uint64_t warp = (uint64_t)v0 + (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= v1) return;
     const uint32_t v = (uint32_t)warp;
     uint64_t pos = off[v];
     const uint64_t end = off[v + 1];
     uint64_t base = 0;
     uint32_t cnt = 0;
     bool ok = true;
+    RunTracker rt;
     while (pos < end) {
-        WindowDecode<uint64_t> r = decode_window<uint64_t>(bytes, pos, end, base, lane);
-        if (r.term_mask == 0) {  // a varint runs past the node's range or over 32 bytes
-            ok = false;
-            break;
-        }
-        const bool term = (r.term_mask >> lane) & 1u;
-        const bool first_of_list = (cnt == 0) && (lane == __ffs(r.term_mask) - 1);
+        int advance = 0;
+        uint64_t next = 0;
         bool fail = false;
-        if (term) {
-            if (r.bad) fail = true;
-            if (!first_of_list && r.value == 0) fail = true;  // duplicate neighbour
-            if (r.id >= (uint64_t)n) fail = true;
-            if (r.id == (uint64_t)v) fail = true;              // self loop
-        }
-        if (__any_sync(0xffffffffu, fail)) {
+        const int c = decode_window4<uint64_t, true>(bytes, pos, end, base, lane, ids, advance, next, cnt == 0,
+                                                     (uint64_t)n, (uint64_t)v, fail);
+        if (c == 0 || fail) {  // a varint runs past the node's range, or a rule is broken
             ok = false;
             break;
         }
-        cnt += __popc(r.term_mask);
-        base = r.next_base;
-        pos += (uint64_t)r.advance;
+        __syncwarp();
+        rt.window<false>(ids, c, lane, n, nullptr);
+        __syncwarp();
+        cnt += (uint32_t)c;
+        base = next;
+        pos += (uint64_t)advance;
     }
+    rt.finish<false>(lane, n, nullptr);
     if (lane == 0) {
         degree[v] = ok ? cnt : 0;
+        lk_count[v] = ok ? (uint32_t)rt.out : 0u;
         if (!ok) atomicMin(bad_node, v);
         atomicAdd(edge_total, (unsigned long long)cnt);
         atomicMax(max_degree, cnt);
     }
 }
 
+static int launch_validate(const uint64_t *d_offsets, const uint8_t *d_bytes, uint32_t n, uint32_t v0, uint32_t v1,
+                           uint32_t *degree, uint32_t *lk_count, unsigned long long *d_edges, uint32_t *d_maxdeg,
+                           uint32_t *d_bad, cudaStream_t stream) {
+    if (v1 <= v0) return VGA_OK;
+    const int warps = 8;
+    const uint64_t blocks = ((uint64_t)(v1 - v0) + warps - 1) / warps;
+    validate_kernel<<<(unsigned)blocks, warps * 32, 0, stream>>>(d_offsets, d_bytes, n, v0, v1, degree, lk_count,
+                                                                  d_edges, d_maxdeg, d_bad);
+    count_launch();
+    VGA_CHECK_CUDA(cudaGetLastError());
+    return VGA_OK;
+}
+
+// Validation of a freshly copied CSR; with h_bytes given, the byte stream is
+// also copied here, in chunks, and each chunk's complete nodes are validated
+// on a second stream while the next chunk is in flight.
 int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t *d_bytes, const uint32_t *comp_host,
-                      cudaStream_t stream, vga_graph **out) {
-    DeviceBuffer offsets, bytes, degree, comp, counters;
+                      cudaStream_t stream, vga_graph **out, const uint64_t *h_offsets, const uint8_t *h_bytes) {
+    DeviceBuffer offsets, bytes, degree, comp, counters, lk_count;
     offsets.ptr = d_offsets;
     bytes.ptr = d_bytes;
     VGA_TRY(degree.alloc(sizeof(uint32_t) * (size_t)(n ? n : 1)));
+    VGA_TRY(lk_count.alloc(sizeof(uint32_t) * (size_t)(n ? n : 1)));
     if (comp_host) {
         VGA_TRY(comp.alloc(sizeof(uint32_t) * (size_t)n));
         VGA_CHECK_CUDA(cudaMemcpyAsync(comp.ptr, comp_host, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
@@ -83,16 +103,46 @@ int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t
     unsigned long long *d_edges = counters.as<unsigned long long>();
     uint32_t *d_maxdeg = reinterpret_cast<uint32_t *>(counters.as<uint8_t>() + 8);
     uint32_t *d_bad = reinterpret_cast<uint32_t *>(counters.as<uint8_t>() + 12);
-    if (n > 0) {
-        const int warps = 8;
-        const uint64_t blocks = ((uint64_t)n + warps - 1) / warps;
-        validate_kernel<<<(unsigned)blocks, warps * 32, 0, stream>>>(d_offsets, d_bytes, n, degree.as<uint32_t>(),
-                                                                      d_edges, d_maxdeg, d_bad);
-        count_launch();
-        VGA_CHECK_CUDA(cudaGetLastError());
+    if (h_bytes && n_bytes > 0) {
+        constexpr uint64_t kChunk = 256ull << 20;
+        cudaStream_t vs = nullptr;
+        cudaEvent_t ev = nullptr;
+        VGA_CHECK_CUDA(cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking));
+        struct Cleanup {
+            cudaStream_t &s;
+            cudaEvent_t &e;
+            ~Cleanup() {
+                if (e) cudaEventDestroy(e);
+                if (s) cudaStreamDestroy(s);
+            }
+        } cleanup{vs, ev};
+        VGA_CHECK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        VGA_CHECK_CUDA(cudaEventRecord(ev, stream));  // offsets, pad and counters are set
+        VGA_CHECK_CUDA(cudaStreamWaitEvent(vs, ev, 0));
+        uint32_t done = 0;
+        for (uint64_t c0 = 0; c0 < n_bytes; c0 += kChunk) {
+            const uint64_t c1 = std::min(c0 + kChunk, n_bytes);
+            VGA_CHECK_CUDA(cudaMemcpyAsync(d_bytes + c0, h_bytes + c0, c1 - c0, cudaMemcpyHostToDevice, stream));
+            VGA_CHECK_CUDA(cudaEventRecord(ev, stream));
+            VGA_CHECK_CUDA(cudaStreamWaitEvent(vs, ev, 0));
+            // nodes whose byte range ends by c1
+            const uint32_t upto = c1 == n_bytes ? n
+                                                : (uint32_t)(std::upper_bound(h_offsets + 1, h_offsets + n + 1, c1) -
+                                                             (h_offsets + 1));
+            VGA_TRY(launch_validate(d_offsets, d_bytes, n, done, upto, degree.as<uint32_t>(), lk_count.as<uint32_t>(),
+                                    d_edges, d_maxdeg, d_bad, vs));
+            done = std::max(done, upto);
+        }
+        VGA_CHECK_CUDA(cudaEventRecord(ev, vs));
+        VGA_CHECK_CUDA(cudaStreamWaitEvent(stream, ev, 0));
+    } else if (n > 0) {
+        VGA_TRY(launch_validate(d_offsets, d_bytes, n, 0, n, degree.as<uint32_t>(), lk_count.as<uint32_t>(), d_edges,
+                                d_maxdeg, d_bad, stream));
     }
     uint8_t host_counters[16];
+    std::vector<uint32_t> h_cnt(n);
     VGA_CHECK_CUDA(cudaMemcpyAsync(host_counters, counters.ptr, 16, cudaMemcpyDeviceToHost, stream));
+    if (n) VGA_CHECK_CUDA(cudaMemcpyAsync(h_cnt.data(), lk_count.ptr, 4 * (size_t)n, cudaMemcpyDeviceToHost, stream));
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
     uint64_t edges;
     uint32_t maxdeg, bad;
@@ -117,6 +167,10 @@ int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t
     g->d_bytes = static_cast<uint8_t *>(bytes.release());
     g->d_degree = static_cast<uint32_t *>(degree.release());
     g->d_comp = static_cast<uint32_t *>(comp.release());
+    // offsets of the run-aware union's lookups (the list itself is built on first use)
+    g->h_lk_off.assign((size_t)n + 1, 0);
+    for (uint32_t v = 0; v < n; v++) g->h_lk_off[v + 1] = g->h_lk_off[v] + h_cnt[v];
+    g->lk_total = g->h_lk_off[n];
     *out = g;
     return VGA_OK;
 }
@@ -232,13 +286,13 @@ int vga_graph_load(uint32_t n, const uint64_t *offsets, const uint8_t *bytes_hos
     cudaStream_t stream = 0;
     VGA_CHECK_CUDA(cudaMemcpyAsync(off.ptr, offsets, sizeof(uint64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
                                    stream));
-    if (n_bytes) VGA_CHECK_CUDA(cudaMemcpyAsync(bytes.ptr, bytes_host, n_bytes, cudaMemcpyHostToDevice, stream));
     VGA_CHECK_CUDA(cudaMemsetAsync(bytes.as<uint8_t>() + n_bytes, 0, kBytePad, stream));
     uint64_t *po = off.as<uint64_t>();
     uint8_t *pb = bytes.as<uint8_t>();
     off.release();
     bytes.release();
-    return finish_graph_load(n, n_bytes, po, pb, comp_size, stream, out);
+    // the byte stream is copied in chunks, overlapped with validation
+    return finish_graph_load(n, n_bytes, po, pb, comp_size, stream, out, offsets, bytes_host);
 }
 
 void vga_graph_free(vga_graph *g) {
