@@ -329,12 +329,17 @@ int hyperball_run_batch(vga_job *jobs, int n_jobs, void *workspace_dev, uint64_t
 typedef struct vga_server vga_server;
 
 typedef struct vga_server_config {
-    uint64_t hbm_budget_bytes;  /* device bytes requests may hold at once (0: 150 GiB)      */
+    uint64_t hbm_budget_bytes;  /* device bytes requests may hold at once (0: 150 GiB); the
+                                   server's memory pool keeps up to this much after requests
+                                   finish, for the next ones                                  */
     int max_batch;              /* requests advanced together in the batched lane (0: 256) */
-    int solo_nodes;             /* graphs above this many nodes use the solo lane (0: 65536) */
+    int solo_nodes;             /* graphs above this many nodes use the solo lane (0: 32768) */
     int lane_priority;          /* 0: lanes equal; 1: solo lane's stream gets the higher
                                    priority; -1: batched lane's does                          */
-    int reserved[3];
+    int batched_share;          /* percent of the batched lane's union CTAs kept while a
+                                   solo-lane analysis runs, leaving the other SMs to it
+                                   (0 or 100: no limit)                                       */
+    int reserved[2];
 } vga_server_config;
 
 typedef struct vga_server_stats_t {

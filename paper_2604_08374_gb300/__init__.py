@@ -43,7 +43,7 @@ class VgaJob(C.Structure):
 
 class VgaServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_batch", C.c_int), ("solo_nodes", C.c_int),
-                ("lane_priority", C.c_int), ("reserved", C.c_int * 3)]
+                ("lane_priority", C.c_int), ("batched_share", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class VgaServerStats(C.Structure):
@@ -395,10 +395,11 @@ class Server:
     """Request loop with continuous batching (vga_server_*).  Results arrive in
     host numpy arrays; keep graphs loaded until their requests are waited for."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, max_batch: int = 0, solo_nodes: int = 0, lane_priority: int = 0):
+    def __init__(self, hbm_budget_bytes: int = 0, max_batch: int = 0, solo_nodes: int = 0, lane_priority: int = 0,
+                 batched_share: int = 0):
         cfg = VgaServerConfig()
         cfg.hbm_budget_bytes, cfg.max_batch, cfg.solo_nodes = hbm_budget_bytes, max_batch, solo_nodes
-        cfg.lane_priority = lane_priority
+        cfg.lane_priority, cfg.batched_share = lane_priority, batched_share
         h = C.c_void_p()
         _check(lib().vga_server_create(C.byref(cfg), C.byref(h)))
         self._h = h

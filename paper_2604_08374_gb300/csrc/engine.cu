@@ -420,19 +420,20 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
 }
 
 template <int S, bool RUNS>
-void launch_group(const EngineArrays &A, const EngineGroup &G, cudaStream_t stream) {
-    batch_union_kernel<S, RUNS><<<G.grid, kEngineWarps * 32, 0, stream>>>(A.jobs, A.gjobs + G.gjob_off,
+void launch_group(const EngineArrays &A, const EngineGroup &G, cudaStream_t stream, int grid_pct) {
+    const unsigned grid = (grid_pct > 0 && grid_pct < 100) ? std::max(1u, G.grid * (unsigned)grid_pct / 100u) : G.grid;
+    batch_union_kernel<S, RUNS><<<grid, kEngineWarps * 32, 0, stream>>>(A.jobs, A.gjobs + G.gjob_off,
                                                                          A.item_start + G.item_off, G.n,
                                                                          G.total_items, A.counters + G.index, A.error);
 }
 
 int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, cudaGraphConditionalHandle cond,
-                int use_cond) {
+                int use_cond, int grid_pct) {
     for (const EngineGroup &G : E.groups) {
 #define VGA_G(SS)                                                                         \
     case SS:                                                                              \
-        if (G.mode == 2) launch_group<SS, true>(A, G, stream);                            \
-        else launch_group<SS, false>(A, G, stream);                                       \
+        if (G.mode == 2) launch_group<SS, true>(A, G, stream, grid_pct);                  \
+        else launch_group<SS, false>(A, G, stream, grid_pct);                             \
         break;
         switch (G.S) {
             VGA_G(16) VGA_G(32) VGA_G(64) VGA_G(128) VGA_G(256) VGA_G(512) VGA_G(1024)
@@ -596,7 +597,7 @@ int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaSt
     } else {
         int running = 1;
         while (running) {
-            VGA_TRY(engine_pass(A, E, stream, 0, 0));
+            VGA_TRY(engine_pass(A, E, stream, 0, 0, 100));
             VGA_CHECK_CUDA(cudaMemcpyAsync(&running, A.any_running, sizeof(int), cudaMemcpyDeviceToHost, stream));
             VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
         }

@@ -88,8 +88,10 @@ uint64_t engine_arrays_bytes(int cap);
 EngineArrays engine_arrays_at(uint8_t *base, int cap);
 int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, EngineSet *E, cudaStream_t stream);
 int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const EngineSet &E, cudaStream_t stream);
+// One pass of every uploaded job.  grid_pct < 100 runs the union kernels on
+// that share of their usual grid (the server's solo-lane priority).
 int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, cudaGraphConditionalHandle cond,
-                int use_cond);
+                int use_cond, int grid_pct = 100);
 int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t stream);
 
 }  // namespace vga

@@ -18,6 +18,7 @@
 //
 // Each request's results are bit-identical to running it alone.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -69,6 +70,11 @@ struct vga_server {
     std::thread lane_batched, lane_solo;
     // batched-lane device state
     cudaStream_t stream_batched = nullptr, stream_solo = nullptr;
+    // requests' workspaces come from the server's own stream-ordered pool, which
+    // keeps freed memory (up to the HBM budget) for the next request instead of
+    // returning it to the driver at every synchronisation
+    cudaMemPool_t pool = nullptr;
+    std::atomic<int> solo_active{0};  // a solo-lane analysis is on the GPU
     uint8_t *arrays = nullptr;  // active and start arrays, LC tables
 };
 
@@ -151,7 +157,7 @@ void batched_lane(vga_server *S) {
         std::vector<std::shared_ptr<Request>> started;
         for (const auto &r : fresh) {
             void *mem = nullptr;
-            if (cudaMallocAsync(&mem, r->bytes, stream) != cudaSuccess) {
+            if (cudaMallocFromPoolAsync(&mem, r->bytes, S->pool, stream) != cudaSuccess) {
                 cudaGetLastError();
                 fail(S, r, VGA_ENOMEM, "device allocation for the request failed", stream);
                 continue;
@@ -188,7 +194,8 @@ void batched_lane(vga_server *S) {
         // one pass for every admitted request
         EngineSet E;
         int rc = engine_upload(A_run, host, &E, stream);
-        if (rc == VGA_OK) rc = engine_pass(A_run, E, stream, 0, 0);
+        const int share = S->solo_active.load() ? S->cfg.batched_share : 100;
+        if (rc == VGA_OK) rc = engine_pass(A_run, E, stream, 0, 0, share);
         cudaError_t e = cudaSuccess;
         int err = 0;
         if (rc == VGA_OK) {
@@ -248,7 +255,7 @@ void solo_lane(vga_server *S) {
             r->t_admit = Clock::now();
         }
         void *mem = nullptr;
-        if (cudaMallocAsync(&mem, r->bytes, stream) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&mem, r->bytes, S->pool, stream) != cudaSuccess) {
             cudaGetLastError();
             fail(S, r, VGA_ENOMEM, "device allocation for the request failed", stream);
             continue;
@@ -257,8 +264,10 @@ void solo_lane(vga_server *S) {
         const uint64_t ws_bytes = r->bytes - align256(16ull * r->g->n);
         double *md = reinterpret_cast<double *>(r->ws + ws_bytes);
         int it = 0;
+        S->solo_active.store(1);
         const int rc = hyperball_run_dev(r->g, r->p, r->d, r->seed, r->conv, md, md + r->g->n, &it, r->ws, ws_bytes,
                                          stream, nullptr);
+        S->solo_active.store(0);
         if (rc != VGA_OK) {
             fail(S, r, rc, vga_last_error(), stream);
             continue;
@@ -285,9 +294,22 @@ int vga_server_create(const vga_server_config *cfg, vga_server **out) {
     if (cfg) S->cfg = *cfg;
     if (S->cfg.hbm_budget_bytes == 0) S->cfg.hbm_budget_bytes = 150ull << 30;
     if (S->cfg.max_batch <= 0) S->cfg.max_batch = 256;
-    if (S->cfg.solo_nodes == 0) S->cfg.solo_nodes = 65536;
+    if (S->cfg.solo_nodes == 0) S->cfg.solo_nodes = 32768;
+    if (S->cfg.batched_share < 0 || S->cfg.batched_share > 100) {
+        set_error("vga_server_create: batched_share = %d is outside 0..100", S->cfg.batched_share);
+        return VGA_EINVAL;
+    }
     VGA_CHECK_CUDA(cudaGetDevice(&S->device));
     S->l2_budget = l2_budget_bytes(S->device);
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = S->device;
+        VGA_CHECK_CUDA(cudaMemPoolCreate(&S->pool, &props));
+        uint64_t keep = S->cfg.hbm_budget_bytes;
+        VGA_CHECK_CUDA(cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     const uint64_t arrays = 2 * align256(engine_arrays_bytes(S->cfg.max_batch)) + lc_all_bytes();
     void *mem = nullptr;
     VGA_CHECK_CUDA(cudaMalloc(&mem, arrays));
@@ -424,6 +446,7 @@ void vga_server_destroy(vga_server *S) {
     if (S->stream_batched) cudaStreamSynchronize(S->stream_batched);
     if (S->stream_solo) cudaStreamSynchronize(S->stream_solo);
     if (S->arrays) cudaFree(S->arrays);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
     if (S->stream_batched) cudaStreamDestroy(S->stream_batched);
     if (S->stream_solo) cudaStreamDestroy(S->stream_solo);
     delete S;
