@@ -289,18 +289,22 @@ def run_reference(args, dist: Dist):
 # ----------------------------------------------------------------------------
 
 def kernel_source_sha() -> str:
-    """Hash of the union kernels' source: their device code (hb_device.cuh, the
-    graph and lookup declarations in vga_common.cuh) and their definitions in
-    hyperball.cu (host code there does not count)."""
+    """Hash of the union kernels' source: their device code (hb_device.cuh), the
+    lookup and work-item declarations in vga_common.cuh, and their definitions
+    in hyperball.cu (host code there does not count)."""
     h = hashlib.sha256()
-    for rel in ("paper_2604_08374_gb300/csrc/hb_device.cuh", "paper_2604_08374_gb300/csrc/vga_common.cuh"):
+
+    def region(rel, start, end):
         with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
-    with open(os.path.join(ROOT, "paper_2604_08374_gb300/csrc/hyperball.cu"), "rb") as f:
-        src = f.read()
-    a = src.find(b"// Eq. hll-union for one register slice, one warp per node")
-    b = src.find(b"// Microbenchmark twin of hb_union_kernel")
-    h.update(src[a:b] if 0 <= a < b else src)
+            src = f.read()
+        a = src.find(start) if start else 0
+        b = src.find(end, a) if end else len(src)
+        h.update(src[a:b] if 0 <= a < b else src)
+
+    region("paper_2604_08374_gb300/csrc/hb_device.cuh", None, None)
+    region("paper_2604_08374_gb300/csrc/vga_common.cuh", b"constexpr int kRunLevels", b"// Work list of the run-aware")
+    region("paper_2604_08374_gb300/csrc/hyperball.cu", b"// Eq. hll-union for one register slice, one warp per node",
+           b"// Microbenchmark twin of hb_union_kernel")
     return h.hexdigest()[:16]
 
 
@@ -354,7 +358,10 @@ def run_ours(args, dist: Dist):
         from paper_2604_08374_gb300.sharded import hyperball_run_sharded
         args.no_extras = True  # e2e, d = unlimited and the CPU leg are single-GPU measurements
 
-    def step(d, union_mode=None):
+    def step(d, union_mode=None, p=None, bits=None):
+        if p is not None or bits is not None:  # sweep legs: other precision or register width, own workspace
+            return vga.hyperball_run_dev(g, args.p if p is None else p, d, args.seed, md, ball, stream=stream,
+                                         register_bits=0 if bits in (None, 8) else bits)
         if sharded and union_mode is None:
             with torch.cuda.stream(stream):
                 return hyperball_run_sharded(g, args.p, d, args.seed, md, ball, slice_bytes=args.slice_bytes,
@@ -487,6 +494,19 @@ def run_ours(args, dist: Dist):
         torch.cuda.synchronize()
         extras["other_union_mode"] = {"union_mode": other, "seconds": f0.elapsed_time(f1) / 1e3,
                                       "geu_per_s": o_passes * E / (f0.elapsed_time(f1) / 1e3) / 1e9}
+        # ---- sweeps of the city configuration: p = 8 and 12, d = 10, and the
+        #      paper's packed 4-bit registers (rho clamped to 15) ----
+        sweep = []
+        for (sp, sd, sb) in ((8, args.d, 8), (12, args.d, 8), (args.p, 10, 8), (args.p, args.d, 4)):
+            step(sd, p=sp, bits=sb)
+            f0.record(stream)
+            s_passes = step(sd, p=sp, bits=sb)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            sec_s = f0.elapsed_time(f1) / 1e3
+            sweep.append({"p": sp, "d": sd, "register_bits": sb, "seconds": sec_s, "passes": s_passes,
+                          "geu_per_s": s_passes * E / sec_s / 1e9})
+        extras["sweep"] = sweep
         if dist.rank == 0 and dist.world == 1:
             extras["cpu_baseline"] = cpu_baseline(obst, args)
 
