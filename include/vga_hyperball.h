@@ -186,7 +186,12 @@ typedef struct vga_tuning {
                             chunks of at most this many, each folded by its own warp and
                             merged by a word-wise atomic max (0 = automatic: half of one
                             warp's even share of the lookups, at least 2048)              */
-    int reserved[2];
+    int table_levels;    /* mode 2: rows per node of a slice's table of range maxima:
+                            5 (windows of 1, 2, 4, 8, 16 rows: fewest lookups) or 3 (1, 4,
+                            16: lets wider slices fit the L2); 0 = automatic (3 when five
+                            rows of 128-byte slices would exceed 3/4 of the L2).  A
+                            non-automatic choice builds its own lookup list on first use. */
+    int reserved[1];
 } vga_tuning;
 
 /*

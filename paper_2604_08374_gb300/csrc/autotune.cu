@@ -65,7 +65,7 @@ int tune_graph(const vga_graph *g, int p, cudaStream_t stream, vga_tune_entry *e
     // 1. variant x slice width, 8 warps, automatic hub threshold
     for (int mode = 1; mode <= 2; mode++) {
         if (mode == 2 && (uint64_t)g->n > kRunMaxNodes) continue;
-        const uint64_t rows = mode == 2 ? (uint64_t)kRunLevels + 1 : 1;
+        const uint64_t rows = mode == 2 ? (uint64_t)table_rows(g->lk_scheme) : 1;
         for (uint32_t S = 16; S <= std::min<uint32_t>(m, 1024u); S <<= 1) {
             if (S > 16 && (uint64_t)S * g->n * rows > l2_bytes) break;
             vga_tuning t{};
@@ -88,7 +88,7 @@ int tune_graph(const vga_graph *g, int p, cudaStream_t stream, vga_tune_entry *e
     }
     // 3. hub threshold (mode 2): the automatic one, then smaller
     if (best.union_mode == 2) {
-        const uint32_t autoh = hub_lookups_auto(g);
+        const uint32_t autoh = hub_lookups_auto(g, g->lk_scheme);
         const vga_tuning base2 = best;
         for (uint32_t div : {2u, 4u}) {
             vga_tuning t = base2;

@@ -128,10 +128,10 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         const uint64_t slice = (uint64_t)s * J.n * S;
         const uint8_t *cur = J.regs[(t - 1) & 1] + slice;
         uint8_t *nxt = J.regs[t & 1] + slice;
-        uint8_t *tab = RUNS ? J.tab + (uint64_t)s * (kRunLevels + 1) * J.n * S : nullptr;
+        uint8_t *tab = RUNS ? J.tab + (uint64_t)s * table_rows(J.scheme) * J.n * S : nullptr;
         if (RUNS) {
             if (q < (uint64_t)J.tblocks) {
-                table_item<S>(cur, tab, J.n, (uint32_t)q * (uint32_t)TableShape<S>::B, s_tab);
+                table_item<S>(cur, tab, J.n, (uint32_t)q * (uint32_t)TableShape<S>::B, s_tab, J.scheme);
                 __threadfence();  // every writer publishes its table rows device-wide
                 __syncthreads();
                 if (threadIdx.x == 0) atomicAdd(J.tab_done + s, 1u);
@@ -217,11 +217,12 @@ uint64_t l2_budget_bytes(int dev) {
     return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
 }
 
-JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode) {
+JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode, int scheme) {
     JobLayout L;
     L.mode = (mode == 1 || (uint64_t)n > kRunMaxNodes) ? 1 : 2;
+    L.scheme = scheme;
     const uint32_t m = 1u << p;
-    const uint64_t rows = L.mode == 2 ? (uint64_t)kRunLevels + 1 : 1;
+    const uint64_t rows = L.mode == 2 ? (uint64_t)table_rows(scheme) : 1;
     int S = (int)std::min<uint32_t>(m, (uint32_t)(slice_cap > 0 ? slice_cap : 1024));
     while (S > 16 && (uint64_t)S * n * rows > budget) S >>= 1;
     L.S = S;
@@ -235,7 +236,7 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
     o = align256(o + 8ull * n);
     o = align256(o + 8ull * n);
     if (L.mode == 2) {
-        o = align256(o + (uint64_t)(kRunLevels + 1) * n * m);
+        o = align256(o + (uint64_t)table_rows(scheme) * n * m);
         o = align256(o + 4ull * L.slices);
     }
     L.bytes = o;
@@ -253,11 +254,13 @@ int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const
     J.c[1] = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
     J.sum_d = reinterpret_cast<double *>(ws + o); o = align256(o + 8 * n);
     if (L.mode == 2) {
-        J.tab = ws + o; o = align256(o + (uint64_t)(kRunLevels + 1) * n * m);
+        J.tab = ws + o; o = align256(o + (uint64_t)table_rows(L.scheme) * n * m);
         J.tab_done = reinterpret_cast<uint32_t *>(ws + o);
         RunItemList list;
-        VGA_TRY(ensure_run_items(g, hub_lookups ? hub_lookups : hub_lookups_auto(g), stream, &list));
-        J.lk = g->d_lk;
+        VGA_TRY(ensure_run_items(g, L.scheme, hub_lookups ? hub_lookups : hub_lookups_auto(g, L.scheme), stream,
+                                 &list));
+        J.lk = g->lk[L.scheme].d_lk;
+        J.scheme = L.scheme;
         J.items = list.items;
         J.units = (uint32_t)list.count;
     } else {
@@ -544,7 +547,7 @@ int plan_batch(const vga_job *jobs, int n_jobs, int slice_cap, BatchPlan *B) {
         const bool tabled = tune_table_lookup(jb.graph, &te);
         const int mode = jb.union_mode ? jb.union_mode : (tabled ? te.union_mode : 0);
         const int cap = slice_cap ? slice_cap : (tabled ? te.slice_bytes : 0);
-        const JobLayout L = job_layout(jb.graph->n, jb.p, cap, budget, mode);
+        const JobLayout L = job_layout(jb.graph->n, jb.p, cap, budget, mode, jb.graph->lk_scheme);
         B->idx.push_back(i);
         B->lay.push_back(L);
         B->job_off.push_back(o);

@@ -19,7 +19,7 @@ struct JobDev {
     const uint32_t *comp;
     const uint32_t *lk;      // run-aware union: the graph's range lookups
     const RunItem *items;    // and its work list (nodes, split hubs' chunks)
-    uint8_t *tab;            // table regions T_0..T_4, slice s at tab + s * (kRunLevels + 1) * N * S
+    uint8_t *tab;            // table regions, slice s at tab + s * table_rows(scheme) * N * S
     uint32_t *tab_done;      // per slice: table items finished, over all passes
     uint8_t *regs[2];   // slice-major [m/S][N][S]; pass t reads regs[(t-1)&1], writes regs[t&1]
     double *c[2];       // c_t lives in c[t&1]
@@ -33,6 +33,7 @@ struct JobDev {
     uint32_t units;         // union items per slice: work-list entries (mode 2) or nodes (mode 1)
     int mode;               // 1 one gather per neighbour, 2 per run (sparse tables)
     int tblocks;            // table items per slice (mode 2), TableShape<S>::B rows each
+    int scheme;             // table scheme of the lookups (mode 2)
     uint32_t changed, inc;  // flags of the pass in progress
     int t;                  // passes completed
     int state;              // 0 running, 1 stopped at this step (finalize), 2 done
@@ -41,7 +42,7 @@ struct JobDev {
 // Per-job union variant, slice width and workspace size (regs0, regs1, c0,
 // c1, sum_d, and in mode 2 the sparse tables of every slice and their counters).
 struct JobLayout {
-    int mode = 2, S = 0, slices = 0, tblocks = 0;
+    int mode = 2, S = 0, slices = 0, tblocks = 0, scheme = 0;
     uint64_t bytes = 0;
 };
 
@@ -75,7 +76,7 @@ struct EngineSet {
 
 uint64_t align256(uint64_t x);
 uint64_t l2_budget_bytes(int dev);
-JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode);
+JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode, int scheme);
 // Device view of one analysis in workspace ws; in mode 2 it builds (on first
 // use) the graph's lookups and its work list for hub threshold hub_lookups
 // (0 = automatic).

@@ -271,14 +271,19 @@ __device__ __forceinline__ void lk_stage_init(LkStage &st, int lane) {
     __syncwarp();
 }
 
+// The lookup stream is read once per slice: its lines are marked evict-first in
+// L2 so that they do not push out the slice's table region.
 __device__ __forceinline__ void lk_bulk_load(LkStage &st, int slot, const uint32_t *src, uint32_t bytes) {
     const uint32_t bar = smem_u32(&st.bar[slot]);
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(st.buf[slot])),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(st.buf[slot])),
+        "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+        : "memory");
 }
 
 // Bounded wait for the phase `parity` of a barrier to complete.
@@ -414,16 +419,17 @@ struct TableShape {
 };
 constexpr int kTableSmemBytes = (16 + 15) * 1024;  // largest (B + 15) * S
 
-// Sparse-table rows [r0, r0 + B) of one slice, all levels, straight from the
-// slice's counters: T_0[i] = cur[i] and T_k[i] = max(cur[i .. i + 2^k)) for
-// k = 1..kRunLevels and the rows with i + 2^k <= n.  The rows and their halo
-// are staged once in `buf`; each thread then owns one 16-byte chunk of one
-// output row, copies it to T_0 and folds the 16 rows of its widest window,
-// writing T_1, T_2, T_3, T_4 as the window reaches 2, 4, 8 and 16 rows
-// (tab + k * n * S for level k).  All threads of the CTA (256) take part.
+// Table-region rows [r0, r0 + B) of one slice, straight from the slice's
+// counters: T_0[i] = cur[i] and T_k[i] = max(cur[i .. i + 2^k)) for the
+// scheme's levels k (scheme 0: 1..4; scheme 1: 2 and 4) and the rows with
+// i + 2^k <= n.  The rows and their halo are staged once in `buf`; each thread
+// then owns one 16-byte chunk of one output row, copies it to T_0 and folds
+// the 16 rows of its widest window, writing each kept level as the window
+// reaches 2^k rows (at tab + slot * n * S; scheme 0: slot k, scheme 1: slot
+// k / 2).  All threads of the CTA (256) take part.
 template <int S, bool NIB = false>
 __device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict__ tab, uint32_t n, uint32_t r0,
-                           uint8_t *buf) {
+                           uint8_t *buf, int scheme = 0) {
     using T = TableShape<S>;
     uint4 *b4 = reinterpret_cast<uint4 *>(buf);
     const uint32_t avail = (n - r0 < (uint32_t)T::R) ? n - r0 : (uint32_t)T::R;
@@ -443,7 +449,10 @@ __device__ void table_item(const uint8_t *__restrict__ cur, uint8_t *__restrict_
             acc = RegFmt<NIB>::max4(acc, b4[x + j * T::C16]);
             if ((j & (j + 1)) == 0) {  // window of j + 1 = 2^k rows complete
                 const int k = 31 - __clz(j + 1);
-                if (i + (1u << k) <= n) reinterpret_cast<uint4 *>(tab + ((uint64_t)k * n + i) * S)[c] = acc;
+                const bool kept = scheme == 0 || (k & 1) == 0;
+                const int slot = scheme == 0 ? k : k / 2;
+                if (kept && i + (1u << k) <= n)
+                    reinterpret_cast<uint4 *>(tab + ((uint64_t)slot * n + i) * S)[c] = acc;
             }
         }
     }

@@ -95,13 +95,13 @@ __global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__res
         union_store<S, NIB>(acc, cur, nxt, it.v, lane, flags);
 }
 
-// The slice's table region T_0 .. T_4 (table_item), B rows per CTA of 256
-// threads, in one launch.
+// The slice's table region (table_item: T_0 and the scheme's levels), B rows
+// per CTA of 256 threads, in one launch.
 template <int S, bool NIB>
 __global__ void __launch_bounds__(256) hb_table_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ tab,
-                                                       uint32_t n) {
+                                                       uint32_t n, int scheme) {
     __shared__ __align__(16) uint8_t buf[TableShape<S>::R * S];
-    table_item<S, NIB>(cur, tab, n, blockIdx.x * (uint32_t)TableShape<S>::B, buf);
+    table_item<S, NIB>(cur, tab, n, blockIdx.x * (uint32_t)TableShape<S>::B, buf, scheme);
 }
 
 // Microbenchmark twin of hb_union_kernel: rows drawn from a hash instead of
@@ -234,6 +234,7 @@ struct Plan {
     int slices = 1;
     int warps = 8;         // union kernel warps per CTA
     int mode = kModeRuns;  // union variant
+    int scheme = 0;        // runs mode: table scheme (table_rows(scheme) rows per node and slice)
     uint32_t hub_req = 0;  // runs mode: requested hub threshold (0 = automatic)
     uint32_t hub = 0;      // runs mode: nodes with more lookups than this are split across warps
     RunItemList items;     // runs mode: the union's work list for `hub`
@@ -246,8 +247,8 @@ struct Plan {
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 // Hub threshold of the run-aware union (lookups per work item).
-static uint32_t hub_threshold(const vga_graph *g, uint32_t requested) {
-    return requested > 0 ? requested : hub_lookups_auto(g);
+static uint32_t hub_threshold(const vga_graph *g, int scheme, uint32_t requested) {
+    return requested > 0 ? requested : hub_lookups_auto(g, scheme);
 }
 
 static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P) {
@@ -285,8 +286,15 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     const bool runs_ok = (uint64_t)g->n <= kRunMaxNodes;
     P->mode = req_mode ? req_mode
                        : (tabled && te.union_mode == kModePerEdge) || !runs_ok ? kModePerEdge : kModeRuns;
-    // rows of counters the union reads per slice: the slice, plus the sparse-table levels in runs mode
-    const uint64_t rows_per_node = P->mode == kModeRuns ? (uint64_t)kRunLevels + 1 : 1;
+    // table scheme (runs mode): the graph's own unless the caller asks for one
+    const int levels = tune ? tune->table_levels : 0;
+    if (levels != 0 && levels != 5 && levels != 3) {
+        set_error("table_levels = %d must be 0 (automatic), 5 or 3", levels);
+        return VGA_EINVAL;
+    }
+    P->scheme = levels == 5 ? 0 : levels == 3 ? 1 : g->lk_scheme;
+    // rows of counters the union reads per slice: the slice, or in runs mode its table region
+    const uint64_t rows_per_node = P->mode == kModeRuns ? (uint64_t)table_rows(P->scheme) : 1;
     int S = tune ? tune->slice_bytes : 0;
     if (S != 0) {
         if (S < 16 || S > 1024 || (S & (S - 1)) || (uint32_t)S > P->node_bytes) {
@@ -301,6 +309,7 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         const bool tabled_S = tabled && te.slice_bytes > 0 && !(tune && tune->l2_budget_mb > 0);
         uint64_t budget = (tune && tune->l2_budget_mb > 0) ? (uint64_t)tune->l2_budget_mb << 20
                           : tabled_S                       ? l2_bytes
+                          : P->mode == kModeRuns           ? union_l2_budget(g->device)
                                                            : l2_bytes * 6 / 10;
         S = (int)std::min<uint32_t>(P->node_bytes, tabled_S ? (uint32_t)std::min(te.slice_bytes, 1024) : 1024u);
         while (S > 16 && (uint64_t)S * P->n * rows_per_node > budget) S >>= 1;
@@ -334,7 +343,7 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->off_lc = o;    o = align256(o + 8 * ((uint64_t)P->m + 1));
     P->off_flags = o; o = align256(o + 64);
     P->off_tab = o;
-    if (P->mode == kModeRuns) o = align256(o + (uint64_t)(kRunLevels + 1) * P->n * (uint64_t)S);
+    if (P->mode == kModeRuns) o = align256(o + (uint64_t)table_rows(P->scheme) * P->n * (uint64_t)S);
     P->total = o;
     return VGA_OK;
 }
@@ -369,10 +378,10 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
     if (P.mode == kModeRuns) {
         const unsigned item_blocks = (unsigned)((P.items.count + P.warps - 1) / P.warps);
         const unsigned table_blocks = (unsigned)((P.n + TableShape<SS>::B - 1) / TableShape<SS>::B);
-        hb_table_kernel<SS, NIB><<<table_blocks, 256, 0, stream>>>(c, tab, (uint32_t)P.n);
+        hb_table_kernel<SS, NIB><<<table_blocks, 256, 0, stream>>>(c, tab, (uint32_t)P.n, P.scheme);
         count_launch();
         hb_union_runs_kernel<SS, NIB><<<item_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
-            P.items.items, P.items.count, g->d_lk, c, tab, x, (uint32_t)P.n, flags);
+            P.items.items, P.items.count, g->lk[P.scheme].d_lk, c, tab, x, (uint32_t)P.n, flags);
     } else {
         hb_union_kernel<SS, NIB><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
                                                                     flags);
@@ -415,8 +424,8 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
             pt.edges = g->n_edges;
             if (P.mode == kModeRuns) {
-                pt.gather_bytes = g->lk_total * (uint64_t)P.S;
-                pt.hbm_bytes = 4 * g->lk_total + 16 * P.items.count + 2 * P.n * (uint64_t)P.S;
+                pt.gather_bytes = g->lk[P.scheme].total * (uint64_t)P.S;
+                pt.hbm_bytes = 4 * g->lk[P.scheme].total + 16 * P.items.count + 2 * P.n * (uint64_t)P.S;
             } else {
                 pt.gather_bytes = g->n_edges * (uint64_t)P.S;
                 pt.hbm_bytes = g->n_bytes + 8 * (P.n + 1) + 2 * P.n * (uint64_t)P.S;
@@ -530,9 +539,9 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
     uint32_t *flags = reinterpret_cast<uint32_t *>(base + P.off_flags);
     uint8_t *tab = base + P.off_tab;
     if (P.mode == kModeRuns && P.n > 0) {
-        VGA_TRY(ensure_run_lookups(g, stream));
-        P.hub = hub_threshold(g, P.hub_req);
-        VGA_TRY(ensure_run_items(g, P.hub, stream, &P.items));
+        VGA_TRY(ensure_run_lookups(g, P.scheme, stream));
+        P.hub = hub_threshold(g, P.scheme, P.hub_req);
+        VGA_TRY(ensure_run_items(g, P.scheme, P.hub, stream, &P.items));
     }
 
     bool profiling;
@@ -707,7 +716,7 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     const uint64_t off_lc = o;    o = align256(o + 8 * ((uint64_t)P.m + 1));
     const uint64_t off_flags = o; o = align256(o + 64);
     const uint64_t off_tab = o;
-    if (P.mode == kModeRuns) o = align256(o + (uint64_t)(kRunLevels + 1) * n * (uint64_t)P.S);
+    if (P.mode == kModeRuns) o = align256(o + (uint64_t)table_rows(P.scheme) * n * (uint64_t)P.S);
     const int rc = s->ws.alloc(o);
     if (rc != VGA_OK) {
         delete s;
@@ -725,10 +734,10 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     s->zeros_off = align256(8 * n);
     s->block_bytes = s->zeros_off + align256(4 * n);
     if (P.mode == kModeRuns && n > 0) {
-        int r = ensure_run_lookups(g, 0);
+        int r = ensure_run_lookups(g, P.scheme, 0);
         if (r == VGA_OK) {
-            P.hub = hub_threshold(g, P.hub_req);
-            r = ensure_run_items(g, P.hub, 0, &P.items);
+            P.hub = hub_threshold(g, P.scheme, P.hub_req);
+            r = ensure_run_items(g, P.scheme, P.hub, 0, &P.items);
         }
         if (r != VGA_OK) {
             delete s;

@@ -24,10 +24,13 @@
 namespace vga {
 namespace {
 
-// One warp per node: write node v's lookups at lk[lk_off[v] ...] (their
-// counts were taken when the graph was validated).
+// One warp per node.  WRITE: write node v's lookups for table scheme `scheme`
+// at lk[lk_off[v] ...]; otherwise store their number in cnt[v] (the scheme
+// chosen for the graph is counted by validation at load instead).
+template <bool WRITE>
 __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes, uint32_t n,
-                                   const uint64_t *__restrict__ lk_off, uint32_t *__restrict__ lk) {
+                                   int scheme, const uint64_t *__restrict__ lk_off, uint32_t *__restrict__ lk,
+                                   uint32_t *__restrict__ cnt) {
     __shared__ uint32_t s_ids[8][128];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -39,7 +42,8 @@ __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8
     const uint64_t end = off[v + 1];
     uint32_t base = 0;
     RunTracker rt;
-    rt.out = lk_off[v];
+    rt.scheme = scheme;
+    rt.out = WRITE ? lk_off[v] : 0;
     while (pos < end) {
         int advance = 0;
         uint32_t next = 0;
@@ -48,64 +52,96 @@ __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8
                                                       unused);
         if (c == 0) break;  // cannot happen on a validated graph
         __syncwarp();
-        rt.window<true>(ids, c, lane, n, lk);
+        rt.window<WRITE>(ids, c, lane, n, lk);
         __syncwarp();
         base = next;
         pos += (uint64_t)advance;
     }
-    rt.finish<true>(lane, n, lk);
+    rt.finish<WRITE>(lane, n, lk);
+    if (!WRITE && lane == 0) cnt[v] = (uint32_t)rt.out;
 }
 
 }  // namespace
 
-int ensure_run_lookups(const vga_graph *g, cudaStream_t stream) {
+uint64_t union_l2_budget(int device) {
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 3 / 4;
+}
+
+int table_scheme_auto(uint32_t n, int device) {
+    return (uint64_t)table_rows(0) * n * 128u > union_l2_budget(device) ? 1 : 0;
+}
+
+int ensure_run_lookups(const vga_graph *g, int scheme, cudaStream_t stream) {
     std::lock_guard<std::mutex> lock(g->lk_mu);
-    if (g->lk_ready) return VGA_OK;
+    if (scheme < 0 || scheme >= kTableSchemes) {
+        set_error("internal: table scheme %d", scheme);
+        return VGA_EINVAL;
+    }
+    vga_graph::RunLookups &L = g->lk[scheme];
+    if (L.ready) return VGA_OK;
     if ((uint64_t)g->n > kRunMaxNodes) {
         set_error("run-aware union supports at most 2^29 nodes (graph has %u)", g->n);
         return VGA_EINVAL;
     }
     const uint32_t n = g->n;
-    const std::vector<uint64_t> &h_off = g->h_lk_off;  // prefix sums of the counts taken at load
-    const uint64_t total = h_off[n];
+    const int warps = 8;
+    const unsigned blocks = (unsigned)(((uint64_t)n + warps - 1) / warps);
+    if (L.h_off.empty()) {  // a scheme other than the one counted at load
+        std::vector<uint32_t> h_cnt(n);
+        L.h_off.assign((size_t)n + 1, 0);
+        if (n) {
+            DeviceBuffer d_cnt;
+            VGA_TRY(d_cnt.alloc(4 * (size_t)n));
+            run_lookups_kernel<false><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, scheme, nullptr,
+                                                                         nullptr, d_cnt.as<uint32_t>());
+            count_launch();
+            VGA_CHECK_CUDA(cudaGetLastError());
+            VGA_CHECK_CUDA(cudaMemcpyAsync(h_cnt.data(), d_cnt.ptr, 4 * (size_t)n, cudaMemcpyDeviceToHost, stream));
+            VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+        }
+        for (uint32_t v = 0; v < n; v++) L.h_off[v + 1] = L.h_off[v] + h_cnt[v];
+        L.total = L.h_off[n];
+    }
+    const uint64_t total = L.total;
     DeviceBuffer d_off, d_lk;
     VGA_TRY(d_off.alloc(8 * ((size_t)n + 1)));
     VGA_TRY(d_lk.alloc(4 * ((size_t)total + 4)));  // + one 16-byte group: TMA copies round up to whole groups
     VGA_CHECK_CUDA(cudaMemsetAsync(d_lk.as<uint8_t>() + 4 * total, 0, 16, stream));
-    VGA_CHECK_CUDA(cudaMemcpyAsync(d_off.ptr, h_off.data(), 8 * ((size_t)n + 1), cudaMemcpyHostToDevice, stream));
+    VGA_CHECK_CUDA(cudaMemcpyAsync(d_off.ptr, L.h_off.data(), 8 * ((size_t)n + 1), cudaMemcpyHostToDevice, stream));
     if (n) {
-        const int warps = 8;
-        const unsigned blocks = (unsigned)(((uint64_t)n + warps - 1) / warps);
-        run_lookups_kernel<<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, d_off.as<uint64_t>(),
-                                                              d_lk.as<uint32_t>());
+        run_lookups_kernel<true><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, scheme,
+                                                                    d_off.as<uint64_t>(), d_lk.as<uint32_t>(),
+                                                                    nullptr);
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
-    g->d_lk_off = static_cast<uint64_t *>(d_off.release());
-    g->d_lk = static_cast<uint32_t *>(d_lk.release());
-    g->lk_total = total;
-    g->lk_ready = true;
+    L.d_off = static_cast<uint64_t *>(d_off.release());
+    L.d_lk = static_cast<uint32_t *>(d_lk.release());
+    L.ready = true;
     return VGA_OK;
 }
 
-uint32_t hub_lookups_auto(const vga_graph *g) {
+uint32_t hub_lookups_auto(const vga_graph *g, int scheme) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    const uint64_t share = g->lk_total / ((uint64_t)(sms > 0 ? sms : 1) * 64);
+    const uint64_t share = g->lk[scheme].total / ((uint64_t)(sms > 0 ? sms : 1) * 64);
     return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(share / 2, 2048), 0x7fffffffull);
 }
 
-int ensure_run_items(const vga_graph *g, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out) {
-    VGA_TRY(ensure_run_lookups(g, stream));
+int ensure_run_items(const vga_graph *g, int scheme, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out) {
+    VGA_TRY(ensure_run_lookups(g, scheme, stream));
     std::lock_guard<std::mutex> lock(g->lk_mu);
     if (hub_lookups == 0) hub_lookups = 1;
-    for (const vga_graph::RunItemSet &r : g->lk_items)
+    vga_graph::RunLookups &L = g->lk[scheme];
+    for (const vga_graph::RunItemSet &r : L.items)
         if (r.hub_lookups == hub_lookups) {
             *out = RunItemList{static_cast<const RunItem *>(r.d_items), r.count, r.hub_items, r.hubs};
             return VGA_OK;
         }
-    const std::vector<uint64_t> &off = g->h_lk_off;
+    const std::vector<uint64_t> &off = L.h_off;
     std::vector<RunItem> items;
     items.reserve((size_t)g->n);
     uint32_t hubs = 0;
@@ -130,8 +166,8 @@ int ensure_run_items(const vga_graph *g, uint32_t hub_lookups, cudaStream_t stre
         VGA_CHECK_CUDA(cudaMemcpyAsync(d.ptr, items.data(), sizeof(RunItem) * items.size(), cudaMemcpyHostToDevice,
                                        stream));
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));  // the host vector goes out of scope
-    g->lk_items.push_back(vga_graph::RunItemSet{hub_lookups, (uint64_t)items.size(), hub_items, hubs, d.release()});
-    const vga_graph::RunItemSet &r = g->lk_items.back();
+    L.items.push_back(vga_graph::RunItemSet{hub_lookups, (uint64_t)items.size(), hub_items, hubs, d.release()});
+    const vga_graph::RunItemSet &r = L.items.back();
     *out = RunItemList{static_cast<const RunItem *>(r.d_items), r.count, r.hub_items, r.hubs};
     return VGA_OK;
 }

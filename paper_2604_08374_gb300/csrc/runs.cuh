@@ -8,26 +8,36 @@
 namespace vga {
 namespace {
 
-// Number of lookups covering the run [a, a + L).
-__device__ __forceinline__ uint32_t run_lookup_count(uint32_t L) {
-    if (L < 32u) {
-        const uint32_t k = 31u - __clz(L);
-        return (L == (1u << k)) ? 1u : 2u;
+// Window width w and region slot of the lookups covering a run of length L:
+// the widest kept window not longer than the run (scheme 0: 2^floor(log2 L)
+// up to 16; scheme 1: 1, 4 or 16).  ceil(L / w) windows cover it, the last
+// one ending at the run's end.
+__device__ __forceinline__ void run_window(uint32_t L, int scheme, uint32_t &w, uint32_t &slot) {
+    if (scheme == 0) {
+        const uint32_t k = L < 16u ? 31u - __clz(L) : 4u;
+        w = 1u << k;
+        slot = k;
+    } else {
+        slot = L < 4u ? 0u : (L < 16u ? 1u : 2u);
+        w = 1u << (2u * slot);
     }
-    return (L >> 4) + ((L & 15u) ? 1u : 0u);
 }
 
-// Lookups covering the run [a, a + L) as table row indices k * n + i.
-__device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_t n, uint32_t *out) {
-    if (L < 32u) {
-        const uint32_t k = 31u - __clz(L);
-        out[0] = k * n + a;
-        if (L != (1u << k)) out[1] = k * n + (a + L - (1u << k));
-        return;
-    }
-    const uint32_t full = L >> 4;
-    for (uint32_t j = 0; j < full; j++) out[j] = 4u * n + (a + 16u * j);
-    if (L & 15u) out[full] = 4u * n + (a + L - 16u);
+// Number of lookups covering the run [a, a + L).
+__device__ __forceinline__ uint32_t run_lookup_count(uint32_t L, int scheme) {
+    uint32_t w, slot;
+    run_window(L, scheme, w, slot);
+    return (L + w - 1u) / w;
+}
+
+// Lookups covering the run [a, a + L) as table row indices slot * n + i.
+__device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_t n, int scheme, uint32_t *out) {
+    uint32_t w, slot;
+    run_window(L, scheme, w, slot);
+    const uint32_t c = (L + w - 1u) / w;
+    const uint32_t base = slot * n + a;
+    for (uint32_t j = 0; j + 1u < c; j++) out[j] = base + w * j;
+    out[c - 1u] = base + L - w;
 }
 
 // Runs of consecutive ids across a node's decoded windows.  Per window the
@@ -39,6 +49,8 @@ __device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_
 struct RunTracker {
     uint32_t run_a = 0, run_len = 0;  // the run still open at the end of the last window
     uint64_t out = 0;
+
+    int scheme = 0;  // table scheme of the lookups
 
     template <bool WRITE>
     __device__ __forceinline__ void window(const uint32_t *ids, int c, int lane, uint32_t n, uint32_t *lk) {
@@ -74,7 +86,7 @@ struct RunTracker {
         // lookups of this lane's complete runs (and, on lane 0, of the carried run)
         const bool carried = run_len > 0 && first != kNone;
         const uint32_t carried_len = carried ? run_len + (uint32_t)first : 0u;
-        uint32_t my = (lane == 0 && carried) ? run_lookup_count(carried_len) : 0u;
+        uint32_t my = (lane == 0 && carried) ? run_lookup_count(carried_len, scheme) : 0u;
         uint32_t len[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -84,7 +96,7 @@ struct RunTracker {
                 const int next = later ? j0 + __ffs(later) - 1 : after;
                 if (next != kNone) {
                     len[k] = (uint32_t)(next - (j0 + k));
-                    my += run_lookup_count(len[k]);
+                    my += run_lookup_count(len[k], scheme);
                 }
             }
         }
@@ -97,14 +109,14 @@ struct RunTracker {
         if (WRITE) {
             uint64_t at = out + (incl - my);
             if (lane == 0 && carried) {
-                run_lookup_write(run_a, carried_len, n, lk + at);
-                at += run_lookup_count(carried_len);
+                run_lookup_write(run_a, carried_len, n, scheme, lk + at);
+                at += run_lookup_count(carried_len, scheme);
             }
 #pragma unroll
             for (int k = 0; k < 4; k++)
                 if (len[k]) {
-                    run_lookup_write(id[k], len[k], n, lk + at);
-                    at += run_lookup_count(len[k]);
+                    run_lookup_write(id[k], len[k], n, scheme, lk + at);
+                    at += run_lookup_count(len[k], scheme);
                 }
         }
         out += __shfl_sync(0xffffffffu, incl, 31);
@@ -121,8 +133,8 @@ struct RunTracker {
     template <bool WRITE>
     __device__ __forceinline__ void finish(int lane, uint32_t n, uint32_t *lk) {
         if (run_len > 0) {
-            if (WRITE && lane == 0) run_lookup_write(run_a, run_len, n, lk + out);
-            out += run_lookup_count(run_len);
+            if (WRITE && lane == 0) run_lookup_write(run_a, run_len, n, scheme, lk + out);
+            out += run_lookup_count(run_len, scheme);
             run_len = 0;
         }
     }

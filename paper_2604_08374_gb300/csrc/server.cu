@@ -352,7 +352,7 @@ int vga_server_submit(vga_server *S, const vga_graph *g, int p, int d, uint64_t 
     r->t_submit = Clock::now();
     r->lane = g->n > (uint32_t)S->cfg.solo_nodes ? 1 : 0;
     if (r->lane == 0) {
-        r->L = job_layout(g->n, p, 0, S->l2_budget, 0);
+        r->L = job_layout(g->n, p, 0, S->l2_budget, 0, g->lk_scheme);
         r->bytes = request_bytes_batched(r->L, g->n);
     } else {
         uint64_t ws = 0;

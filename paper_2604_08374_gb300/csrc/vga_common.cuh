@@ -26,14 +26,8 @@ struct vga_graph {
     uint8_t *d_bytes = nullptr;     // n_bytes + kBytePad
     uint32_t *d_degree = nullptr;   // n
     uint32_t *d_comp = nullptr;     // n, or nullptr: every node in one component of size n
-    // Range lookups of the run-aware union, built on first use (see runs.cu):
-    // node v's lookups are d_lk[d_lk_off[v] .. d_lk_off[v+1]).
-    mutable std::mutex lk_mu;
-    mutable uint64_t *d_lk_off = nullptr;  // n+1
-    mutable uint32_t *d_lk = nullptr;      // lk_total
-    mutable uint64_t lk_total = 0;
-    mutable bool lk_ready = false;
-    mutable std::vector<uint64_t> h_lk_off;  // host copy of d_lk_off
+    // Range lookups of the run-aware union, per table scheme (runs.cuh), built
+    // on first use: node v's lookups are lk[s].d_lk[lk[s].d_off[v] .. d_off[v+1]).
     // Work lists of the run-aware union, one per hub threshold (ensure_run_items).
     struct RunItemSet {
         uint32_t hub_lookups;
@@ -41,7 +35,17 @@ struct vga_graph {
         uint32_t hubs;
         void *d_items;
     };
-    mutable std::vector<RunItemSet> lk_items;
+    struct RunLookups {
+        uint64_t *d_off = nullptr;    // n+1
+        uint32_t *d_lk = nullptr;     // total (+ 4 zero entries)
+        uint64_t total = 0;
+        std::vector<uint64_t> h_off;  // prefix sums of the counts (empty until counted)
+        bool ready = false;           // d_off and d_lk built
+        std::vector<RunItemSet> items;
+    };
+    mutable std::mutex lk_mu;
+    mutable RunLookups lk[2];
+    int lk_scheme = 0;  // the table scheme chosen for this graph (counted at load)
 };
 
 namespace vga {
@@ -134,12 +138,24 @@ struct PinnedBuffer {
 
 // Range lookups of the run-aware union.  A neighbour list in raster order is a
 // sequence of runs of consecutive ids; the maximum over a run [a, a+L) is read
-// from a sparse table T_k[i] = max(cur[i .. i + 2^k)) for k = 0..kRunLevels.
-constexpr int kRunLevels = 4;  // sparse-table levels T_1..T_4: windows of 2, 4, 8, 16 rows
-// A lookup is the row index r = k * N + i of window T_k[i] in a slice's table
-// region, where T_0 (a copy of the slice) and T_1..T_4 lie one after another
-// (kRunLevels + 1 rows per node); r < 5 N must fit in 32 bits.
+// from a slice's table region: rows T_k[i] = max(cur[i .. i + 2^k)) for the
+// window widths 2^k of the graph's table scheme, one N-row level after
+// another.  A lookup is the row index r = slot * N + i of T_k[i], slot being
+// the level's place in the region.
+//   scheme 0: k = 0, 1, 2, 3, 4 (5 rows per node); fewest lookups.
+//   scheme 1: k = 0, 2, 4 (3 rows per node); for graphs whose 5-row region
+//             would not fit the L2 at 128-byte slices.
+constexpr int kRunLevels = 4;  // widest window 2^4 = 16 rows
+constexpr int kTableSchemes = 2;
+__host__ __device__ constexpr int table_rows(int scheme) { return scheme == 0 ? 5 : 3; }
+// r < 5 N must fit in 32 bits.
 constexpr uint64_t kRunMaxNodes = 1ull << 29;
+
+// The table scheme for a graph of n nodes on `device`: 1 when a 5-row region
+// of 128-byte slices would exceed the L2 share the union aims at, else 0.
+int table_scheme_auto(uint32_t n, int device);
+// L2 share the run-aware union's table region aims at (bytes).
+uint64_t union_l2_budget(int device);
 
 // One warp's work in the run-aware union: the lookups lk[b .. b + cnt) of node
 // v & ~kHubChunk.  A node with more lookups than the hub threshold is split
@@ -160,12 +176,13 @@ struct RunItemList {
     uint64_t count = 0, hub_items = 0;
     uint32_t hubs = 0;
 };
-int ensure_run_items(const vga_graph *g, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out);
+int ensure_run_items(const vga_graph *g, int scheme, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out);
 
 // Automatic hub threshold (lookups per work item): half of one warp's even
 // share of a slice's lookups when every SM holds 64 warps, and at least 2048,
-// so only nodes that would outlast the rest of a launch are split.
-uint32_t hub_lookups_auto(const vga_graph *g);
+// so only nodes that would outlast the rest of a launch are split.  The
+// scheme's lookups must have been counted (ensure_run_lookups).
+uint32_t hub_lookups_auto(const vga_graph *g, int scheme);
 
 // Autotuner table (autotune.cu): the installed entry for g's degree bucket.
 bool tune_table_lookup(const vga_graph *g, vga_tune_entry *out);
@@ -174,8 +191,9 @@ bool tune_table_lookup(const vga_graph *g, vga_tune_entry *out);
 int run_timed(const vga_graph *g, int p, int d, uint64_t seed, const vga_tuning *tune, cudaStream_t stream,
               double *union_ms, int *iterations);
 
-// Build the graph's lookup list on first use (thread-safe); no-op afterwards.
-int ensure_run_lookups(const vga_graph *g, cudaStream_t stream);
+// Build the graph's lookup list for a table scheme on first use (thread-safe);
+// no-op afterwards.
+int ensure_run_lookups(const vga_graph *g, int scheme, cudaStream_t stream);
 
 // Creates a graph object around device offsets and bytes: validates the
 // stream on the device, derives degrees, E and the run-aware union's lookup

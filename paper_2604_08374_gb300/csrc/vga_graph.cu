@@ -26,7 +26,7 @@ void clear_error() { g_err[0] = 0; }
 // lookups the run-aware union will need (runs.cuh), and folds E, the maximum
 // degree and the lowest bad node id into global counters.
 __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes, uint32_t n,
-                                uint32_t v0, uint32_t v1, uint32_t *__restrict__ degree,
+                                uint32_t v0, uint32_t v1, int scheme, uint32_t *__restrict__ degree,
                                 uint32_t *__restrict__ lk_count, unsigned long long *__restrict__ edge_total,
                                 uint32_t *__restrict__ max_degree, uint32_t *__restrict__ bad_node) {
     __shared__ uint32_t s_ids[8][128];
@@ -42,6 +42,7 @@ __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t 
     uint32_t cnt = 0;
     bool ok = true;
     RunTracker rt;
+    rt.scheme = scheme;
     while (pos < end) {
         int advance = 0;
         uint64_t next = 0;
@@ -70,13 +71,13 @@ __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t 
 }
 
 static int launch_validate(const uint64_t *d_offsets, const uint8_t *d_bytes, uint32_t n, uint32_t v0, uint32_t v1,
-                           uint32_t *degree, uint32_t *lk_count, unsigned long long *d_edges, uint32_t *d_maxdeg,
-                           uint32_t *d_bad, cudaStream_t stream) {
+                           int scheme, uint32_t *degree, uint32_t *lk_count, unsigned long long *d_edges,
+                           uint32_t *d_maxdeg, uint32_t *d_bad, cudaStream_t stream) {
     if (v1 <= v0) return VGA_OK;
     const int warps = 8;
     const uint64_t blocks = ((uint64_t)(v1 - v0) + warps - 1) / warps;
-    validate_kernel<<<(unsigned)blocks, warps * 32, 0, stream>>>(d_offsets, d_bytes, n, v0, v1, degree, lk_count,
-                                                                  d_edges, d_maxdeg, d_bad);
+    validate_kernel<<<(unsigned)blocks, warps * 32, 0, stream>>>(d_offsets, d_bytes, n, v0, v1, scheme, degree,
+                                                                  lk_count, d_edges, d_maxdeg, d_bad);
     count_launch();
     VGA_CHECK_CUDA(cudaGetLastError());
     return VGA_OK;
@@ -90,6 +91,9 @@ int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t
     DeviceBuffer offsets, bytes, degree, comp, counters, lk_count;
     offsets.ptr = d_offsets;
     bytes.ptr = d_bytes;
+    int device = 0;
+    VGA_CHECK_CUDA(cudaGetDevice(&device));
+    const int scheme = table_scheme_auto(n, device);  // the lookups counted during validation
     VGA_TRY(degree.alloc(sizeof(uint32_t) * (size_t)(n ? n : 1)));
     VGA_TRY(lk_count.alloc(sizeof(uint32_t) * (size_t)(n ? n : 1)));
     if (comp_host) {
@@ -129,15 +133,15 @@ int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t
             const uint32_t upto = c1 == n_bytes ? n
                                                 : (uint32_t)(std::upper_bound(h_offsets + 1, h_offsets + n + 1, c1) -
                                                              (h_offsets + 1));
-            VGA_TRY(launch_validate(d_offsets, d_bytes, n, done, upto, degree.as<uint32_t>(), lk_count.as<uint32_t>(),
-                                    d_edges, d_maxdeg, d_bad, vs));
+            VGA_TRY(launch_validate(d_offsets, d_bytes, n, done, upto, scheme, degree.as<uint32_t>(),
+                                    lk_count.as<uint32_t>(), d_edges, d_maxdeg, d_bad, vs));
             done = std::max(done, upto);
         }
         VGA_CHECK_CUDA(cudaEventRecord(ev, vs));
         VGA_CHECK_CUDA(cudaStreamWaitEvent(stream, ev, 0));
     } else if (n > 0) {
-        VGA_TRY(launch_validate(d_offsets, d_bytes, n, 0, n, degree.as<uint32_t>(), lk_count.as<uint32_t>(), d_edges,
-                                d_maxdeg, d_bad, stream));
+        VGA_TRY(launch_validate(d_offsets, d_bytes, n, 0, n, scheme, degree.as<uint32_t>(), lk_count.as<uint32_t>(),
+                                d_edges, d_maxdeg, d_bad, stream));
     }
     uint8_t host_counters[16];
     std::vector<uint32_t> h_cnt(n);
@@ -168,9 +172,11 @@ int finish_graph_load(uint32_t n, uint64_t n_bytes, uint64_t *d_offsets, uint8_t
     g->d_degree = static_cast<uint32_t *>(degree.release());
     g->d_comp = static_cast<uint32_t *>(comp.release());
     // offsets of the run-aware union's lookups (the list itself is built on first use)
-    g->h_lk_off.assign((size_t)n + 1, 0);
-    for (uint32_t v = 0; v < n; v++) g->h_lk_off[v + 1] = g->h_lk_off[v] + h_cnt[v];
-    g->lk_total = g->h_lk_off[n];
+    g->lk_scheme = scheme;
+    vga_graph::RunLookups &L = g->lk[scheme];
+    L.h_off.assign((size_t)n + 1, 0);
+    for (uint32_t v = 0; v < n; v++) L.h_off[v + 1] = L.h_off[v] + h_cnt[v];
+    L.total = L.h_off[n];
     *out = g;
     return VGA_OK;
 }
@@ -304,9 +310,11 @@ void vga_graph_free(vga_graph *g) {
     cudaFree(g->d_bytes);
     cudaFree(g->d_degree);
     if (g->d_comp) cudaFree(g->d_comp);
-    if (g->d_lk_off) cudaFree(g->d_lk_off);
-    if (g->d_lk) cudaFree(g->d_lk);
-    for (const vga_graph::RunItemSet &r : g->lk_items) cudaFree(r.d_items);
+    for (const vga_graph::RunLookups &L : g->lk) {
+        if (L.d_off) cudaFree(L.d_off);
+        if (L.d_lk) cudaFree(L.d_lk);
+        for (const vga_graph::RunItemSet &r : L.items) cudaFree(r.d_items);
+    }
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     delete g;
 }

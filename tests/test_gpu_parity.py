@@ -428,3 +428,46 @@ def test_hub_lookups_rejects_negative(vga):
     with vga.vga_graph_load(off, b) as g:
         with pytest.raises(vga.VgaError):
             vga.hyperball_run_trace(g, 8, 1, max_trace=1, union_mode=2, hub_lookups=-3)
+
+
+# ----------------------------------------------------------------------------
+# table schemes of the run-aware union (5 rows: windows 1..16; 3 rows: 1, 4, 16)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("levels,p,S,bits,hub", [(3, 10, 0, 8, 0), (3, 8, 16, 8, 0), (3, 12, 128, 8, 0), (5, 10, 64, 8, 0),
+                                                 (3, 10, 64, 4, 0), (3, 8, 32, 8, 5)])
+def test_table_levels_bit_exact(vga, levels, p, S, bits, hub):
+    _, off, b, _ = tiny_graph(1)
+    ref = oracle.hyperball(off, b, p, 0, seed=77, trace=12, reg_bits=bits)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, p, 0, seed=77, max_trace=12, slice_bytes=S, union_mode=2,
+                                      register_bits=0 if bits == 8 else bits, hub_lookups=hub, table_levels=levels)
+        # the other scheme on the same graph object: its own lookup list
+        other = vga.hyperball_run_trace(g, p, 0, seed=77, max_trace=12, slice_bytes=S, union_mode=2,
+                                        register_bits=0 if bits == 8 else bits, table_levels=8 - levels)
+    assert_same_run(got, ref)
+    assert_same_run(other, ref)
+
+
+@pytest.mark.parametrize("grid", ["open40x30", "open1x300", "comb"])
+def test_table_levels_long_runs(vga, grid):
+    # runs of every length up to N-1: windows of 1, 4 and 16 rows, 16-row pieces
+    if grid == "open40x30":
+        obst = workloads.open_grid(40, 30)
+    elif grid == "open1x300":
+        obst = workloads.open_grid(300, 1)
+    else:
+        obst = workloads.open_grid(33, 21)
+        obst[2:19:2, 3:30] = 1
+    off, b, cells = oracle.build_graph(obst)
+    ref = oracle.hyperball(off, b, 8, 0, seed=2, trace=6)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, 8, 0, seed=2, max_trace=6, union_mode=2, table_levels=3)
+    assert_same_run(got, ref)
+
+
+def test_table_levels_rejects_bad_value(vga):
+    _, off, b, _ = tiny_graph(1)
+    with vga.vga_graph_load(off, b) as g:
+        with pytest.raises(vga.VgaError):
+            vga.hyperball_run_trace(g, 8, 1, max_trace=1, union_mode=2, table_levels=4)
