@@ -90,6 +90,8 @@ def parse_args():
     ap.add_argument("--autotune", action="store_true",
                     help="run the per-degree-bucket autotuner on the workload's graphs before timing")
     ap.add_argument("--hub-lookups", type=int, default=0, help="force the run-aware hub threshold (0 = automatic)")
+    ap.add_argument("--table-levels", type=int, default=0, choices=[0, 3, 5],
+                    help="run-aware table rows per node: 5 (windows 1..16), 3 (1, 4, 16), 0 = automatic")
     ap.add_argument("--sharded", action="store_true",
                     help="N > 1: split one analysis over the ranks by register slice (strong scaling) instead of "
                          "running one replica per rank")
@@ -367,12 +369,15 @@ def run_ours(args, dist: Dist):
                 return hyperball_run_sharded(g, args.p, d, args.seed, md, ball, slice_bytes=args.slice_bytes,
                                              warps_per_cta=args.warps, union_mode=args.union_mode,
                                              register_bits=0 if args.register_bits == 8 else args.register_bits,
-                                             hub_lookups=args.hub_lookups)
-        return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=ws, stream=stream,
+                                             hub_lookups=args.hub_lookups, table_levels=args.table_levels)
+        # a forced slice width or table scheme sizes its own workspace
+        forced = args.slice_bytes or args.table_levels
+        return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=None if forced else ws,
+                                     stream=stream,
                                      slice_bytes=args.slice_bytes, warps_per_cta=args.warps,
                                      union_mode=args.union_mode if union_mode is None else union_mode,
                                      register_bits=0 if args.register_bits == 8 else args.register_bits,
-                                     hub_lookups=args.hub_lookups)
+                                     hub_lookups=args.hub_lookups, table_levels=args.table_levels)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -515,7 +520,8 @@ def run_ours(args, dist: Dist):
             "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
                        "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode, "order": args.order,
-                       "register_bits": args.register_bits, "autotune": tuned,
+                       "register_bits": args.register_bits, "table_levels": args.table_levels or "auto",
+                       "autotune": tuned,
                        "parallelism": f"register shards x{dist.world}" if sharded else f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",
                        "graph_build_seconds": build_s},
