@@ -90,6 +90,8 @@ def parse_args():
     ap.add_argument("--autotune", action="store_true",
                     help="run the per-degree-bucket autotuner on the workload's graphs before timing")
     ap.add_argument("--hub-lookups", type=int, default=0, help="force the run-aware hub threshold (0 = automatic)")
+    ap.add_argument("--l2-window", type=int, default=0, choices=[0, 1],
+                    help="1: mark the union's table region persisting in L2 (access-policy window)")
     ap.add_argument("--table-levels", type=int, default=0, choices=[0, 3, 5],
                     help="run-aware table rows per node: 5 (windows 1..16), 3 (1, 4, 16), 0 = automatic")
     ap.add_argument("--sharded", action="store_true",
@@ -377,7 +379,8 @@ def run_ours(args, dist: Dist):
                                      slice_bytes=args.slice_bytes, warps_per_cta=args.warps,
                                      union_mode=args.union_mode if union_mode is None else union_mode,
                                      register_bits=0 if args.register_bits == 8 else args.register_bits,
-                                     hub_lookups=args.hub_lookups, table_levels=args.table_levels)
+                                     hub_lookups=args.hub_lookups, table_levels=args.table_levels,
+                                     l2_window=args.l2_window)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -521,6 +524,7 @@ def run_ours(args, dist: Dist):
             "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
                        "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode, "order": args.order,
                        "register_bits": args.register_bits, "table_levels": args.table_levels or "auto",
+                       "l2_window": args.l2_window,
                        "autotune": tuned,
                        "parallelism": f"register shards x{dist.world}" if sharded else f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",

@@ -191,7 +191,11 @@ typedef struct vga_tuning {
                             16: lets wider slices fit the L2); 0 = automatic (3 when five
                             rows of 128-byte slices would exceed 3/4 of the L2).  A
                             non-automatic choice builds its own lookup list on first use. */
-    int reserved[1];
+    int l2_window;       /* 1: during the run, mark the union's table region (mode 2) or
+                            register slice (mode 1) persisting in L2 through an access-
+                            policy window on the stream, with the process's persisting L2
+                            set-aside raised to cover it; both are put back afterwards.
+                            0: off (default; the lookup stream is evict-first anyway)      */
 } vga_tuning;
 
 /*

@@ -32,7 +32,7 @@ vp, i32, u32, u64, i64, f64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_i
 class VgaTuning(C.Structure):
     _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
                 ("union_mode", C.c_int), ("register_bits", C.c_int), ("hub_lookups", C.c_int),
-                ("table_levels", C.c_int), ("reserved", C.c_int * 1)]
+                ("table_levels", C.c_int), ("l2_window", C.c_int)]
 
 
 class VgaJob(C.Structure):
@@ -160,13 +160,14 @@ def _ptr(a) -> int | None:
 
 
 def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0, register_bits=0, hub_lookups=0,
-            table_levels=0):
+            table_levels=0, l2_window=0):
     if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode or register_bits or hub_lookups
-            or table_levels):
+            or table_levels or l2_window):
         return None
     t = VgaTuning()
     t.slice_bytes, t.warps_per_cta, t.l2_budget_mb, t.union_mode = slice_bytes, warps_per_cta, l2_budget_mb, union_mode
     t.register_bits, t.hub_lookups, t.table_levels = register_bits, hub_lookups, table_levels
+    t.l2_window = l2_window
     return C.pointer(t)
 
 
@@ -320,14 +321,14 @@ def hyperball_workspace_bytes(g: Graph, p: int) -> int:
 def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
                       workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
                       l2_budget_mb: int = 0, union_mode: int = 0, register_bits: int = 0,
-                      hub_lookups: int = 0, table_levels: int = 0) -> int:
+                      hub_lookups: int = 0, table_levels: int = 0, l2_window: int = 0) -> int:
     """Algorithm 1 into device tensors (float64, N each); returns passes run."""
     it = C.c_int()
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
                                    _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode, register_bits,
-                                           hub_lookups, table_levels)))
+                                           hub_lookups, table_levels, l2_window)))
     return it.value
 
 

@@ -351,6 +351,46 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
 
 static std::atomic<uint64_t> g_kernel_launches{0};
 
+// Access-policy window (vga_tuning.l2_window): the union's gather source marked
+// persisting in L2 on the run's stream, the persisting set-aside raised to fit;
+// both restored when the run ends.  In mode 1 the window covers the first
+// register slice of `cur` (the slice a launch gathers from moves every launch,
+// so only the first of each pass benefits; mode 2 reuses one table region).
+struct L2Window {
+    cudaStream_t stream = nullptr;
+    size_t old_limit = 0;
+    cudaStreamAttrValue old_attr{};
+    bool active = false;
+    int open(cudaStream_t s, void *base, uint64_t bytes, int device) {
+        int max_persist = 0, max_window = 0;
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, device);
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, device);
+        if (max_persist <= 0 || max_window <= 0 || !s) return VGA_OK;  // not supported, or the legacy stream
+        VGA_CHECK_CUDA(cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize));
+        VGA_CHECK_CUDA(cudaStreamGetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &old_attr));
+        const size_t window = (size_t)std::min<uint64_t>(bytes, (uint64_t)max_window);
+        const size_t setaside = std::min<size_t>(window, (size_t)max_persist);
+        VGA_CHECK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, setaside));
+        cudaStreamAttrValue a{};
+        a.accessPolicyWindow.base_ptr = base;
+        a.accessPolicyWindow.num_bytes = window;
+        a.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)setaside / (double)window);
+        a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        VGA_CHECK_CUDA(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &a));
+        stream = s;
+        active = true;
+        return VGA_OK;
+    }
+    ~L2Window() {
+        if (!active) return;
+        cudaStreamSynchronize(stream);
+        cudaStreamSetAttribute(stream, cudaStreamAttributeAccessPolicyWindow, &old_attr);
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+    }
+};
+
 // Benchmark counters (vga_profile_*): union launches are bracketed by CUDA
 // events on their stream while profiling is on; the events are read after the
 // run's final synchronisation.
@@ -574,6 +614,12 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         if (max_trace >= 0) VGA_TRY(copy_trace(P, cur, c_prev, 0, trace_regs, trace_c, stream));
         uint32_t hflags[3];
         VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 12, stream));
+        L2Window window;
+        if (tune && tune->l2_window) {
+            // the bytes every union launch gathers from: the table region, or the register slices
+            const uint64_t bytes = P.mode == kModeRuns ? (uint64_t)table_rows(P.scheme) * P.n * P.S : P.n * P.S;
+            VGA_TRY(window.open(stream, P.mode == kModeRuns ? tab : cur, bytes, g->device));
+        }
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
             VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, timed ? &timings : nullptr));

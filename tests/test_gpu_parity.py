@@ -471,3 +471,19 @@ def test_table_levels_rejects_bad_value(vga):
     with vga.vga_graph_load(off, b) as g:
         with pytest.raises(vga.VgaError):
             vga.hyperball_run_trace(g, 8, 1, max_trace=1, union_mode=2, table_levels=4)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_l2_window_same_result(vga, mode):
+    torch = pytest.importorskip("torch")
+    _, off, b, _ = tiny_graph(2)
+    ref = oracle.hyperball(off, b, 10, 3, seed=4)
+    with vga.vga_graph_load(off, b) as g:
+        md = torch.empty(g.n_nodes, dtype=torch.float64, device="cuda")
+        ball = torch.empty_like(md)
+        s = torch.cuda.Stream()
+        it = vga.hyperball_run_dev(g, 10, 3, 4, md, ball, stream=s, union_mode=mode, l2_window=1)
+        torch.cuda.synchronize()
+    assert it == ref["iterations"]
+    assert np.array_equal(md.cpu().numpy(), ref["mean_depth"], equal_nan=True)
+    assert np.array_equal(ball.cpu().numpy(), ref["ball"])
