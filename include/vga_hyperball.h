@@ -532,7 +532,7 @@ typedef struct vga_tune_entry {
     int degree_log2;     /* bucket: graphs whose average degree E/N has floor(log2) = this  */
     int union_mode;      /* 1 per neighbour, 2 per run                                       */
     int slice_bytes;     /* slice width; applied as an upper bound, lowered when the slice
-                            (and in mode 2 its four sparse-table levels) would not fit the
+                            (and in mode 2 its table of range maxima) would not fit the
                             whole L2 for a larger graph of the bucket                        */
     int warps_per_cta;   /* union CTA size in warps                                          */
     int hub_lookups;     /* mode 2 hub threshold (0 = automatic)                             */

@@ -5,17 +5,17 @@
 // sequence of runs of consecutive ids: a visible stretch of a grid row is a
 // block of consecutive node ids (the paper's one-byte deltas of 1).  On the
 // 236k-cell city graph a list of ~20k neighbours has ~1.8k runs.  The max over
-// a run [a, a+L) equals the max of two overlapping power-of-two windows of a
-// sparse table T_k[i] = max(cur[i .. i + 2^k)), so each run costs one or two
-// gathers instead of L; runs of 32 or more are covered by ceil(L/16) windows of
-// 16.  Max is associative, commutative and idempotent, so the result is the
-// same register array, bit for bit.
+// a run [a, a+L) equals the max of a few overlapping windows of a table of
+// range maxima T_k[i] = max(cur[i .. i + 2^k)) (runs.cuh: the widest kept
+// width w <= L, ceil(L / w) windows), so each run costs one or a few gathers
+// instead of L.  Max is associative, commutative and idempotent, so the
+// result is the same register array, bit for bit.
 //
 // This file turns the LEB128 CSR into the list of lookups of every node, once
-// per graph: one warp per node decodes its list with the warp window decoder,
-// finds run boundaries across windows, and emits each completed run's lookups
-// as row indices k * N + i of a slice's table region (T_0 = the slice, then
-// T_1..T_4), so that the union addresses a row with one multiply-add.
+// per graph and table scheme: one warp per node decodes its list with the wide
+// window decoder, finds run boundaries across windows, and emits each
+// completed run's lookups as row indices slot * N + i of a slice's table
+// region, so that the union addresses a row with one multiply-add.
 #include <algorithm>
 #include <vector>
 
