@@ -230,7 +230,9 @@ class OracleSample:
         self.n = len(cells)
         rng = np.random.default_rng(rng_seed)
         self.sample = np.sort(rng.choice(self.n, min(n_sample, self.n), replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
         row_ptr_s, col = oracle.visibility_csr(obst, cells, nodes=self.sample, nthreads=self.cores)
+        self.build_seconds = time.perf_counter() - t0  # the oracle's builder on the sampled sources
         counts = np.zeros(self.n, np.int64)
         counts[self.sample] = np.diff(row_ptr_s.astype(np.int64))
         row_ptr = np.zeros(self.n + 1, np.uint64)
@@ -261,7 +263,10 @@ def cpu_baseline(obst, args) -> dict:
         total_e += e
         reps += 1
     return {"value": total_e / total_t / 1e9, "unit": UNIT, "cores": s.cores, "kind": "oracle",
-            "sample": s.describe(reps), "seconds": total_t}
+            "sample": s.describe(reps), "seconds": total_t,
+            "builder": {"sources": len(s.sample), "seconds": s.build_seconds,
+                        "pair_tests_per_s": len(s.sample) * (s.n - 1) / s.build_seconds,
+                        "what": "the oracle's visibility builder (supercover DDA per pair) for the sampled sources"}}
 
 
 def run_reference(args, dist: Dist):
@@ -517,6 +522,15 @@ def run_ours(args, dist: Dist):
         extras["sweep"] = sweep
         if dist.rank == 0 and dist.world == 1:
             extras["cpu_baseline"] = cpu_baseline(obst, args)
+        # the GPU visibility builder (run once before the timed region) beside the oracle's
+        extras["builder"] = {"gpu_seconds": build_s, "pair_tests": N * (N - 1) // 2,
+                             "pair_tests_per_s": N * (N - 1) / 2 / build_s,
+                             "what": "vga_visibility_build: main component on the host, then every pair of the "
+                                     "upper triangle walked by supercover DDA on the device, mirrored, encoded"}
+        if "cpu_baseline" in extras:
+            cb = extras["cpu_baseline"]["builder"]
+            extras["builder"]["cpu_oracle_pair_tests_per_s"] = cb["pair_tests_per_s"]
+            extras["builder"]["cpu_oracle_cores"] = extras["cpu_baseline"]["cores"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps, "higher_is_better": True,

@@ -199,6 +199,16 @@ typedef struct vga_tuning {
 } vga_tuning;
 
 /*
+ * vga_set_table_scheme_nodes -- graphs loaded from now on with at least this
+ * many nodes get the 3-row table of range maxima (windows of 1, 4 and 16 rows),
+ * smaller ones the 5-row table (windows 1..16); 0 restores the automatic
+ * choice (3 rows when five rows of 128-byte slices would exceed 3/4 of the L2).
+ * Process-wide; the choice fixes which lookups a graph counts at load, and
+ * vga_tuning.table_levels can still ask for the other table per run.
+ */
+int vga_set_table_scheme_nodes(uint32_t nodes);
+
+/*
  * hyperball_run -- Algorithm 1 end to end, host outputs.
  *   g           loaded graph.
  *   p           HLL precision, 4 <= p <= 16; m = 2^p uint8 registers per node.

@@ -107,6 +107,7 @@ SIGNATURES = {
     "vga_shard_estimate": ([vp, vp, C.POINTER(u32), vp], i32),
     "vga_shard_finalize": ([vp, vp, vp, vp], i32),
     "vga_shard_free": ([vp], None),
+    "vga_set_table_scheme_nodes": ([u32], i32),
     "vga_autotune": ([C.POINTER(vp), i32, i32, vp, C.POINTER(VgaTuneEntry), i32, C.POINTER(i32), i32], i32),
     "vga_tune_table_set": ([C.POINTER(VgaTuneEntry), i32], i32),
     "vga_tune_table_get": ([C.POINTER(VgaTuneEntry), i32, C.POINTER(i32)], i32),
@@ -573,3 +574,9 @@ def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, sli
                                           table_levels),
                                   C.byref(h)))
     return Shard(h)
+
+
+def vga_set_table_scheme_nodes(nodes: int = 0):
+    """Graphs loaded from now on with at least `nodes` nodes get 3-row tables of
+    range maxima (0: automatic, from the L2 size)."""
+    _check(lib().vga_set_table_scheme_nodes(nodes))

@@ -17,6 +17,7 @@
 // completed run's lookups as row indices slot * N + i of a slice's table
 // region, so that the union addresses a row with one multiply-add.
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "runs.cuh"
@@ -69,9 +70,23 @@ uint64_t union_l2_budget(int device) {
     return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 3 / 4;
 }
 
+static std::atomic<uint32_t> g_scheme_nodes{0};  // vga_set_table_scheme_nodes (0 = from the L2 size)
+
 int table_scheme_auto(uint32_t n, int device) {
+    const uint32_t above = g_scheme_nodes.load();
+    if (above) return n > above - 1u ? 1 : 0;
     return (uint64_t)table_rows(0) * n * 128u > union_l2_budget(device) ? 1 : 0;
 }
+
+}  // namespace vga
+
+extern "C" int vga_set_table_scheme_nodes(uint32_t nodes) {
+    vga::clear_error();
+    vga::g_scheme_nodes.store(nodes);
+    return VGA_OK;
+}
+
+namespace vga {
 
 int ensure_run_lookups(const vga_graph *g, int scheme, cudaStream_t stream) {
     std::lock_guard<std::mutex> lock(g->lk_mu);
