@@ -519,6 +519,33 @@ def run_ours(args, dist: Dist):
             sec_s = f0.elapsed_time(f1) / 1e3
             sweep.append({"p": sp, "d": sd, "register_bits": sb, "seconds": sec_s, "passes": s_passes,
                           "geu_per_s": s_passes * E / sec_s / 1e9})
+        # register shards (the multi-GPU split) run in lockstep on this one GPU: the same
+        # union work as one run plus the per-pass partial sums and their estimate, so the
+        # time over the unsharded run is the split's compute overhead (no interconnect)
+        if not sharded:
+            from paper_2604_08374_gb300.sharded import hyperball_run_sharded_local
+            hyperball_run_sharded_local(g, args.p, args.d, args.seed, 2, md, ball, stream=stream)
+            f0.record(stream)
+            sh_passes = hyperball_run_sharded_local(g, args.p, args.d, args.seed, 2, md, ball, stream=stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            sec_sh = f0.elapsed_time(f1) / 1e3
+            extras["shards_local"] = {"n_shards": 2, "seconds": sec_sh, "passes": sh_passes,
+                                      "unsharded_seconds": sec_max / args.steps,
+                                      "overhead": sec_sh / (sec_max / args.steps) - 1.0}
+        # the paper's optional Hilbert numbering (Sec. 3.2): the same grid, its own graph
+        if args.order == "raster":
+            gh = vga.vga_visibility_build(obst, order="hilbert")
+            mdh = torch.empty(max(gh.n_nodes, 1), dtype=torch.float64, device=dev)
+            vga.hyperball_run_dev(gh, args.p, args.d, args.seed, mdh, None, stream=stream)
+            f0.record(stream)
+            h_passes = vga.hyperball_run_dev(gh, args.p, args.d, args.seed, mdh, None, stream=stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            sec_h = f0.elapsed_time(f1) / 1e3
+            sweep.append({"order": "hilbert", "p": args.p, "d": args.d, "csr_bytes": gh.n_bytes, "seconds": sec_h,
+                          "passes": h_passes, "geu_per_s": h_passes * gh.n_edges / sec_h / 1e9})
+            gh.free()
         extras["sweep"] = sweep
         if dist.rank == 0 and dist.world == 1:
             extras["cpu_baseline"] = cpu_baseline(obst, args)
