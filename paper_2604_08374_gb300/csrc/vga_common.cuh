@@ -290,12 +290,13 @@ __device__ __forceinline__ int decode_window4(const uint8_t *__restrict__ bytes,
     if (lane == 31) wn = __ldg(aw + 32);
     const uint32_t word = __funnelshift_r(w, wn, (uint32_t)(pos & 3ull) * 8u);
     const uint32_t prev_word = __shfl_up_sync(0xffffffffu, word, 1);
-    const uint64_t dw = ((uint64_t)word << 32) | (lane ? prev_word : 0u);  // window bytes 4L-4 .. 4L+3
-    const uint64_t p0 = pos + 4u * (uint32_t)lane;
-    uint32_t tm = 0;  // terminator bits of this lane's bytes
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-        if (p0 + (uint64_t)k < end && !((word >> (8 * k)) & 0x80u)) tm |= 1u << k;
+    const uint32_t pw = lane ? prev_word : 0u;  // window bytes 4L-4 .. 4L-1 (none before the window)
+    // terminator bits of this lane's bytes inside [pos, end): bit 7 clear
+    const uint64_t rem64 = end - pos;
+    const int rem = rem64 < 128u ? (int)rem64 : 128;
+    const int mine = min(max(rem - 4 * lane, 0), 4);
+    const uint32_t hb = ~word & 0x80808080u;
+    uint32_t tm = ((hb >> 7) | (hb >> 14) | (hb >> 21) | (hb >> 28)) & ((1u << mine) - 1u);
     // last terminator before this lane's bytes (window position), -1 if none
     int pt = tm ? 4 * lane + (31 - __clz(tm)) : -1;
 #pragma unroll
@@ -317,10 +318,15 @@ __device__ __forceinline__ int decode_window4(const uint8_t *__restrict__ bytes,
             const int q = 4 * lane + k;  // terminator position
             const int len = q - prev;    // bytes prev+1 .. q
             uint64_t v = 0;
-            if (len <= 5) {
-                // the varint's bytes, first (least significant group) lowest, then
-                // the 7-bit groups packed together
-                const uint64_t x = (dw >> (8 * (prev + 1 - 4 * lane + 4))) & ((1ull << (8 * len)) - 1ull);
+            // the varint's bytes, first (least significant group) lowest, taken from
+            // the previous lane's word and this one; then its 7-bit groups packed
+            const int sb = prev + 1 - 4 * lane + 4;  // first byte within (pw, word): 0 .. 7
+            if (len <= 4) {
+                const uint32_t x = (sb < 4 ? __funnelshift_r(pw, word, 8u * (uint32_t)sb) : word >> (8 * (sb - 4))) &
+                                   (0xFFFFFFFFu >> (32 - 8 * len));
+                v = (x & 0x7Fu) | ((x >> 1) & 0x3F80u) | ((x >> 2) & 0x1FC000u) | ((x >> 3) & 0xFE00000u);
+            } else if (len == 5) {
+                const uint64_t x = ((((uint64_t)word << 32) | pw) >> (8 * sb)) & 0xFFFFFFFFFFull;
                 v = (x & 0x7Full) | ((x >> 1) & (0x7Full << 7)) | ((x >> 2) & (0x7Full << 14)) |
                     ((x >> 3) & (0x7Full << 21)) | ((x >> 4) & (0x7Full << 28));
             } else {
