@@ -266,109 +266,6 @@ __device__ __forceinline__ WindowDecode<Id> decode_window(const uint8_t *__restr
     return r;
 }
 
-// Wide variant of decode_window for the passes that only need the ids (graph
-// validation, lookup building): each lane takes 4 bytes, so a warp decodes
-// 128 bytes per step.  The window starts at a varint boundary `pos`; lane L
-// holds window bytes 4L .. 4L+3 (two aligned 32-bit loads per lane shared
-// through a shuffle, then a funnel shift; the byte buffer carries 256 bytes
-// of padding).  Every varint that ends in the window is assembled from at
-// most 5 bytes (its own lane and the one before), the deltas are prefix-
-// summed across the warp, and the ids are written in order to ids[0 ..
-// count).  Returns count; advance = bytes consumed up to the window's last
-// complete varint (0 if none); next_base = its id.  CHECK also tests every
-// rule of the format (varint of at most 5 bytes and 32 bits, no zero delta
-// after a list's first entry, id < n, id != self) and sets fail on any
-// break; list_start says the window begins the node's list.
-template <class Id, bool CHECK>
-__device__ __forceinline__ int decode_window4(const uint8_t *__restrict__ bytes, uint64_t pos, uint64_t end,
-                                              Id base, int lane, uint32_t *ids, int &advance, Id &next_base,
-                                              bool list_start, uint64_t n, uint64_t self, bool &fail) {
-    const uint64_t a0 = pos & ~3ull;
-    const uint32_t *aw = reinterpret_cast<const uint32_t *>(bytes + a0);
-    const uint32_t w = __ldg(aw + lane);
-    uint32_t wn = __shfl_down_sync(0xffffffffu, w, 1);
-    if (lane == 31) wn = __ldg(aw + 32);
-    const uint32_t word = __funnelshift_r(w, wn, (uint32_t)(pos & 3ull) * 8u);
-    const uint32_t prev_word = __shfl_up_sync(0xffffffffu, word, 1);
-    const uint32_t pw = lane ? prev_word : 0u;  // window bytes 4L-4 .. 4L-1 (none before the window)
-    // terminator bits of this lane's bytes inside [pos, end): bit 7 clear
-    const uint64_t rem64 = end - pos;
-    const int rem = rem64 < 128u ? (int)rem64 : 128;
-    const int mine = min(max(rem - 4 * lane, 0), 4);
-    const uint32_t hb = ~word & 0x80808080u;
-    uint32_t tm = ((hb >> 7) | (hb >> 14) | (hb >> 21) | (hb >> 28)) & ((1u << mine) - 1u);
-    // last terminator before this lane's bytes (window position), -1 if none
-    int pt = tm ? 4 * lane + (31 - __clz(tm)) : -1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pt, o);
-        if (lane >= o) pt = max(pt, t);
-    }
-    const int last_all = __shfl_sync(0xffffffffu, pt, 31);
-    int prev = __shfl_up_sync(0xffffffffu, pt, 1);
-    if (lane == 0) prev = -1;
-    // assemble this lane's varints
-    uint32_t val[4];
-    Id lane_sum = 0;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        val[k] = 0;
-        if ((tm >> k) & 1u) {
-            const int q = 4 * lane + k;  // terminator position
-            const int len = q - prev;    // bytes prev+1 .. q
-            uint64_t v = 0;
-            // the varint's bytes, first (least significant group) lowest, taken from
-            // the previous lane's word and this one; then its 7-bit groups packed
-            const int sb = prev + 1 - 4 * lane + 4;  // first byte within (pw, word): 0 .. 7
-            if (len <= 4) {
-                const uint32_t x = (sb < 4 ? __funnelshift_r(pw, word, 8u * (uint32_t)sb) : word >> (8 * (sb - 4))) &
-                                   (0xFFFFFFFFu >> (32 - 8 * len));
-                v = (x & 0x7Fu) | ((x >> 1) & 0x3F80u) | ((x >> 2) & 0x1FC000u) | ((x >> 3) & 0xFE00000u);
-            } else if (len == 5) {
-                const uint64_t x = ((((uint64_t)word << 32) | pw) >> (8 * sb)) & 0xFFFFFFFFFFull;
-                v = (x & 0x7Full) | ((x >> 1) & (0x7Full << 7)) | ((x >> 2) & (0x7Full << 14)) |
-                    ((x >> 3) & (0x7Full << 21)) | ((x >> 4) & (0x7Full << 28));
-            } else {
-                bad = true;
-            }
-            if (v > 0xFFFFFFFFull) bad = true;
-            val[k] = (uint32_t)v;
-            lane_sum += (Id)(uint32_t)v;
-            prev = q;
-        }
-    }
-    // prefix sums of the deltas and of the varint counts across lanes
-    Id incl = lane_sum;
-    int cnt_incl = __popc(tm);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Id t = __shfl_up_sync(0xffffffffu, incl, o);
-        const int c = __shfl_up_sync(0xffffffffu, cnt_incl, o);
-        if (lane >= o) {
-            incl += t;
-            cnt_incl += c;
-        }
-    }
-    Id id = base + incl - lane_sum;
-    int idx = cnt_incl - __popc(tm);
-    bool f = bad;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if ((tm >> k) & 1u) {
-            id += (Id)val[k];
-            if (CHECK) {
-                if (val[k] == 0u && !(list_start && idx == 0)) f = true;  // duplicate neighbour
-                if ((uint64_t)id >= n || (uint64_t)id == self) f = true;
-            }
-            ids[idx++] = (uint32_t)id;
-        }
-    }
-    if (CHECK) fail = __any_sync(0xffffffffu, f);
-    advance = last_all + 1;
-    next_base = base + __shfl_sync(0xffffffffu, incl, 31);
-    return __shfl_sync(0xffffffffu, cnt_incl, 31);
-}
 
 __device__ __forceinline__ uint4 vmax4(uint4 a, uint4 b) {
     return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z), __vmaxu4(a.w, b.w));

@@ -21,19 +21,16 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
-// One warp per node v0 .. v1-1: decode its byte range with the wide window
-// decoder and check every rule of the format.  Writes the degree and the number of range
+// One warp per node v0 .. v1-1: decode its byte range 512 bytes at a time
+// (scan_window16) and check every rule of the format.  Writes the degree and the number of range
 // lookups the run-aware union will need (runs.cuh), and folds E, the maximum
 // degree and the lowest bad node id into global counters.
 __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes, uint32_t n,
                                 uint32_t v0, uint32_t v1, int scheme, uint32_t *__restrict__ degree,
                                 uint32_t *__restrict__ lk_count, unsigned long long *__restrict__ edge_total,
                                 uint32_t *__restrict__ max_degree, uint32_t *__restrict__ bad_node) {
-    __shared__ uint32_t s_ids[8][128];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    uint32_t *ids = s_ids[wib];
-    const uint64_t warp = (uint64_t)v0 + (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const uint64_t warp = (uint64_t)v0 + (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= v1) return;
     const uint32_t v = (uint32_t)warp;
     uint64_t pos = off[v];
@@ -41,29 +38,20 @@ __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t 
     uint64_t base = 0;
     uint32_t cnt = 0;
     bool ok = true;
-    RunTracker rt;
-    rt.scheme = scheme;
+    RunCarry rc;
     while (pos < end) {
-        int advance = 0;
-        uint64_t next = 0;
-        bool fail = false;
-        const int c = decode_window4<uint64_t, true>(bytes, pos, end, base, lane, ids, advance, next, cnt == 0,
-                                                     (uint64_t)n, (uint64_t)v, fail);
-        if (c == 0 || fail) {  // a varint runs past the node's range, or a rule is broken
+        const Window16 W = scan_window16<true, false>(bytes, pos, end, base, cnt == 0, n, v, scheme, nullptr, rc, lane);
+        if (W.count == 0 || W.fail) {  // a varint runs past the node's range, or a rule is broken
             ok = false;
             break;
         }
-        __syncwarp();
-        rt.window<false>(ids, c, lane, n, nullptr);
-        __syncwarp();
-        cnt += (uint32_t)c;
-        base = next;
-        pos += (uint64_t)advance;
+        cnt += (uint32_t)W.count;
+        pos += W.advance;
     }
-    rt.finish<false>(lane, n, nullptr);
+    finish_runs<false>(rc, lane, n, scheme, nullptr);
     if (lane == 0) {
         degree[v] = ok ? cnt : 0;
-        lk_count[v] = ok ? (uint32_t)rt.out : 0u;
+        lk_count[v] = ok ? (uint32_t)rc.out : 0u;
         if (!ok) atomicMin(bad_node, v);
         atomicAdd(edge_total, (unsigned long long)cnt);
         atomicMax(max_degree, cnt);
