@@ -1,12 +1,14 @@
 // hyperball.cu -- HyperBall (Algorithm 1, Sec. 3.3) on the device-resident
 // compressed CSR: counter initialisation, the register-wise union of
-// Eq. hll-union with on-the-fly LEB128 decoding, the HLL estimator, the
-// distance accumulation of Eq. sumD and Visual Mean Depth.
+// Eq. hll-union (per run of consecutive neighbour ids through a per-slice
+// table of range maxima, or per neighbour with on-the-fly LEB128 decoding),
+// the HLL estimator, the distance accumulation of Eq. sumD and Visual Mean
+// Depth; plus the register-range shards of one analysis.
 //
 // Register layout: the N x m uint8 registers are stored slice-major,
 // [m/S][N][S] for a slice width of S bytes, so that one union launch touches
-// only N*S bytes of counters (sized to stay resident in L2) and every
-// neighbour gather is S contiguous, 16-byte aligned bytes.
+// only N*S bytes of counters (the slice and its table sized to stay resident
+// in L2) and every gather is S contiguous, 16-byte aligned bytes.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -487,3 +487,25 @@ def test_l2_window_same_result(vga, mode):
     assert it == ref["iterations"]
     assert np.array_equal(md.cpu().numpy(), ref["mean_depth"], equal_nan=True)
     assert np.array_equal(ball.cpu().numpy(), ref["ball"])
+
+
+def test_load_from_device_buffers(vga):
+    torch = pytest.importorskip("torch")
+    _, off, b, cells = tiny_graph(3)
+    off_d = torch.from_numpy(off.view(np.int64).copy()).cuda()
+    b_d = torch.from_numpy(b.copy()).cuda()
+    with vga.vga_graph_load_device(off_d, b_d, len(b)) as g:
+        o2, b2, _ = g.copy_csr()
+        assert np.array_equal(o2, off) and np.array_equal(b2, b)
+        got = vga.hyperball_run_trace(g, 8, 3, seed=6, max_trace=3)
+    ref = oracle.hyperball(off, b, 8, 3, seed=6, trace=3)
+    assert_same_run(got, ref)
+
+
+@pytest.mark.parametrize("S", [16, 64, 128, 1024])
+def test_gather_microbenchmark(vga, S):
+    for consumer in (0, 1):
+        gbs = vga.vga_bench_gather(64 << 20, S, 1 << 22, consumer=consumer)
+        assert 100.0 < gbs < 1e6
+    with pytest.raises(vga.VgaError):
+        vga.vga_bench_gather(64 << 20, 48, 1 << 20)
