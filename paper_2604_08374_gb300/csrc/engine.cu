@@ -211,11 +211,7 @@ uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 
 
-uint64_t l2_budget_bytes(int dev) {
-    int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 6 / 10;
-}
+uint64_t l2_budget_bytes(int dev) { return union_l2_budget(dev); }  // 3/4 of the L2, as for single runs
 
 JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode, int scheme) {
     JobLayout L;
