@@ -455,6 +455,19 @@ def run_ours(args, dist: Dist):
     }
     if traffic_note:
         roofline["traffic_note"] = traffic_note
+    # The bound of the per-neighbour method (one gather of every neighbour's
+    # registers per edge, E x m bytes a pass, at the measured gather rate; the
+    # CSR and register arrays at HBM peak): the run-aware union beats it by
+    # gathering a table row per run instead.
+    m_bytes = (1 << args.p) // (2 if args.register_bits == 4 else 1)
+    t_l2 = E * m_bytes / (l2_peak * 1e9) if l2_peak else None
+    t_hbm = (B + 8 * (N + 1) + 2 * N * m_bytes) / (hbm_peak * 1e9) if hbm_peak else None
+    if t_l2 and t_hbm:
+        per_nb = E / max(t_l2, t_hbm) / 1e9
+        roofline["per_neighbour_roofline"] = {
+            "geu_per_s": per_nb, "value_over_it": value / per_nb,
+            "definition": "E / max((CSR + 8(N+1) + 2 N m) / hbm_gbs, E m / measured gather peak): the ceiling "
+                          "of a union that gathers every neighbour's registers"}
     union_share = prof["union_ms"] / (sec * 1e3) if sec > 0 else None
 
     extras = {}
