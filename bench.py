@@ -92,6 +92,8 @@ def parse_args():
     ap.add_argument("--hub-lookups", type=int, default=0, help="force the run-aware hub threshold (0 = automatic)")
     ap.add_argument("--l2-window", type=int, default=0, choices=[0, 1],
                     help="1: mark the union's table region persisting in L2 (access-policy window)")
+    ap.add_argument("--first-pass", type=int, default=0, choices=[0, 1, 2],
+                    help="pass 1: 0 automatic (scatter), 1 the union's gather, 2 the scatter")
     ap.add_argument("--table-levels", type=int, default=0, choices=[0, 3, 5],
                     help="run-aware table rows per node: 5 (windows 1..16), 3 (1, 4, 16), 0 = automatic")
     ap.add_argument("--sharded", action="store_true",
@@ -376,7 +378,8 @@ def run_ours(args, dist: Dist):
                 return hyperball_run_sharded(g, args.p, d, args.seed, md, ball, slice_bytes=args.slice_bytes,
                                              warps_per_cta=args.warps, union_mode=args.union_mode,
                                              register_bits=0 if args.register_bits == 8 else args.register_bits,
-                                             hub_lookups=args.hub_lookups, table_levels=args.table_levels)
+                                             hub_lookups=args.hub_lookups, table_levels=args.table_levels,
+                                             first_pass=args.first_pass)
         # a forced slice width or table scheme sizes its own workspace
         forced = args.slice_bytes or args.table_levels
         return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=None if forced else ws,
@@ -385,7 +388,7 @@ def run_ours(args, dist: Dist):
                                      union_mode=args.union_mode if union_mode is None else union_mode,
                                      register_bits=0 if args.register_bits == 8 else args.register_bits,
                                      hub_lookups=args.hub_lookups, table_levels=args.table_levels,
-                                     l2_window=args.l2_window)
+                                     l2_window=args.l2_window, first_pass=args.first_pass)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -468,7 +471,16 @@ def run_ours(args, dist: Dist):
             "geu_per_s": per_nb, "value_over_it": value / per_nb,
             "definition": "E / max((CSR + 8(N+1) + 2 N m) / hbm_gbs, E m / measured gather peak): the ceiling "
                           "of a union that gathers every neighbour's registers"}
-    union_share = prof["union_ms"] / (sec * 1e3) if sec > 0 else None
+    if prof["first_pass_launches"]:
+        # pass 1 by the scatter of the nodes' hashes (one launch for all slices)
+        fp_ms = prof["first_pass_ms"] / prof["first_pass_launches"]
+        roofline["first_pass"] = {
+            "kernel": "hb_first_pass_kernel", "launches_timed": prof["first_pass_launches"], "avg_launch_ms": fp_ms,
+            "share_of_step": prof["first_pass_ms"] / (sec * 1e3) if sec > 0 else None,
+            "edge_unions_per_s": E / (fp_ms / 1e3) / 1e9, "unit": "GEdge-unions/s",
+            "what": "pass 1 of Eq. hll-union as a scatter: every counter holds only its own node, so each "
+                    "neighbour's (register index, rho) is max-folded into shared-memory cells; no rows gathered"}
+    union_share = (prof["union_ms"] + prof["first_pass_ms"]) / (sec * 1e3) if sec > 0 else None
 
     extras = {}
     if not args.no_extras:
@@ -579,6 +591,7 @@ def run_ours(args, dist: Dist):
                        "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode, "order": args.order,
                        "register_bits": args.register_bits, "table_levels": args.table_levels or "auto",
                        "l2_window": args.l2_window,
+                       "first_pass": {0: "auto", 1: "gather", 2: "scatter"}[args.first_pass],
                        "autotune": tuned,
                        "parallelism": f"register shards x{dist.world}" if sharded else f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",

@@ -196,6 +196,14 @@ typedef struct vga_tuning {
                             policy window on the stream, with the process's persisting L2
                             set-aside raised to cover it; both are put back afterwards.
                             0: off (default; the lookup stream is evict-first anyway)      */
+    int first_pass;      /* mode 2: how pass 1 of Eq. hll-union is computed.  Every counter
+                            then holds only its own node, so register j of the result is
+                            the largest rho among the node's and its neighbours' hashes with
+                            index j.  2: that scatter, one launch for all slices (each warp
+                            folds the hashes of its node's neighbour runs into m cells of
+                            shared memory; p <= 13); 1: the union kernel, like every later
+                            pass; 0: automatic (2 wherever allowed).  Same registers bit
+                            for bit.                                                       */
 } vga_tuning;
 
 /*
@@ -447,6 +455,10 @@ typedef struct vga_profile {
     int slice_bytes;              /* slice width of the last timed launch                 */
     int union_mode;               /* union variant of the last timed launch (1 or 2)      */
     int reserved[2];
+    uint64_t first_pass_launches; /* first passes computed by the scatter (vga_tuning.
+                                     first_pass), timed apart from the union slices       */
+    double first_pass_ms;         /* their summed device time                             */
+    uint64_t first_pass_edges;    /* neighbour unions they performed (E per launch)       */
 } vga_profile;
 
 /* Enable (1) or disable (0) event timing of union launches. */

@@ -32,7 +32,7 @@ vp, i32, u32, u64, i64, f64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_i
 class VgaTuning(C.Structure):
     _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
                 ("union_mode", C.c_int), ("register_bits", C.c_int), ("hub_lookups", C.c_int),
-                ("table_levels", C.c_int), ("l2_window", C.c_int)]
+                ("table_levels", C.c_int), ("l2_window", C.c_int), ("first_pass", C.c_int)]
 
 
 class VgaJob(C.Structure):
@@ -55,7 +55,9 @@ class VgaServerStats(C.Structure):
 class VgaProfile(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("union_launches", C.c_uint64), ("union_ms", C.c_double),
                 ("union_edges", C.c_uint64), ("union_gather_bytes", C.c_uint64), ("union_hbm_bytes", C.c_uint64),
-                ("slice_bytes", C.c_int), ("union_mode", C.c_int), ("reserved", C.c_int * 2)]
+                ("slice_bytes", C.c_int), ("union_mode", C.c_int), ("reserved", C.c_int * 2),
+                ("first_pass_launches", C.c_uint64), ("first_pass_ms", C.c_double),
+                ("first_pass_edges", C.c_uint64)]
 
 
 class VgaTuneEntry(C.Structure):
@@ -161,14 +163,14 @@ def _ptr(a) -> int | None:
 
 
 def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0, register_bits=0, hub_lookups=0,
-            table_levels=0, l2_window=0):
+            table_levels=0, l2_window=0, first_pass=0):
     if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode or register_bits or hub_lookups
-            or table_levels or l2_window):
+            or table_levels or l2_window or first_pass):
         return None
     t = VgaTuning()
     t.slice_bytes, t.warps_per_cta, t.l2_budget_mb, t.union_mode = slice_bytes, warps_per_cta, l2_budget_mb, union_mode
     t.register_bits, t.hub_lookups, t.table_levels = register_bits, hub_lookups, table_levels
-    t.l2_window = l2_window
+    t.l2_window, t.first_pass = l2_window, first_pass
     return C.pointer(t)
 
 
@@ -322,14 +324,15 @@ def hyperball_workspace_bytes(g: Graph, p: int) -> int:
 def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_size_dev, conv_mode: int = 0,
                       workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
                       l2_budget_mb: int = 0, union_mode: int = 0, register_bits: int = 0,
-                      hub_lookups: int = 0, table_levels: int = 0, l2_window: int = 0) -> int:
+                      hub_lookups: int = 0, table_levels: int = 0, l2_window: int = 0,
+                      first_pass: int = 0) -> int:
     """Algorithm 1 into device tensors (float64, N each); returns passes run."""
     it = C.c_int()
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
                                    _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode, register_bits,
-                                           hub_lookups, table_levels, l2_window)))
+                                           hub_lookups, table_levels, l2_window, first_pass)))
     return it.value
 
 
@@ -346,7 +349,7 @@ def hyperball_run_noalloc(g: Graph, p: int, d: int, seed: int, mean_depth_dev, b
 
 def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0, max_trace: int = 8,
                         slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
-                        hub_lookups: int = 0, table_levels: int = 0):
+                        hub_lookups: int = 0, table_levels: int = 0, first_pass: int = 0):
     """Run with per-pass register and estimate dumps (bit-exact checks).
 
     Returns dict(mean_depth, ball, iterations, regs[(max_trace+1), N, m], c[(max_trace+1), N])."""
@@ -360,7 +363,7 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
                                      _ptr(regs), _ptr(cc), max_trace,
                                      _tuning(slice_bytes, warps_per_cta, union_mode=union_mode,
                                              register_bits=register_bits, hub_lookups=hub_lookups,
-                                             table_levels=table_levels)))
+                                             table_levels=table_levels, first_pass=first_pass)))
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}
@@ -567,11 +570,11 @@ class Shard:
 
 def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, slice_bytes: int = 0,
                      warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
-                     hub_lookups: int = 0, table_levels: int = 0) -> Shard:
+                     hub_lookups: int = 0, table_levels: int = 0, first_pass: int = 0) -> Shard:
     h = C.c_void_p()
     _check(lib().vga_shard_create(g.handle, p, seed, shard, n_shards,
                                   _tuning(slice_bytes, warps_per_cta, 0, union_mode, register_bits, hub_lookups,
-                                          table_levels),
+                                          table_levels, first_pass=first_pass),
                                   C.byref(h)))
     return Shard(h)
 

@@ -164,25 +164,29 @@ __device__ __forceinline__ void finish_groups(const typename RegFmt<NIB>::Acc (&
         }
 }
 
-// Alg. 1 initialisation of node v: its counter gets rho in register j, where j
-// is the top p bits of the hash and rho the position of the first set bit of
-// the remaining 64-p bits (65-p if none).  The registers were zeroed before.
-// With 4-bit registers (nib) rho is clamped to 15 and register j is nibble
-// j % 2 of byte j / 2 (the low nibble first).  A shard stores only slices
-// [s0, s1), its slice s0 first.
-__device__ __forceinline__ void init_node(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed,
-                                          uint32_t v, bool nib = false, uint32_t s0 = 0u,
-                                          uint32_t s1 = 0xffffffffu) {
+// Alg. 1 initialisation of node v, as a key j << 8 | rho: its counter gets rho
+// in register j, where j is the top p bits of the hash and rho the position of
+// the first set bit of the remaining 64-p bits (65-p if none).  With 4-bit
+// registers (nib) rho is clamped to 15.
+__device__ __forceinline__ uint32_t node_key(uint32_t v, int p, uint64_t seed, bool nib) {
     const uint64_t h = splitmix64((uint64_t)v ^ seed);
     const uint32_t j = (uint32_t)(h >> (64 - p));
     const uint64_t w = h << p;
     uint32_t rho = w ? (uint32_t)__clzll((long long)w) + 1u : (uint32_t)(65 - p);
-    uint32_t byte = j, val = rho;
-    if (nib) {
-        rho = rho < 15u ? rho : 15u;
-        byte = j >> 1;
-        val = rho << (4u * (j & 1u));
-    }
+    if (nib && rho > 15u) rho = 15u;
+    return j << 8 | rho;
+}
+
+// Store node v's initial counter into registers that were zeroed before.  With
+// 4-bit registers register j is nibble j % 2 of byte j / 2 (the low nibble
+// first).  A shard stores only slices [s0, s1), its slice s0 first.
+__device__ __forceinline__ void init_node(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed,
+                                          uint32_t v, bool nib = false, uint32_t s0 = 0u,
+                                          uint32_t s1 = 0xffffffffu) {
+    const uint32_t key = node_key(v, p, seed, nib);
+    const uint32_t j = key >> 8, rho = key & 0xffu;
+    const uint32_t byte = nib ? j >> 1 : j;
+    const uint32_t val = nib ? rho << (4u * (j & 1u)) : rho;
     const uint32_t s = byte / (uint32_t)S, o = byte % (uint32_t)S;
     if (s < s0 || s >= s1) return;  // a register-range shard holds slices [s0, s1) only
     regs[((uint64_t)(s - s0) * n + v) * (uint64_t)S + o] = (uint8_t)val;
@@ -403,6 +407,100 @@ __device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc 
             atomic_max_word<NIB>(dst + 4 * q + 3, res.w, err);
             changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
         }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) {
+        if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
+    }
+}
+
+// First pass of Eq. hll-union (t = 1) as a scatter.  After the initialisation
+// (Alg. 1) every counter holds one register, the node's key (node_key), so
+// register j of next[v] is the largest rho among the keys of v and its
+// neighbours whose register index is j: no register row needs to be gathered.
+// A warp walks its work item's range lookups; a lookup r = slot * n + i of
+// window width w (runs.cuh: the windows of a run stay inside it) covers the
+// neighbour ids i .. i + w - 1.  The lookups of one width are compacted
+// through `stage` (32 words), so that 32 / w of them share a round of the
+// warp with consecutive lanes on consecutive ids; their keys are read from
+// `keys` and folded into the warp's m shared-memory cells (one u32 per
+// register) by atomicMax.  The cells are then packed into register words and
+// stored for slices [s0, s1) of the slice-major layout (all slices, or a
+// register-range shard's own, its slice s0 first), or merged word by word by
+// atomic max for the chunk of a split hub (atomic_max_word; next[v] holds no
+// register above the result when the pass starts).  *flag is set when a
+// stored register exceeds the node's own counter.
+template <bool NIB>
+__device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t *__restrict__ lk,
+                                                const uint32_t *__restrict__ keys, uint32_t n, int p, int scheme,
+                                                int s_log2, uint32_t s0, uint32_t s1, uint8_t *__restrict__ nxt,
+                                                uint32_t *cells, uint32_t *stage, int lane, uint32_t *flag,
+                                                int *err) {
+    const uint32_t m = 1u << p;
+    const uint32_t v = it.v & ~kHubChunk;
+    for (uint32_t k = lane; k < m / 4u; k += 32) reinterpret_cast<uint4 *>(cells)[k] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    const uint32_t own = __ldg(keys + v);
+    if (lane == 0) cells[own >> 8] = own & 0xffu;
+    __syncwarp();
+    const int rows = table_rows(scheme);
+    const uint64_t e = it.b + it.cnt;
+    uint32_t r_next = (it.b + (uint64_t)lane < e) ? __ldcs(lk + it.b + lane) : 0u;
+    for (uint64_t base = it.b; base < e; base += 32) {
+        const bool valid = base + (uint64_t)lane < e;
+        const uint32_t r = r_next;
+        if (base + 32 + (uint64_t)lane < e) r_next = __ldcs(lk + base + 32 + lane);
+        uint32_t slot = 0;
+        for (int s = 1; s < rows; s++) slot += r >= (uint32_t)s * n ? 1u : 0u;
+        const uint32_t i = r - slot * n;
+        for (int s = 0; s < rows; s++) {
+            const uint32_t mask = __ballot_sync(0xffffffffu, valid && slot == (uint32_t)s);
+            if (!mask) continue;
+            if ((mask >> lane) & 1u) stage[__popc(mask & ((1u << lane) - 1u))] = i;
+            __syncwarp();
+            const int level = scheme == 0 ? s : 2 * s;
+            const int c = __popc(mask), per = 32 >> level;
+            const int my = lane >> level;
+            const uint32_t off = (uint32_t)lane & ((1u << level) - 1u);
+            for (int q = 0; q < c; q += 4 * per) {
+                uint32_t key[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int x = q + u * per + my;
+                    key[u] = x < c ? __ldg(keys + stage[x] + off) : 0u;  // a key is never 0 (rho >= 1)
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (key[u]) atomicMax(cells + (key[u] >> 8), key[u] & 0xffu);
+            }
+            __syncwarp();
+        }
+    }
+    // pack: 32-bit word k holds registers 4k .. 4k+3 (bytes), or 8k .. 8k+7
+    // (nibbles, the low nibble first)
+    const uint32_t per_word = NIB ? 8u : 4u, words = m / per_word;
+    const uint32_t own_j = own >> 8, own_rho = own & 0xffu;
+    const uint32_t S = 1u << s_log2;
+    bool changed = false;
+    for (uint32_t k = lane; k < words; k += 32) {
+        uint32_t w;
+        if (NIB) {
+            const uint4 a = reinterpret_cast<const uint4 *>(cells)[2 * k];
+            const uint4 b = reinterpret_cast<const uint4 *>(cells)[2 * k + 1];
+            w = a.x | a.y << 4 | a.z << 8 | a.w << 12 | b.x << 16 | b.y << 20 | b.z << 24 | b.w << 28;
+        } else {
+            const uint4 a = reinterpret_cast<const uint4 *>(cells)[k];
+            w = a.x | a.y << 8 | a.z << 16 | a.w << 24;
+        }
+        const uint32_t byte = 4u * k, sl = byte >> s_log2;
+        if (sl < s0 || sl >= s1) continue;
+        const uint32_t mine = own_j / per_word == k ? own_rho << ((32u / per_word) * (own_j % per_word)) : 0u;
+        changed |= w != mine;
+        uint32_t *dst =
+            reinterpret_cast<uint32_t *>(nxt + (((uint64_t)(sl - s0) * n + v) << s_log2) + (byte & (S - 1u)));
+        if (it.v & kHubChunk)
+            atomic_max_word<NIB>(dst, w, err);
+        else
+            *dst = w;
     }
     if (__any_sync(0xffffffffu, changed) && lane == 0) {
         if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);

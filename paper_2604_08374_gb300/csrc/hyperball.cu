@@ -47,11 +47,34 @@ const std::vector<double> &lc_table(int p) {
 
 namespace {
 
+// Alg. 1 initialisation; with `keys` given, each node's key (node_key) for the
+// first pass's scatter as well.
 __global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed, int nib,
-                               uint32_t s0, uint32_t s1) {
+                               uint32_t s0, uint32_t s1, uint32_t *__restrict__ keys) {
     const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     init_node(regs, n, p, S, seed, (uint32_t)v, nib != 0, s0, s1);
+    if (keys) keys[v] = node_key((uint32_t)v, p, seed, nib != 0);
+}
+
+// First pass of Eq. hll-union as a scatter of the nodes' keys (first_pass_item),
+// one warp per work item; all slices in one launch.  Each warp holds m + 32
+// words of shared memory (its register cells, then its lookup stage).
+template <bool NIB>
+__global__ void __launch_bounds__(128) hb_first_pass_kernel(const RunItem *__restrict__ items, uint64_t n_items,
+                                                            const uint32_t *__restrict__ lk,
+                                                            const uint32_t *__restrict__ keys, uint32_t n, int p,
+                                                            int scheme, int s_log2, uint32_t s0, uint32_t s1,
+                                                            uint8_t *__restrict__ nxt, uint32_t *__restrict__ flags) {
+    extern __shared__ __align__(16) uint32_t s_cells[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= n_items) return;
+    const uint32_t m = 1u << p;
+    uint32_t *cells = s_cells + (uint64_t)wib * (m + 32u);
+    first_pass_item<NIB>(items[warp], lk, keys, n, p, scheme, s_log2, s0, s1, nxt, cells, cells + m, lane, flags,
+                         reinterpret_cast<int *>(flags + 2));
 }
 
 // Eq. hll-union for one register slice, one warp per node (union_node_edges).
@@ -240,6 +263,7 @@ struct Plan {
     uint32_t hub_req = 0;  // runs mode: requested hub threshold (0 = automatic)
     uint32_t hub = 0;      // runs mode: nodes with more lookups than this are split across warps
     RunItemList items;     // runs mode: the union's work list for `hub`
+    bool first_scatter = false;  // runs mode: pass 1 by hb_first_pass_kernel (the keys live in the table region)
     uint64_t n = 0;
     // workspace layout (byte offsets, 256-aligned)
     uint64_t off_cur = 0, off_next = 0, off_c0 = 0, off_c1 = 0, off_sum = 0, off_lc = 0, off_flags = 0, off_tab = 0,
@@ -247,6 +271,11 @@ struct Plan {
 };
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// The first pass's scatter keeps one u32 cell per register for each of its
+// kFirstPassWarps warps in shared memory: up to 4 x (2^13 + 32) x 4 bytes.
+constexpr int kFirstPassMaxP = 13;
+constexpr int kFirstPassWarps = 4;
 
 // Hub threshold of the run-aware union (lookups per work item).
 static uint32_t hub_threshold(const vga_graph *g, int scheme, uint32_t requested) {
@@ -335,6 +364,17 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->hub_req = (tune && tune->hub_lookups > 0) ? (uint32_t)tune->hub_lookups
                  : (tabled && te.hub_lookups > 0) ? (uint32_t)te.hub_lookups
                                                   : 0u;
+    const int first = tune ? tune->first_pass : 0;
+    if (first < 0 || first > 2) {
+        set_error("first_pass = %d must be 0 (automatic), 1 (gather) or 2 (scatter)", first);
+        return VGA_EINVAL;
+    }
+    const bool scatter_ok = P->mode == kModeRuns && p <= kFirstPassMaxP;
+    if (first == 2 && !scatter_ok) {
+        set_error("first_pass = 2 (scatter) needs union mode 2 and p <= %d", kFirstPassMaxP);
+        return VGA_EINVAL;
+    }
+    P->first_scatter = scatter_ok && first != 1;
     const uint64_t regs = (uint64_t)P->n * P->node_bytes;
     uint64_t o = 0;
     P->off_cur = o;   o = align256(o + regs);
@@ -410,6 +450,7 @@ struct PendingTiming {
     cudaEvent_t start, stop;
     uint64_t edges, gather_bytes, hbm_bytes;
     int S, mode;
+    bool first;  // the first pass's scatter (hb_first_pass_kernel), not a union slice
 };
 
 template <int SS, bool NIB>
@@ -481,6 +522,52 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
     return VGA_OK;
 }
 
+// First pass of a run (or of a register-range shard holding slices [s0, s1))
+// by the scatter of the nodes' keys; `keys` were written by hb_init_kernel.
+static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *keys, uint8_t *nxt, uint32_t s0,
+                             uint32_t s1, uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings) {
+    const size_t smem = (size_t)kFirstPassWarps * (P.m + 32u) * 4u;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        const int most = kFirstPassWarps * ((1 << kFirstPassMaxP) + 32) * 4;
+        attr_err = cudaFuncSetAttribute(hb_first_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (attr_err == cudaSuccess)
+            attr_err =
+                cudaFuncSetAttribute(hb_first_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    });
+    VGA_CHECK_CUDA(attr_err);
+    PendingTiming pt{};
+    if (timings) {
+        VGA_CHECK_CUDA(cudaEventCreate(&pt.start));
+        VGA_CHECK_CUDA(cudaEventCreate(&pt.stop));
+        VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
+    }
+    const unsigned blocks = (unsigned)((P.items.count + kFirstPassWarps - 1) / kFirstPassWarps);
+    const int s_log2 = __builtin_ctz((unsigned)P.S);
+    if (blocks) {
+        if (P.nib)
+            hb_first_pass_kernel<true><<<blocks, kFirstPassWarps * 32, smem, stream>>>(
+                P.items.items, P.items.count, g->lk[P.scheme].d_lk, keys, (uint32_t)P.n, P.p, P.scheme, s_log2, s0,
+                s1, nxt, flags);
+        else
+            hb_first_pass_kernel<false><<<blocks, kFirstPassWarps * 32, smem, stream>>>(
+                P.items.items, P.items.count, g->lk[P.scheme].d_lk, keys, (uint32_t)P.n, P.p, P.scheme, s_log2, s0,
+                s1, nxt, flags);
+        count_launch();
+    }
+    VGA_CHECK_CUDA(cudaGetLastError());
+    if (timings) {
+        VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
+        pt.edges = g->n_edges;
+        pt.S = P.S;
+        pt.mode = P.mode;
+        pt.first = true;
+        timings->push_back(pt);
+    }
+    return VGA_OK;
+}
+
 // Read the union timings of a run: into the profile counters when profiling is
 // on, and summed into *sum_ms when it is given.
 static void settle_timings(std::vector<PendingTiming> &timings, bool to_profile, double *sum_ms) {
@@ -491,7 +578,11 @@ static void settle_timings(std::vector<PendingTiming> &timings, bool to_profile,
         const bool ok = cudaEventElapsedTime(&ms, pt.start, pt.stop) == cudaSuccess;
         if (sum_ms && !ok) *sum_ms = -1.0;
         if (sum_ms && ok && *sum_ms >= 0.0) *sum_ms += ms;
-        if (to_profile && ok) {
+        if (to_profile && ok && pt.first) {
+            ps.acc.first_pass_launches++;
+            ps.acc.first_pass_ms += ms;
+            ps.acc.first_pass_edges += pt.edges;
+        } else if (to_profile && ok) {
             ps.acc.union_launches++;
             ps.acc.union_ms += ms;
             ps.acc.union_edges += pt.edges;
@@ -608,8 +699,9 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         // split hubs merge into next[v] by atomic max: it must start below the result
         if (P.items.hubs) VGA_CHECK_CUDA(cudaMemsetAsync(nxt, 0, P.n * P.node_bytes, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
+        uint32_t *keys = P.first_scatter ? reinterpret_cast<uint32_t *>(tab) : nullptr;  // tab is unused in pass 1
         hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed, P.nib, 0u,
-                                                                          (uint32_t)P.slices);
+                                                                          (uint32_t)P.slices, keys);
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
         VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0
@@ -624,7 +716,11 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         }
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
-            VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, timed ? &timings : nullptr));
+            if (t == 1 && keys)
+                VGA_TRY(launch_first_pass(P, g, keys, nxt, 0u, (uint32_t)P.slices, flags, stream,
+                                          timed ? &timings : nullptr));
+            else
+                VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, timed ? &timings : nullptr));
             VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
             if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
             VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 12, cudaMemcpyDeviceToHost, stream));
@@ -845,8 +941,9 @@ int vga_shard_start(vga_shard *s, void *partial_dev, void *stream_ptr) {
         VGA_CHECK_CUDA(cudaMemsetAsync(s->cur, 0, regs, stream));
         if (P.items.hubs) VGA_CHECK_CUDA(cudaMemsetAsync(s->nxt, 0, regs, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(s->sum_d, 0, 8 * P.n, stream));
-        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(s->cur, (uint32_t)P.n, s->p, P.S, s->seed,
-                                                                          P.nib, s->s0, s->s1);
+        hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(
+            s->cur, (uint32_t)P.n, s->p, P.S, s->seed, P.nib, s->s0, s->s1,
+            P.first_scatter ? reinterpret_cast<uint32_t *>(s->tab) : nullptr);
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
@@ -876,7 +973,11 @@ int vga_shard_union(vga_shard *s, void *partial_dev, uint32_t *changed, void *st
     } settle{timings};
     if (P.n > 0) {
         VGA_CHECK_CUDA(cudaMemsetAsync(s->flags, 0, 4, stream));
-        VGA_TRY(launch_union(P, s->g, s->cur, s->nxt, s->tab, s->flags, stream, profiling ? &timings : nullptr));
+        if (s->t == 0 && P.first_scatter)
+            VGA_TRY(launch_first_pass(P, s->g, reinterpret_cast<const uint32_t *>(s->tab), s->nxt, s->s0, s->s1,
+                                      s->flags, stream, profiling ? &timings : nullptr));
+        else
+            VGA_TRY(launch_union(P, s->g, s->cur, s->nxt, s->tab, s->flags, stream, profiling ? &timings : nullptr));
     }
     VGA_TRY(shard_partials(s, s->nxt, partial_dev, stream));
     VGA_CHECK_CUDA(cudaMemcpyAsync(h, s->flags, 12, cudaMemcpyDeviceToHost, stream));
