@@ -18,6 +18,7 @@
 // single-graph run of the same job (same device functions, same order of
 // floating-point operations per node).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "engine.cuh"
@@ -48,7 +49,33 @@ __global__ void batch_init_kernel(JobDev *jobs, const uint64_t *__restrict__ nod
          x += (uint64_t)gridDim.x * blockDim.x) {
         const int j = find_job(node_start, n_jobs, x);
         const JobDev &J = jobs[j];
-        init_node(J.regs[0], J.n, J.p, J.S, J.seed, (uint32_t)(x - node_start[j]));
+        const uint32_t v = (uint32_t)(x - node_start[j]);
+        init_node(J.regs[0], J.n, J.p, J.S, J.seed, v);
+        if (J.first) reinterpret_cast<uint32_t *>(J.tab)[v] = node_key(v, J.p, J.seed, false);
+    }
+}
+
+// Pass 1 of the jobs in fjobs[0 .. n) (all of precision p, all fresh) as the
+// scatter of their nodes' keys (first_pass_item), one warp per work item of
+// the concatenated work lists; the jobs' union launch skips them in pass 1.
+__global__ void __launch_bounds__(kFirstPassWarps * 32) batch_first_pass_kernel(JobDev *jobs,
+                                                                               const uint32_t *__restrict__ fjobs,
+                                                                               const uint64_t *__restrict__ fstart,
+                                                                               int n, int p, int *error) {
+    extern __shared__ __align__(16) uint32_t s_cells[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t m = 1u << p;
+    uint32_t *cells = s_cells + (uint64_t)wib * (m + 32u);
+    const uint64_t total = fstart[n];
+    const uint64_t warps = (uint64_t)gridDim.x * kFirstPassWarps;
+    for (uint64_t x = (uint64_t)blockIdx.x * kFirstPassWarps + wib; x < total; x += warps) {
+        const int k = find_job(fstart, n, x);
+        JobDev &J = jobs[fjobs[k]];
+        const RunItem it = J.items[x - fstart[k]];
+        first_pass_item<false>(it, J.lk, reinterpret_cast<const uint32_t *>(J.tab), J.n, J.p, J.scheme,
+                               __ffs(J.S) - 1, 0u, (uint32_t)J.slices, J.regs[1], cells, cells + m, lane, &J.changed,
+                               error);
     }
 }
 
@@ -119,6 +146,7 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         const int k = find_job(item_start, n_jobs, item);
         JobDev &J = jobs[gjobs[k]];
         if (J.state != 0) continue;
+        if (RUNS && J.first && J.t == 0) continue;  // pass 1 was the scatter (engine_start)
         const uint32_t ublocks = (J.units + kEngineBlock - 1) / kEngineBlock;
         const uint64_t per_slice = (uint64_t)ublocks + (RUNS ? (uint64_t)J.tblocks : 0);
         const uint64_t r = item - item_start[k];
@@ -139,7 +167,8 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
             }
             q -= J.tblocks;
             if (threadIdx.x == 0) {
-                s_ok = wait_tables(J.tab_done + s, (uint32_t)t * (uint32_t)J.tblocks);
+                // every pass builds the slice's tables, but a scattered pass 1
+                s_ok = wait_tables(J.tab_done + s, (uint32_t)(t - J.first) * (uint32_t)J.tblocks);
                 if (!s_ok) atomicExch(error, 1);
             }
             __syncthreads();
@@ -259,6 +288,7 @@ int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const
         J.scheme = L.scheme;
         J.items = list.items;
         J.units = (uint32_t)list.count;
+        J.first = p <= kFirstPassMaxP ? 1 : 0;
     } else {
         J.units = g->n;
     }
@@ -304,7 +334,7 @@ int upload_lc_tables(uint8_t *dst, const bool *used, cudaStream_t stream) {
 uint64_t engine_arrays_bytes(int cap) {
     const uint64_t c = (uint64_t)std::max(cap, 1);
     return align256(sizeof(JobDev) * c) + align256(8 * (c + 1)) + align256(4 * c) + align256(8 * (c + kGroups)) +
-           align256(8 * kGroups) + 256;
+           align256(8 * kGroups) + 256 + align256(4 * c) + align256(8 * (c + kGroups));
 }
 
 EngineArrays engine_arrays_at(uint8_t *base, int cap) {
@@ -318,6 +348,9 @@ EngineArrays engine_arrays_at(uint8_t *base, int cap) {
     A.counters = reinterpret_cast<unsigned long long *>(base + o); o = align256(o + 8 * kGroups);
     A.any_running = reinterpret_cast<int *>(base + o);
     A.error = reinterpret_cast<int *>(base + o + 4);
+    o += 256;
+    A.fjobs = reinterpret_cast<uint32_t *>(base + o); o = align256(o + 4 * c);
+    A.fstart = reinterpret_cast<uint64_t *>(base + o);
     A.cap = cap;
     return A;
 }
@@ -415,6 +448,55 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
     batch_estimate_kernel<<<E.grid_warps, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes, 1);
     count_launch();
     VGA_CHECK_CUDA(cudaGetLastError());
+    // pass 1 of the run-aware jobs: the scatter, one launch per precision
+    std::vector<uint32_t> fj;
+    std::vector<uint64_t> fs;
+    struct Launch {
+        int p, n;
+        size_t job_off, start_off;
+    };
+    std::vector<Launch> launches;
+    for (int p = 4; p <= kFirstPassMaxP; p++) {
+        Launch L{p, 0, fj.size(), fs.size()};
+        uint64_t items = 0;
+        for (size_t k = 0; k < jobs.size(); k++) {
+            if (!jobs[k].first || jobs[k].p != p) continue;
+            fj.push_back((uint32_t)k);
+            fs.push_back(items);
+            items += jobs[k].units;
+            L.n++;
+        }
+        if (!L.n) continue;
+        fs.push_back(items);
+        launches.push_back(L);
+    }
+    if (launches.empty()) return VGA_OK;
+    VGA_CHECK_CUDA(cudaMemcpyAsync(A.fjobs, fj.data(), 4 * fj.size(), cudaMemcpyHostToDevice, stream));
+    VGA_CHECK_CUDA(cudaMemcpyAsync(A.fstart, fs.data(), 8 * fs.size(), cudaMemcpyHostToDevice, stream));
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(batch_first_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kFirstPassWarps * ((1 << kFirstPassMaxP) + 32) * 4);
+    });
+    VGA_CHECK_CUDA(attr_err);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (const Launch &L : launches) {
+        const size_t smem = (size_t)kFirstPassWarps * ((1u << L.p) + 32u) * 4u;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_first_pass_kernel, kFirstPassWarps * 32, smem);
+        const uint64_t items = fs[L.start_off + L.n];
+        const unsigned grid = (unsigned)std::max<uint64_t>(
+            1, std::min<uint64_t>((items + kFirstPassWarps - 1) / kFirstPassWarps, (uint64_t)sms * std::max(1, per_sm)));
+        batch_first_pass_kernel<<<grid, kFirstPassWarps * 32, smem, stream>>>(A.jobs, A.fjobs + L.job_off,
+                                                                              A.fstart + L.start_off, L.n, L.p,
+                                                                              A.error);
+        count_launch();
+    }
+    VGA_CHECK_CUDA(cudaGetLastError());
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));  // the host vectors go out of scope
     return VGA_OK;
 }
 

@@ -34,6 +34,7 @@ struct JobDev {
     int mode;               // 1 one gather per neighbour, 2 per run (sparse tables)
     int tblocks;            // table items per slice (mode 2), TableShape<S>::B rows each
     int scheme;             // table scheme of the lookups (mode 2)
+    int first;              // 1: pass 1 is the scatter of the nodes' keys (engine_start; keys in tab)
     uint32_t changed, inc;  // flags of the pass in progress
     int t;                  // passes completed
     int state;              // 0 running, 1 stopped at this step (finalize), 2 done
@@ -55,6 +56,8 @@ struct EngineArrays {
     unsigned long long *counters = nullptr; // kGroups: the groups' item queues
     int *any_running = nullptr;
     int *error = nullptr;                   // set when a bounded wait gave up
+    uint32_t *fjobs = nullptr;              // cap: jobs whose pass 1 is the scatter, grouped by p
+    uint64_t *fstart = nullptr;             // cap + 14: per p group, prefix of work items over its jobs
     int cap = 0;
 };
 

@@ -272,10 +272,6 @@ struct Plan {
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
-// The first pass's scatter keeps one u32 cell per register for each of its
-// kFirstPassWarps warps in shared memory: up to 4 x (2^13 + 32) x 4 bytes.
-constexpr int kFirstPassMaxP = 13;
-constexpr int kFirstPassWarps = 4;
 
 // Hub threshold of the run-aware union (lookups per work item).
 static uint32_t hub_threshold(const vga_graph *g, int scheme, uint32_t requested) {

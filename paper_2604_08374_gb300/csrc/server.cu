@@ -180,6 +180,15 @@ void batched_lane(vga_server *S) {
             EngineSet E;
             int rc = engine_upload(A_new, start, &E, stream);
             if (rc == VGA_OK) rc = engine_start(A_new, start, E, stream);
+            if (rc == VGA_OK) {  // the scattered pass 1 left its change flags in the descriptors
+                cudaError_t e = cudaMemcpyAsync(start.data(), A_new.jobs, sizeof(JobDev) * start.size(),
+                                                cudaMemcpyDeviceToHost, stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+                if (e != cudaSuccess) {
+                    set_error("reading the started requests' state failed: %s", cudaGetErrorString(e));
+                    rc = VGA_ECUDA;
+                }
+            }
             if (rc != VGA_OK) {
                 for (const auto &r : started) fail(S, r, rc, vga_last_error(), stream);
                 started.clear();

@@ -184,6 +184,12 @@ int ensure_run_items(const vga_graph *g, int scheme, uint32_t hub_lookups, cudaS
 // scheme's lookups must have been counted (ensure_run_lookups).
 uint32_t hub_lookups_auto(const vga_graph *g, int scheme);
 
+// The first pass's scatter (first_pass_item) keeps one u32 cell per register
+// for each of its kFirstPassWarps warps in shared memory: up to
+// 4 x (2^13 + 32) x 4 bytes per CTA.
+constexpr int kFirstPassMaxP = 13;
+constexpr int kFirstPassWarps = 4;
+
 // Autotuner table (autotune.cu): the installed entry for g's degree bucket.
 bool tune_table_lookup(const vga_graph *g, vga_tune_entry *out);
 

@@ -110,3 +110,32 @@ def test_batch_rejects_bad_jobs(vga, graphs):
     with pytest.raises(vga.VgaError) as e:
         vga.hyperball_run_batch(jobs)
     assert e.value.status == vga.VGA_EINVAL
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_scattered_first_pass(vga, graphs, use_graph):
+    # run-aware jobs with p <= 13 take pass 1 as the scatter of their keys in
+    # engine_start and skip the union launch of pass 1; p = 14 and
+    # per-neighbour jobs gather it.  Every job must equal a single run whose
+    # pass 1 is the gather, including jobs that stop right after pass 1.
+    torch = pytest.importorskip("torch")
+    jobs = []
+    for k, (p, d, mode, conv) in enumerate([(13, 2, 2, 0), (14, 2, 2, 0), (9, 1, 2, 0), (9, 1, 1, 0), (4, 0, 2, 1),
+                                            (12, 0, 0, 0), (13, 1, 2, 1), (10, 3, 2, 0)]):
+        g = graphs[k % 4][0]
+        n = g.n_nodes
+        jobs.append(dict(graph=g, p=p, d=d, seed=1000 + k, conv_mode=conv, union_mode=mode,
+                         mean_depth=torch.full((n,), -7.0, dtype=torch.float64, device="cuda"),
+                         ball=torch.full((n,), -7.0, dtype=torch.float64, device="cuda")))
+    its = vga.hyperball_run_batch(jobs, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for k, j in enumerate(jobs):
+        g, n = j["graph"], j["graph"].n_nodes
+        md = torch.empty(n, dtype=torch.float64, device="cuda")
+        ball = torch.empty_like(md)
+        it = vga.hyperball_run_dev(g, j["p"], j["d"], j["seed"], md, ball, conv_mode=j["conv_mode"],
+                                   union_mode=j["union_mode"], first_pass=1)
+        torch.cuda.synchronize()
+        assert its[k] == it, k
+        assert np.array_equal(j["mean_depth"].cpu().numpy(), md.cpu().numpy(), equal_nan=True), k
+        assert np.array_equal(j["ball"].cpu().numpy(), ball.cpu().numpy()), k
