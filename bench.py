@@ -94,6 +94,8 @@ def parse_args():
                     help="1: mark the union's table region persisting in L2 (access-policy window)")
     ap.add_argument("--first-pass", type=int, default=0, choices=[0, 1, 2],
                     help="pass 1: 0 automatic (scatter), 1 the union's gather, 2 the scatter")
+    ap.add_argument("--track-changes", type=int, default=0, choices=[0, 1, 2],
+                    help="change tracking: 0 automatic, 1 off, 2 every pass from the second")
     ap.add_argument("--table-levels", type=int, default=0, choices=[0, 3, 5],
                     help="run-aware table rows per node: 5 (windows 1..16), 3 (1, 4, 16), 0 = automatic")
     ap.add_argument("--sharded", action="store_true",
@@ -379,7 +381,7 @@ def run_ours(args, dist: Dist):
                                              warps_per_cta=args.warps, union_mode=args.union_mode,
                                              register_bits=0 if args.register_bits == 8 else args.register_bits,
                                              hub_lookups=args.hub_lookups, table_levels=args.table_levels,
-                                             first_pass=args.first_pass)
+                                             first_pass=args.first_pass, track_changes=args.track_changes)
         # a forced slice width or table scheme sizes its own workspace
         forced = args.slice_bytes or args.table_levels
         return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=None if forced else ws,
@@ -388,7 +390,8 @@ def run_ours(args, dist: Dist):
                                      union_mode=args.union_mode if union_mode is None else union_mode,
                                      register_bits=0 if args.register_bits == 8 else args.register_bits,
                                      hub_lookups=args.hub_lookups, table_levels=args.table_levels,
-                                     l2_window=args.l2_window, first_pass=args.first_pass)
+                                     l2_window=args.l2_window, first_pass=args.first_pass,
+                                     track_changes=args.track_changes)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -592,6 +595,7 @@ def run_ours(args, dist: Dist):
                        "register_bits": args.register_bits, "table_levels": args.table_levels or "auto",
                        "l2_window": args.l2_window,
                        "first_pass": {0: "auto", 1: "gather", 2: "scatter"}[args.first_pass],
+                       "track_changes": {0: "auto", 1: "off", 2: "every pass"}[args.track_changes],
                        "autotune": tuned,
                        "parallelism": f"register shards x{dist.world}" if sharded else f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (compressed CSR > 129 MB), no flush",

@@ -204,6 +204,15 @@ typedef struct vga_tuning {
                             shared memory; p <= 13); 1: the union kernel, like every later
                             pass; 0: automatic (2 wherever allowed).  Same registers bit
                             for bit.                                                       */
+    int track_changes;   /* mode 2, at most 32 slices: change tracking.  Each pass records
+                            which (node, slice) pairs changed; a node needs the next pass in
+                            a slice only if one of its neighbours changed there (otherwise
+                            its registers already hold the maximum), which is found through
+                            the range lookups before the pass, the other nodes keeping their
+                            registers.  0: automatic (a pass is tracked when the one before
+                            changed fewer than 1 % of the pairs, e.g. the last passes of an
+                            unlimited-depth run); 1: off; 2: every pass from the second.
+                            Same registers bit for bit.                                    */
 } vga_tuning;
 
 /*
@@ -459,6 +468,11 @@ typedef struct vga_profile {
                                      first_pass), timed apart from the union slices       */
     double first_pass_ms;         /* their summed device time                             */
     uint64_t first_pass_edges;    /* neighbour unions they performed (E per launch)       */
+    uint64_t tracked_launches;    /* union slices of change-tracked passes (vga_tuning.
+                                     track_changes) and the need step before each such
+                                     pass, timed apart: their work depends on how many
+                                     nodes need it                                        */
+    double tracked_ms;            /* their summed device time                             */
 } vga_profile;
 
 /* Enable (1) or disable (0) event timing of union launches. */

@@ -193,11 +193,12 @@ __device__ __forceinline__ void init_node(uint8_t *__restrict__ regs, uint32_t n
 }
 
 // Fold the node's own slice into the gathered maximum, store it, and set
-// *flag if any register changed (one atomic per warp at most).
+// *flag if any register changed (one atomic per warp at most); with chg given
+// (the slice's change bytes), chg[v] = 1 as well.
 template <int S, bool NIB>
 __device__ __forceinline__ void union_store(const typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4],
                                             const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, uint32_t v,
-                                            int lane, uint32_t *flag) {
+                                            int lane, uint32_t *flag, uint8_t *chg = nullptr) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
     uint4 nb[Sh::V4];
@@ -216,6 +217,7 @@ __device__ __forceinline__ void union_store(const typename RegFmt<NIB>::Acc (&ac
     }
     if (__any_sync(0xffffffffu, changed) && lane == 0) {
         if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
+        if (chg) chg[v] = 1u;
     }
 }
 
@@ -388,7 +390,7 @@ __device__ __forceinline__ void atomic_max_word(uint32_t *p, uint32_t val, int *
 template <int S, bool NIB>
 __device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4],
                                                 const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, uint32_t v,
-                                                int lane, uint32_t *flag, int *err) {
+                                                int lane, uint32_t *flag, int *err, uint8_t *chg = nullptr) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
     uint4 nb[Sh::V4];
@@ -410,6 +412,7 @@ __device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc 
     }
     if (__any_sync(0xffffffffu, changed) && lane == 0) {
         if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
+        if (chg) chg[v] = 1u;
     }
 }
 
@@ -428,13 +431,14 @@ __device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc 
 // register-range shard's own, its slice s0 first), or merged word by word by
 // atomic max for the chunk of a split hub (atomic_max_word; next[v] holds no
 // register above the result when the pass starts).  *flag is set when a
-// stored register exceeds the node's own counter.
+// stored register exceeds the node's own counter, and with chg given (change
+// bytes, [slice][N] from slice s0 on) chg[s][v] = 1 for each slice where one does.
 template <bool NIB>
 __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t *__restrict__ lk,
                                                 const uint32_t *__restrict__ keys, uint32_t n, int p, int scheme,
                                                 int s_log2, uint32_t s0, uint32_t s1, uint8_t *__restrict__ nxt,
                                                 uint32_t *cells, uint32_t *stage, int lane, uint32_t *flag,
-                                                int *err) {
+                                                int *err, uint8_t *chg = nullptr) {
     const uint32_t m = 1u << p;
     const uint32_t v = it.v & ~kHubChunk;
     for (uint32_t k = lane; k < m / 4u; k += 32) reinterpret_cast<uint4 *>(cells)[k] = make_uint4(0, 0, 0, 0);
@@ -495,6 +499,7 @@ __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t
         if (sl < s0 || sl >= s1) continue;
         const uint32_t mine = own_j / per_word == k ? own_rho << ((32u / per_word) * (own_j % per_word)) : 0u;
         changed |= w != mine;
+        if (chg && w != mine) chg[(uint64_t)(sl - s0) * n + v] = 1u;  // lanes of one slice store the same byte
         uint32_t *dst =
             reinterpret_cast<uint32_t *>(nxt + (((uint64_t)(sl - s0) * n + v) << s_log2) + (byte & (S - 1u)));
         if (it.v & kHubChunk)
@@ -504,6 +509,26 @@ __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t
     }
     if (__any_sync(0xffffffffu, changed) && lane == 0) {
         if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
+    }
+}
+
+// A work item whose node has no neighbour that changed in this slice during
+// the previous pass keeps its registers: next[v] = cur[v] (when no neighbour u
+// of v changed, max over u of cur[u] is the previous pass's max over u, which
+// cur[v] already holds).  The chunk of a split hub merges cur[v] into next[v]
+// by word-wise atomic max instead, since other chunks of v may be merging
+// their own results at the same time.
+template <int S, bool NIB>
+__device__ __forceinline__ void keep_item(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, uint32_t v,
+                                          bool hub, int lane, int *err) {
+    const uint64_t row = (uint64_t)v * S;
+    if (!hub) {
+        for (int q = lane; q < S / 16; q += 32)
+            reinterpret_cast<uint4 *>(nxt + row)[q] = __ldg(reinterpret_cast<const uint4 *>(cur + row) + q);
+    } else {
+        for (int q = lane; q < S / 4; q += 32)
+            atomic_max_word<NIB>(reinterpret_cast<uint32_t *>(nxt + row) + q,
+                                 __ldg(reinterpret_cast<const uint32_t *>(cur + row) + q), err);
     }
 }
 

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(128) hb_first_pass_kernel(const RunItem *__res
                                                             const uint32_t *__restrict__ lk,
                                                             const uint32_t *__restrict__ keys, uint32_t n, int p,
                                                             int scheme, int s_log2, uint32_t s0, uint32_t s1,
-                                                            uint8_t *__restrict__ nxt, uint32_t *__restrict__ flags) {
+                                                            uint8_t *__restrict__ nxt, uint32_t *__restrict__ flags,
+                                                            uint8_t *__restrict__ chg) {
     extern __shared__ __align__(16) uint32_t s_cells[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(128) hb_first_pass_kernel(const RunItem *__res
     const uint32_t m = 1u << p;
     uint32_t *cells = s_cells + (uint64_t)wib * (m + 32u);
     first_pass_item<NIB>(items[warp], lk, keys, n, p, scheme, s_log2, s0, s1, nxt, cells, cells + m, lane, flags,
-                         reinterpret_cast<int *>(flags + 2));
+                         reinterpret_cast<int *>(flags + 2), chg);
 }
 
 // Eq. hll-union for one register slice, one warp per node (union_node_edges).
@@ -94,13 +95,17 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
 // Run-aware Eq. hll-union for one register slice, one warp per work item
 // (RunItem: a whole node, or one chunk of a split hub), lookups staged by TMA,
 // after the slice's sparse table has been built.  flags[2] records a bounded
-// wait that ran out.
+// wait that ran out.  With need given (a change-tracked pass), a node whose
+// bit `s` is clear keeps its registers (keep_item); with chg given, changed
+// nodes are recorded in it (the slice's change bytes).
 template <int S, bool NIB>
 __global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__restrict__ items, uint64_t n_items,
                                                             const uint32_t *__restrict__ lk,
                                                             const uint8_t *__restrict__ cur,
                                                             const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt,
-                                                            uint32_t n, uint32_t *__restrict__ flags) {
+                                                            uint32_t n, uint32_t *__restrict__ flags,
+                                                            const uint32_t *__restrict__ need, int s,
+                                                            uint8_t *__restrict__ chg) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     LkStage *stages = reinterpret_cast<LkStage *>(s_dyn);
     const int lane = threadIdx.x & 31;
@@ -108,6 +113,11 @@ __global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__res
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n_items) return;
     const RunItem it = items[warp];
+    if (need && !((need[it.v & ~kHubChunk] >> s) & 1u)) {
+        keep_item<S, NIB>(cur, nxt, it.v & ~kHubChunk, (it.v & kHubChunk) != 0, lane,
+                          reinterpret_cast<int *>(flags + 2));
+        return;
+    }
     LkStage &st = stages[wib];
     lk_stage_init(st, lane);
     uint32_t phase = 0;
@@ -115,9 +125,87 @@ __global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__res
     typename RegFmt<NIB>::Acc acc[4 * GatherShape<S>::V4] = {};
     union_range_runs<S, NIB>(lk, tab, it.b, it.b + it.cnt, st, phase, lane, acc, err);
     if (it.v & kHubChunk)
-        union_store_hub<S, NIB>(acc, cur, nxt, it.v & ~kHubChunk, lane, flags, err);
+        union_store_hub<S, NIB>(acc, cur, nxt, it.v & ~kHubChunk, lane, flags, err, chg);
     else
-        union_store<S, NIB>(acc, cur, nxt, it.v, lane, flags);
+        union_store<S, NIB>(acc, cur, nxt, it.v, lane, flags, chg);
+}
+
+// Change-tracked passes.  The union of pass t records, per slice s, which nodes
+// changed (change bytes chg[s][v], 0 or 1).  A later pass t + 1 needs to
+// recompute node v in slice s only if some neighbour of v changed slice s in
+// pass t; hb_ortab_kernel and hb_need_kernel find those nodes through the
+// run-aware union's own range lookups.
+
+// Number of (node, slice) pairs that changed in the pass just run: the change
+// bytes are 0 or 1, so the set bits of each 32-bit word count them.
+__global__ void hb_count_kernel(const uint32_t *__restrict__ words, uint64_t n_words,
+                                unsigned long long *__restrict__ count) {
+    __shared__ uint32_t part[32];
+    uint32_t c = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        c += __popc(words[i]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+        if (t) atomicAdd(count, t);
+    }
+}
+
+// Range-OR table of the change masks: row r = slot * n + i holds, bit s per
+// slice, whether a node of the window [i, i + w) changed slice s, w being the
+// window width of the slot in the table scheme (the rows and row indices of
+// the table of range maxima, so that a range lookup addresses both).
+__global__ void hb_ortab_kernel(const uint8_t *__restrict__ chg, uint32_t n, int slices, int scheme,
+                                uint32_t *__restrict__ ortab) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int rows = table_rows(scheme);
+    uint32_t acc = 0;
+    int slot = 0;
+    for (uint32_t j = 0; j < (1u << kRunLevels) && slot < rows; j++) {
+        if (i + j < n)
+            for (int sl = 0; sl < slices; sl++) acc |= (uint32_t)chg[(uint64_t)sl * n + i + j] << sl;
+        const int level = scheme == 0 ? slot : 2 * slot;
+        if (j + 1u == (1u << level)) ortab[(uint64_t)slot++ * n + i] = acc;
+    }
+}
+
+// need[v], bit s: one of node v's range lookups covers a node that changed
+// slice s in the previous pass.  One warp per work item; split hubs OR their
+// chunks' masks together (need is zeroed first).  A warp stops early once
+// every slice is needed.
+__global__ void __launch_bounds__(256) hb_need_kernel(const RunItem *__restrict__ items, uint64_t n_items,
+                                                      const uint32_t *__restrict__ lk,
+                                                      const uint32_t *__restrict__ ortab, uint32_t all,
+                                                      uint32_t *__restrict__ need) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= n_items) return;
+    const RunItem it = items[warp];
+    const uint64_t e = it.b + it.cnt;
+    uint32_t acc = 0;
+    uint64_t kb = it.b;  // whole chunks of 256 lookups first (a warp-uniform loop)
+    for (; kb + 256u <= e; kb += 256u) {
+        uint32_t r[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) r[u] = __ldcs(lk + kb + u * 32u + lane);
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc |= __ldg(ortab + r[u]);
+        if (__reduce_or_sync(0xffffffffu, acc) == all) break;
+    }
+    if (__reduce_or_sync(0xffffffffu, acc) != all)
+        for (uint64_t k = kb + lane; k < e; k += 32u) acc |= __ldg(ortab + __ldcs(lk + k));
+    acc = __reduce_or_sync(0xffffffffu, acc);
+    if (lane == 0) {
+        if (it.v & kHubChunk)
+            atomicOr(need + (it.v & ~kHubChunk), acc);
+        else
+            need[it.v] = acc;
+    }
 }
 
 // The slice's table region (table_item: T_0 and the scheme's levels), B rows
@@ -264,13 +352,21 @@ struct Plan {
     uint32_t hub = 0;      // runs mode: nodes with more lookups than this are split across warps
     RunItemList items;     // runs mode: the union's work list for `hub`
     bool first_scatter = false;  // runs mode: pass 1 by hb_first_pass_kernel (the keys live in the table region)
+    int track = 0;               // runs mode, slices <= 32: change tracking (0 off, 1 automatic, 2 every pass)
     uint64_t n = 0;
     // workspace layout (byte offsets, 256-aligned)
     uint64_t off_cur = 0, off_next = 0, off_c0 = 0, off_c1 = 0, off_sum = 0, off_lc = 0, off_flags = 0, off_tab = 0,
-             total = 0;
+             off_chg = 0, off_need = 0, off_ortab = 0, chg_bytes = 0, total = 0;
 };
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Change tracking keeps one bit per slice in a 32-bit mask per node.
+constexpr int kTrackMaxSlices = 32;
+// The automatic rule tracks a pass when the previous one changed fewer than
+// this share of the (node, slice) pairs: after a pass that changed more,
+// nearly every node has a changed neighbour in every slice.
+constexpr double kTrackBelow = 0.01;
 
 
 // Hub threshold of the run-aware union (lookups per work item).
@@ -382,6 +478,23 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->off_flags = o; o = align256(o + 64);
     P->off_tab = o;
     if (P->mode == kModeRuns) o = align256(o + (uint64_t)table_rows(P->scheme) * P->n * (uint64_t)S);
+    const int track = tune ? tune->track_changes : 0;
+    if (track < 0 || track > 2) {
+        set_error("track_changes = %d must be 0 (automatic), 1 (off) or 2 (every pass)", track);
+        return VGA_EINVAL;
+    }
+    const bool track_ok = P->mode == kModeRuns && P->slices <= kTrackMaxSlices;
+    if (track == 2 && !track_ok) {
+        set_error("track_changes = 2 needs union mode 2 and at most %d slices (have %d)", kTrackMaxSlices, P->slices);
+        return VGA_EINVAL;
+    }
+    P->track = !track_ok || track == 1 ? 0 : track == 2 ? 2 : 1;
+    if (P->track) {
+        P->chg_bytes = align256((uint64_t)P->slices * P->n);
+        P->off_chg = o;   o = align256(o + P->chg_bytes);
+        P->off_need = o;  o = align256(o + 4 * P->n);
+        P->off_ortab = o; o = align256(o + 4ull * table_rows(P->scheme) * P->n);
+    }
     P->total = o;
     return VGA_OK;
 }
@@ -446,12 +559,13 @@ struct PendingTiming {
     cudaEvent_t start, stop;
     uint64_t edges, gather_bytes, hbm_bytes;
     int S, mode;
-    bool first;  // the first pass's scatter (hb_first_pass_kernel), not a union slice
+    bool first;    // the first pass's scatter (hb_first_pass_kernel), not a union slice
+    bool tracked;  // a union slice of a change-tracked pass (its work depends on the changes)
 };
 
 template <int SS, bool NIB>
 static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t *c, uint8_t *x, uint8_t *tab,
-                               uint32_t *flags, cudaStream_t stream) {
+                               uint32_t *flags, cudaStream_t stream, const uint32_t *need, int s, uint8_t *chg) {
     const unsigned blocks = (unsigned)((P.n + P.warps - 1) / P.warps);
     const size_t smem = (size_t)P.warps * 32 * sizeof(uint32_t);
     if (P.mode == kModeRuns) {
@@ -460,7 +574,7 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
         hb_table_kernel<SS, NIB><<<table_blocks, 256, 0, stream>>>(c, tab, (uint32_t)P.n, P.scheme);
         count_launch();
         hb_union_runs_kernel<SS, NIB><<<item_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
-            P.items.items, P.items.count, g->lk[P.scheme].d_lk, c, tab, x, (uint32_t)P.n, flags);
+            P.items.items, P.items.count, g->lk[P.scheme].d_lk, c, tab, x, (uint32_t)P.n, flags, need, s, chg);
     } else {
         hb_union_kernel<SS, NIB><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
                                                                     flags);
@@ -468,12 +582,16 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
     count_launch();
 }
 
+// One pass of the union over every slice.  need (a change-tracked pass) and
+// chg (change bytes to record, [slice][N]) may be null.
 static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, uint8_t *nxt, uint8_t *tab,
-                        uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings) {
+                        uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings,
+                        const uint32_t *need = nullptr, uint8_t *chg = nullptr) {
     const uint64_t slice_bytes = (uint64_t)P.n * P.S;
     for (int s = 0; s < P.slices; s++) {
         const uint8_t *c = cur + (uint64_t)s * slice_bytes;
         uint8_t *x = nxt + (uint64_t)s * slice_bytes;
+        uint8_t *cs = chg ? chg + (uint64_t)s * P.n : nullptr;
         PendingTiming pt{};
         if (timings) {
             VGA_CHECK_CUDA(cudaEventCreate(&pt.start));
@@ -481,20 +599,20 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
         }
         switch (P.S) {
-            case 16: P.nib ? launch_union_slice<16, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<16, false>(P, g, c, x, tab, flags, stream); break;
-            case 32: P.nib ? launch_union_slice<32, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<32, false>(P, g, c, x, tab, flags, stream); break;
-            case 64: P.nib ? launch_union_slice<64, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<64, false>(P, g, c, x, tab, flags, stream); break;
-            case 128: P.nib ? launch_union_slice<128, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<128, false>(P, g, c, x, tab, flags, stream); break;
-            case 256: P.nib ? launch_union_slice<256, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<256, false>(P, g, c, x, tab, flags, stream); break;
-            case 512: P.nib ? launch_union_slice<512, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<512, false>(P, g, c, x, tab, flags, stream); break;
-            case 1024: P.nib ? launch_union_slice<1024, true>(P, g, c, x, tab, flags, stream)
-                             : launch_union_slice<1024, false>(P, g, c, x, tab, flags, stream); break;
+            case 16: P.nib ? launch_union_slice<16, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<16, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
+            case 32: P.nib ? launch_union_slice<32, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<32, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
+            case 64: P.nib ? launch_union_slice<64, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<64, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
+            case 128: P.nib ? launch_union_slice<128, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<128, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
+            case 256: P.nib ? launch_union_slice<256, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<256, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
+            case 512: P.nib ? launch_union_slice<512, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<512, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
+            case 1024: P.nib ? launch_union_slice<1024, true>(P, g, c, x, tab, flags, stream, need, s, cs)
+                             : launch_union_slice<1024, false>(P, g, c, x, tab, flags, stream, need, s, cs); break;
             default:
                 set_error("internal: slice width %d", P.S);
                 return VGA_EINVAL;
@@ -511,6 +629,7 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             }
             pt.S = P.S;
             pt.mode = P.mode;
+            pt.tracked = need != nullptr;
             timings->push_back(pt);
         }
     }
@@ -521,7 +640,8 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
 // First pass of a run (or of a register-range shard holding slices [s0, s1))
 // by the scatter of the nodes' keys; `keys` were written by hb_init_kernel.
 static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *keys, uint8_t *nxt, uint32_t s0,
-                             uint32_t s1, uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings) {
+                             uint32_t s1, uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings,
+                             uint8_t *chg = nullptr) {
     const size_t smem = (size_t)kFirstPassWarps * (P.m + 32u) * 4u;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -545,11 +665,11 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *
         if (P.nib)
             hb_first_pass_kernel<true><<<blocks, kFirstPassWarps * 32, smem, stream>>>(
                 P.items.items, P.items.count, g->lk[P.scheme].d_lk, keys, (uint32_t)P.n, P.p, P.scheme, s_log2, s0,
-                s1, nxt, flags);
+                s1, nxt, flags, chg);
         else
             hb_first_pass_kernel<false><<<blocks, kFirstPassWarps * 32, smem, stream>>>(
                 P.items.items, P.items.count, g->lk[P.scheme].d_lk, keys, (uint32_t)P.n, P.p, P.scheme, s_log2, s0,
-                s1, nxt, flags);
+                s1, nxt, flags, chg);
         count_launch();
     }
     VGA_CHECK_CUDA(cudaGetLastError());
@@ -561,6 +681,49 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *
         pt.first = true;
         timings->push_back(pt);
     }
+    return VGA_OK;
+}
+
+// Before a change-tracked pass: the range-OR table of the previous pass's
+// change bytes, then each node's need mask (one bit per slice).  Timed with
+// the tracked union slices.
+static int launch_need(const Plan &P, const vga_graph *g, const uint8_t *chg, uint32_t *ortab, uint32_t *need,
+                       cudaStream_t stream, std::vector<PendingTiming> *timings) {
+    PendingTiming pt{};
+    if (timings) {
+        VGA_CHECK_CUDA(cudaEventCreate(&pt.start));
+        VGA_CHECK_CUDA(cudaEventCreate(&pt.stop));
+        VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
+    }
+    hb_ortab_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(chg, (uint32_t)P.n, P.slices, P.scheme,
+                                                                       ortab);
+    count_launch();
+    VGA_CHECK_CUDA(cudaMemsetAsync(need, 0, 4 * P.n, stream));
+    const uint32_t all = P.slices >= 32 ? 0xffffffffu : (1u << P.slices) - 1u;
+    hb_need_kernel<<<(unsigned)((P.items.count + 7) / 8), 256, 0, stream>>>(P.items.items, P.items.count,
+                                                                            g->lk[P.scheme].d_lk, ortab, all, need);
+    count_launch();
+    VGA_CHECK_CUDA(cudaGetLastError());
+    if (timings) {
+        VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
+        pt.tracked = true;
+        timings->push_back(pt);
+    }
+    return VGA_OK;
+}
+
+// (node, slice) pairs the pass changed, into the 64-bit counter at flags + 4.
+static int launch_count(const Plan &P, const uint8_t *chg, uint32_t *flags, cudaStream_t stream) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t words = P.chg_bytes / 4;
+    const unsigned grid = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((words + 255) / 256, (uint64_t)std::max(sms, 1) * 4));
+    hb_count_kernel<<<grid, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(chg), words,
+                                              reinterpret_cast<unsigned long long *>(flags + 4));
+    count_launch();
+    VGA_CHECK_CUDA(cudaGetLastError());
     return VGA_OK;
 }
 
@@ -578,6 +741,9 @@ static void settle_timings(std::vector<PendingTiming> &timings, bool to_profile,
             ps.acc.first_pass_launches++;
             ps.acc.first_pass_ms += ms;
             ps.acc.first_pass_edges += pt.edges;
+        } else if (to_profile && ok && pt.tracked) {
+            ps.acc.tracked_launches++;
+            ps.acc.tracked_ms += ms;
         } else if (to_profile && ok) {
             ps.acc.union_launches++;
             ps.acc.union_ms += ms;
@@ -702,32 +868,51 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         VGA_CHECK_CUDA(cudaGetLastError());
         VGA_TRY(launch_estimate(P, cur, 0, lc, nullptr, c_prev, sum_d, flags, stream));  // c_0
         if (max_trace >= 0) VGA_TRY(copy_trace(P, cur, c_prev, 0, trace_regs, trace_c, stream));
-        uint32_t hflags[3];
-        VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 12, stream));
+        struct {
+            uint32_t f[4];        // changed, estimate increase, bounded wait gave up, unused
+            uint64_t n_changed;   // (node, slice) pairs changed by the pass (change tracking)
+        } h{};
+        VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, sizeof(h), stream));
         L2Window window;
         if (tune && tune->l2_window) {
             // the bytes every union launch gathers from: the table region, or the register slices
             const uint64_t bytes = P.mode == kModeRuns ? (uint64_t)table_rows(P.scheme) * P.n * P.S : P.n * P.S;
             VGA_TRY(window.open(stream, P.mode == kModeRuns ? tab : cur, bytes, g->device));
         }
+        // change tracking: every pass records its changes; a pass after one
+        // that changed little recomputes only the nodes with a changed neighbour
+        uint8_t *chg = P.track ? base + P.off_chg : nullptr;
+        uint32_t *need = P.track ? reinterpret_cast<uint32_t *>(base + P.off_need) : nullptr;
+        uint32_t *ortab = P.track ? reinterpret_cast<uint32_t *>(base + P.off_ortab) : nullptr;
+        uint64_t changed_prev = ~0ull;
         for (t = 1;; t++) {
             VGA_CHECK_CUDA(cudaMemsetAsync(flags, 0, 8, stream));
+            const bool tracked = chg && t >= 2 &&
+                                 (P.track == 2 || (double)changed_prev < kTrackBelow * (double)P.n * P.slices);
+            if (tracked) VGA_TRY(launch_need(P, g, chg, ortab, need, stream, timed ? &timings : nullptr));
+            if (chg) {
+                VGA_CHECK_CUDA(cudaMemsetAsync(chg, 0, P.chg_bytes, stream));
+                VGA_CHECK_CUDA(cudaMemsetAsync(flags + 4, 0, 8, stream));
+            }
             if (t == 1 && keys)
                 VGA_TRY(launch_first_pass(P, g, keys, nxt, 0u, (uint32_t)P.slices, flags, stream,
-                                          timed ? &timings : nullptr));
+                                          timed ? &timings : nullptr, chg));
             else
-                VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, timed ? &timings : nullptr));
+                VGA_TRY(launch_union(P, g, cur, nxt, tab, flags, stream, timed ? &timings : nullptr,
+                                     tracked ? need : nullptr, chg));
+            if (chg) VGA_TRY(launch_count(P, chg, flags, stream));
             VGA_TRY(launch_estimate(P, nxt, t, lc, c_prev, c_cur, sum_d, flags, stream));
             if (t <= max_trace) VGA_TRY(copy_trace(P, nxt, c_cur, t, trace_regs, trace_c, stream));
-            VGA_CHECK_CUDA(cudaMemcpyAsync(hflags, flags, 12, cudaMemcpyDeviceToHost, stream));
+            VGA_CHECK_CUDA(cudaMemcpyAsync(&h, flags, sizeof(h), cudaMemcpyDeviceToHost, stream));
             VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
-            if (hflags[2]) {
+            if (h.f[2]) {
                 set_error("a bounded wait for a TMA copy ran out in pass %d", t);
                 return VGA_ETIMEOUT;
             }
+            changed_prev = h.n_changed;
             std::swap(cur, nxt);
             std::swap(c_prev, c_cur);
-            const bool stop = (conv_mode == 1) ? (hflags[1] == 0) : (hflags[0] == 0);
+            const bool stop = (conv_mode == 1) ? (h.f[1] == 0) : (h.f[0] == 0);
             if (stop || (d > 0 && t >= d)) break;
         }
         hb_finalize_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>((uint32_t)P.n, g->d_comp, sum_d,
