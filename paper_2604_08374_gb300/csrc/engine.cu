@@ -51,13 +51,20 @@ __global__ void batch_init_kernel(JobDev *jobs, const uint64_t *__restrict__ nod
         const JobDev &J = jobs[j];
         const uint32_t v = (uint32_t)(x - node_start[j]);
         init_node(J.regs[0], J.n, J.p, J.S, J.seed, v);
-        if (J.first) reinterpret_cast<uint32_t *>(J.tab)[v] = node_key(v, J.p, J.seed, false);
+        if (J.first) {
+            const uint32_t key = node_key(v, J.p, J.seed, false);
+            if (J.p <= kKey16MaxP)
+                reinterpret_cast<uint16_t *>(J.tab)[v] = KeyFmt<uint16_t>::pack(key);
+            else
+                reinterpret_cast<uint32_t *>(J.tab)[v] = KeyFmt<uint32_t>::pack(key);
+        }
     }
 }
 
 // Pass 1 of the jobs in fjobs[0 .. n) (all of precision p, all fresh) as the
 // scatter of their nodes' keys (first_pass_item), one warp per work item of
 // the concatenated work lists; the jobs' union launch skips them in pass 1.
+template <class K>
 __global__ void __launch_bounds__(kFirstPassWarps * 32) batch_first_pass_kernel(JobDev *jobs,
                                                                                const uint32_t *__restrict__ fjobs,
                                                                                const uint64_t *__restrict__ fstart,
@@ -73,7 +80,7 @@ __global__ void __launch_bounds__(kFirstPassWarps * 32) batch_first_pass_kernel(
         const int k = find_job(fstart, n, x);
         JobDev &J = jobs[fjobs[k]];
         const RunItem it = J.items[x - fstart[k]];
-        first_pass_item<false>(it, J.lk, reinterpret_cast<const uint32_t *>(J.tab), J.n, J.p, J.scheme,
+        first_pass_item<false, K>(it, J.lk, reinterpret_cast<const K *>(J.tab), J.n, J.p, J.scheme,
                                __ffs(J.S) - 1, 0u, (uint32_t)J.slices, J.regs[1], cells, cells + m, lane, &J.changed,
                                error);
     }
@@ -476,8 +483,12 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(batch_first_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kFirstPassWarps * ((1 << kFirstPassMaxP) + 32) * 4);
+        const int most = kFirstPassWarps * ((1 << kFirstPassMaxP) + 32) * 4;
+        attr_err = cudaFuncSetAttribute(batch_first_pass_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        most);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(batch_first_pass_kernel<uint32_t>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     });
     VGA_CHECK_CUDA(attr_err);
     int dev = 0, sms = 1;
@@ -485,14 +496,23 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (const Launch &L : launches) {
         const size_t smem = (size_t)kFirstPassWarps * ((1u << L.p) + 32u) * 4u;
+        const bool k16 = L.p <= kKey16MaxP;
         int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_first_pass_kernel, kFirstPassWarps * 32, smem);
+        if (k16)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_first_pass_kernel<uint16_t>,
+                                                          kFirstPassWarps * 32, smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_first_pass_kernel<uint32_t>,
+                                                          kFirstPassWarps * 32, smem);
         const uint64_t items = fs[L.start_off + L.n];
         const unsigned grid = (unsigned)std::max<uint64_t>(
             1, std::min<uint64_t>((items + kFirstPassWarps - 1) / kFirstPassWarps, (uint64_t)sms * std::max(1, per_sm)));
-        batch_first_pass_kernel<<<grid, kFirstPassWarps * 32, smem, stream>>>(A.jobs, A.fjobs + L.job_off,
-                                                                              A.fstart + L.start_off, L.n, L.p,
-                                                                              A.error);
+        if (k16)
+            batch_first_pass_kernel<uint16_t><<<grid, kFirstPassWarps * 32, smem, stream>>>(
+                A.jobs, A.fjobs + L.job_off, A.fstart + L.start_off, L.n, L.p, A.error);
+        else
+            batch_first_pass_kernel<uint32_t><<<grid, kFirstPassWarps * 32, smem, stream>>>(
+                A.jobs, A.fjobs + L.job_off, A.fstart + L.start_off, L.n, L.p, A.error);
         count_launch();
     }
     VGA_CHECK_CUDA(cudaGetLastError());

@@ -416,35 +416,52 @@ __device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc 
     }
 }
 
+// Keys of the first pass's scatter: node_key repacked as j << KeyFmt<K>::RHO_BITS
+// | rho.  16-bit keys (p <= 10: j < 2^10, rho <= 61 < 2^6) halve the bytes the
+// scatter reads; wider precisions keep the 32-bit form.
+template <class K>
+struct KeyFmt {
+    static constexpr int RHO_BITS = sizeof(K) == 2 ? 6 : 8;
+    static __device__ __forceinline__ K pack(uint32_t key32) {
+        return (K)(((key32 >> 8) << RHO_BITS) | (key32 & 0xffu));
+    }
+    static __device__ __forceinline__ uint32_t j(uint32_t k) { return k >> RHO_BITS; }
+    static __device__ __forceinline__ uint32_t rho(uint32_t k) { return k & ((1u << RHO_BITS) - 1u); }
+};
+constexpr int kKey16MaxP = 10;
+
 // First pass of Eq. hll-union (t = 1) as a scatter.  After the initialisation
 // (Alg. 1) every counter holds one register, the node's key (node_key), so
 // register j of next[v] is the largest rho among the keys of v and its
 // neighbours whose register index is j: no register row needs to be gathered.
 // A warp walks its work item's range lookups; a lookup r = slot * n + i of
 // window width w (runs.cuh: the windows of a run stay inside it) covers the
-// neighbour ids i .. i + w - 1.  The lookups of one width are compacted
-// through `stage` (32 words), so that 32 / w of them share a round of the
-// warp with consecutive lanes on consecutive ids; their keys are read from
-// `keys` and folded into the warp's m shared-memory cells (one u32 per
-// register) by atomicMax.  The cells are then packed into register words and
-// stored for slices [s0, s1) of the slice-major layout (all slices, or a
-// register-range shard's own, its slice s0 first), or merged word by word by
-// atomic max for the chunk of a split hub (atomic_max_word; next[v] holds no
-// register above the result when the pass starts).  *flag is set when a
-// stored register exceeds the node's own counter, and with chg given (change
-// bytes, [slice][N] from slice s0 on) chg[s][v] = 1 for each slice where one does.
-template <bool NIB>
+// neighbour ids i .. i + w - 1.  The lookups of windows up to 4 ids wide and
+// those of wider ones are compacted in turn through `stage` (32 words, the
+// window start with its level in the top bits), so that 8 narrow or 2 wide
+// lookups share a round of the warp, consecutive lanes taking consecutive
+// ids; their keys are read from `keys` and folded into the warp's m
+// shared-memory cells (one u32 per register) by atomicMax.  The cells are then
+// packed into register words and stored for slices [s0, s1) of the slice-major
+// layout (all slices, or a register-range shard's own, its slice s0 first), or
+// merged word by word by atomic max for the chunk of a split hub
+// (atomic_max_word; next[v] holds no register above the result when the pass
+// starts).  *flag is set when a stored register exceeds the node's own
+// counter, and with chg given (change bytes, [slice][N] from slice s0 on)
+// chg[s][v] = 1 for each slice where one does.
+template <bool NIB, class K>
 __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t *__restrict__ lk,
-                                                const uint32_t *__restrict__ keys, uint32_t n, int p, int scheme,
+                                                const K *__restrict__ keys, uint32_t n, int p, int scheme,
                                                 int s_log2, uint32_t s0, uint32_t s1, uint8_t *__restrict__ nxt,
                                                 uint32_t *cells, uint32_t *stage, int lane, uint32_t *flag,
                                                 int *err, uint8_t *chg = nullptr) {
+    using KF = KeyFmt<K>;
     const uint32_t m = 1u << p;
     const uint32_t v = it.v & ~kHubChunk;
     for (uint32_t k = lane; k < m / 4u; k += 32) reinterpret_cast<uint4 *>(cells)[k] = make_uint4(0, 0, 0, 0);
     __syncwarp();
     const uint32_t own = __ldg(keys + v);
-    if (lane == 0) cells[own >> 8] = own & 0xffu;
+    if (lane == 0) cells[KF::j(own)] = KF::rho(own);
     __syncwarp();
     const int rows = table_rows(scheme);
     const uint64_t e = it.b + it.cnt;
@@ -455,26 +472,33 @@ __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t
         if (base + 32 + (uint64_t)lane < e) r_next = __ldcs(lk + base + 32 + lane);
         uint32_t slot = 0;
         for (int s = 1; s < rows; s++) slot += r >= (uint32_t)s * n ? 1u : 0u;
-        const uint32_t i = r - slot * n;
-        for (int s = 0; s < rows; s++) {
-            const uint32_t mask = __ballot_sync(0xffffffffu, valid && slot == (uint32_t)s);
+        const uint32_t level = scheme == 0 ? slot : 2u * slot;
+        const uint32_t packed = (r - slot * n) | (level << 29);  // i < 2^29 (kRunMaxNodes)
+#pragma unroll
+        for (int grp = 0; grp < 2; grp++) {
+            const int G = grp == 0 ? 4 : 16;  // lanes per lookup: windows of 1..4, of 8..16 ids
+            const int per = 32 / G;
+            const uint32_t mask = __ballot_sync(0xffffffffu, valid && ((level <= 2u) == (grp == 0)));
             if (!mask) continue;
-            if ((mask >> lane) & 1u) stage[__popc(mask & ((1u << lane) - 1u))] = i;
+            if ((mask >> lane) & 1u) stage[__popc(mask & ((1u << lane) - 1u))] = packed;
             __syncwarp();
-            const int level = scheme == 0 ? s : 2 * s;
-            const int c = __popc(mask), per = 32 >> level;
-            const int my = lane >> level;
-            const uint32_t off = (uint32_t)lane & ((1u << level) - 1u);
+            const int c = __popc(mask);
+            const int my = lane / G;
+            const uint32_t off = (uint32_t)(lane % G);
             for (int q = 0; q < c; q += 4 * per) {
                 uint32_t key[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const int x = q + u * per + my;
-                    key[u] = x < c ? __ldg(keys + stage[x] + off) : 0u;  // a key is never 0 (rho >= 1)
+                    key[u] = 0u;  // a key is never 0 (rho >= 1)
+                    if (x < c) {
+                        const uint32_t sx = stage[x];
+                        if (off < (1u << (sx >> 29))) key[u] = __ldg(keys + (sx & 0x1fffffffu) + off);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; u++)
-                    if (key[u]) atomicMax(cells + (key[u] >> 8), key[u] & 0xffu);
+                    if (key[u]) atomicMax(cells + KF::j(key[u]), KF::rho(key[u]));
             }
             __syncwarp();
         }
@@ -482,7 +506,7 @@ __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t
     // pack: 32-bit word k holds registers 4k .. 4k+3 (bytes), or 8k .. 8k+7
     // (nibbles, the low nibble first)
     const uint32_t per_word = NIB ? 8u : 4u, words = m / per_word;
-    const uint32_t own_j = own >> 8, own_rho = own & 0xffu;
+    const uint32_t own_j = KF::j(own), own_rho = KF::rho(own);
     const uint32_t S = 1u << s_log2;
     bool changed = false;
     for (uint32_t k = lane; k < words; k += 32) {

@@ -47,23 +47,29 @@ const std::vector<double> &lc_table(int p) {
 
 namespace {
 
-// Alg. 1 initialisation; with `keys` given, each node's key (node_key) for the
-// first pass's scatter as well.
+// Alg. 1 initialisation; with `keys` given, each node's key for the first
+// pass's scatter as well (KeyFmt: 16-bit for p <= kKey16MaxP, else 32-bit).
 __global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, int S, uint64_t seed, int nib,
-                               uint32_t s0, uint32_t s1, uint32_t *__restrict__ keys) {
+                               uint32_t s0, uint32_t s1, void *__restrict__ keys) {
     const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     init_node(regs, n, p, S, seed, (uint32_t)v, nib != 0, s0, s1);
-    if (keys) keys[v] = node_key((uint32_t)v, p, seed, nib != 0);
+    if (keys) {
+        const uint32_t key = node_key((uint32_t)v, p, seed, nib != 0);
+        if (p <= kKey16MaxP)
+            static_cast<uint16_t *>(keys)[v] = KeyFmt<uint16_t>::pack(key);
+        else
+            static_cast<uint32_t *>(keys)[v] = KeyFmt<uint32_t>::pack(key);
+    }
 }
 
 // First pass of Eq. hll-union as a scatter of the nodes' keys (first_pass_item),
 // one warp per work item; all slices in one launch.  Each warp holds m + 32
 // words of shared memory (its register cells, then its lookup stage).
-template <bool NIB>
+template <bool NIB, class K>
 __global__ void __launch_bounds__(128) hb_first_pass_kernel(const RunItem *__restrict__ items, uint64_t n_items,
                                                             const uint32_t *__restrict__ lk,
-                                                            const uint32_t *__restrict__ keys, uint32_t n, int p,
+                                                            const K *__restrict__ keys, uint32_t n, int p,
                                                             int scheme, int s_log2, uint32_t s0, uint32_t s1,
                                                             uint8_t *__restrict__ nxt, uint32_t *__restrict__ flags,
                                                             uint8_t *__restrict__ chg) {
@@ -74,7 +80,7 @@ __global__ void __launch_bounds__(128) hb_first_pass_kernel(const RunItem *__res
     if (warp >= n_items) return;
     const uint32_t m = 1u << p;
     uint32_t *cells = s_cells + (uint64_t)wib * (m + 32u);
-    first_pass_item<NIB>(items[warp], lk, keys, n, p, scheme, s_log2, s0, s1, nxt, cells, cells + m, lane, flags,
+    first_pass_item<NIB, K>(items[warp], lk, keys, n, p, scheme, s_log2, s0, s1, nxt, cells, cells + m, lane, flags,
                          reinterpret_cast<int *>(flags + 2), chg);
 }
 
@@ -639,7 +645,7 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
 
 // First pass of a run (or of a register-range shard holding slices [s0, s1))
 // by the scatter of the nodes' keys; `keys` were written by hb_init_kernel.
-static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *keys, uint8_t *nxt, uint32_t s0,
+static int launch_first_pass(const Plan &P, const vga_graph *g, const void *keys, uint8_t *nxt, uint32_t s0,
                              uint32_t s1, uint32_t *flags, cudaStream_t stream, std::vector<PendingTiming> *timings,
                              uint8_t *chg = nullptr) {
     const size_t smem = (size_t)kFirstPassWarps * (P.m + 32u) * 4u;
@@ -647,10 +653,13 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
         const int most = kFirstPassWarps * ((1 << kFirstPassMaxP) + 32) * 4;
-        attr_err = cudaFuncSetAttribute(hb_first_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        if (attr_err == cudaSuccess)
-            attr_err =
-                cudaFuncSetAttribute(hb_first_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        const void *fns[4] = {reinterpret_cast<const void *>(hb_first_pass_kernel<false, uint16_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_kernel<false, uint32_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_kernel<true, uint16_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_kernel<true, uint32_t>)};
+        for (const void *f : fns)
+            if (attr_err == cudaSuccess)
+                attr_err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     });
     VGA_CHECK_CUDA(attr_err);
     PendingTiming pt{};
@@ -661,17 +670,24 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const uint32_t *
     }
     const unsigned blocks = (unsigned)((P.items.count + kFirstPassWarps - 1) / kFirstPassWarps);
     const int s_log2 = __builtin_ctz((unsigned)P.S);
+    const uint32_t *lk = g->lk[P.scheme].d_lk;
+    const uint32_t n = (uint32_t)P.n;
+    const bool k16 = P.p <= kKey16MaxP;
+#define VGA_FP(NIBV, KT)                                                                                          \
+    hb_first_pass_kernel<NIBV, KT><<<blocks, kFirstPassWarps * 32, smem, stream>>>(                              \
+        P.items.items, P.items.count, lk, static_cast<const KT *>(keys), n, P.p, P.scheme, s_log2, s0, s1, nxt, \
+        flags, chg)
     if (blocks) {
-        if (P.nib)
-            hb_first_pass_kernel<true><<<blocks, kFirstPassWarps * 32, smem, stream>>>(
-                P.items.items, P.items.count, g->lk[P.scheme].d_lk, keys, (uint32_t)P.n, P.p, P.scheme, s_log2, s0,
-                s1, nxt, flags, chg);
-        else
-            hb_first_pass_kernel<false><<<blocks, kFirstPassWarps * 32, smem, stream>>>(
-                P.items.items, P.items.count, g->lk[P.scheme].d_lk, keys, (uint32_t)P.n, P.p, P.scheme, s_log2, s0,
-                s1, nxt, flags, chg);
+        if (P.nib) {
+            if (k16) VGA_FP(true, uint16_t);
+            else VGA_FP(true, uint32_t);
+        } else {
+            if (k16) VGA_FP(false, uint16_t);
+            else VGA_FP(false, uint32_t);
+        }
         count_launch();
     }
+#undef VGA_FP
     VGA_CHECK_CUDA(cudaGetLastError());
     if (timings) {
         VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
@@ -861,7 +877,7 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         // split hubs merge into next[v] by atomic max: it must start below the result
         if (P.items.hubs) VGA_CHECK_CUDA(cudaMemsetAsync(nxt, 0, P.n * P.node_bytes, stream));
         VGA_CHECK_CUDA(cudaMemsetAsync(sum_d, 0, 8 * P.n, stream));
-        uint32_t *keys = P.first_scatter ? reinterpret_cast<uint32_t *>(tab) : nullptr;  // tab is unused in pass 1
+        void *keys = P.first_scatter ? tab : nullptr;  // tab is unused in pass 1
         hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(cur, (uint32_t)P.n, p, P.S, seed, P.nib, 0u,
                                                                           (uint32_t)P.slices, keys);
         count_launch();
@@ -1124,7 +1140,7 @@ int vga_shard_start(vga_shard *s, void *partial_dev, void *stream_ptr) {
         VGA_CHECK_CUDA(cudaMemsetAsync(s->sum_d, 0, 8 * P.n, stream));
         hb_init_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(
             s->cur, (uint32_t)P.n, s->p, P.S, s->seed, P.nib, s->s0, s->s1,
-            P.first_scatter ? reinterpret_cast<uint32_t *>(s->tab) : nullptr);
+            P.first_scatter ? static_cast<void *>(s->tab) : nullptr);
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
@@ -1155,7 +1171,7 @@ int vga_shard_union(vga_shard *s, void *partial_dev, uint32_t *changed, void *st
     if (P.n > 0) {
         VGA_CHECK_CUDA(cudaMemsetAsync(s->flags, 0, 4, stream));
         if (s->t == 0 && P.first_scatter)
-            VGA_TRY(launch_first_pass(P, s->g, reinterpret_cast<const uint32_t *>(s->tab), s->nxt, s->s0, s->s1,
+            VGA_TRY(launch_first_pass(P, s->g, s->tab, s->nxt, s->s0, s->s1,
                                       s->flags, stream, profiling ? &timings : nullptr));
         else
             VGA_TRY(launch_union(P, s->g, s->cur, s->nxt, s->tab, s->flags, stream, profiling ? &timings : nullptr));
