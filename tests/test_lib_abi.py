@@ -83,3 +83,35 @@ def test_encoder_wide_ids(built_lib):
     ref_off, ref_b = oracle.csr_encode(row_ptr, col)
     assert bytes(b) == bytes(ref_b)
     assert oracle.decode_list(b, 0, len(b), 2**32).tolist() == col.tolist()
+
+
+STRUCTS = [("vga_tuning", "VgaTuning"), ("vga_job", "VgaJob"), ("vga_server_config", "VgaServerConfig"),
+           ("vga_server_stats_t", "VgaServerStats"), ("vga_profile", "VgaProfile"), ("vga_tune_entry", "VgaTuneEntry")]
+
+
+def test_ctypes_structs_match_the_header(built_lib, tmp_path):
+    # the binding's ctypes mirrors must have the C structs' size and field
+    # offsets (a C program compiled against the header prints them)
+    vga, _ = built_lib
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "vga_hyperball.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS:
+        cls = getattr(vga, pyname)
+        lines.append(f'    printf("{pyname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{pyname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        pyname, field, value = line.split()
+        cls = getattr(vga, pyname)
+        got = __import__("ctypes").sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), (pyname, field)
+        seen += 1
+    assert seen == sum(len(getattr(vga, p)._fields_) + 1 for _, p in STRUCTS)
