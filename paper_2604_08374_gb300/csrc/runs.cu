@@ -12,10 +12,11 @@
 // result is the same register array, bit for bit.
 //
 // This file turns the LEB128 CSR into the list of lookups of every node, once
-// per graph and table scheme: one warp per node decodes its list with the wide
-// window decoder, finds run boundaries across windows, and emits each
-// completed run's lookups as row indices slot * N + i of a slice's table
-// region, so that the union addresses a row with one multiply-add.
+// per graph and table scheme: one warp per node walks its list 128 bytes at a
+// time, finds the run starts from byte masks (only their varints are
+// assembled), and emits each completed run's lookups as row indices slot * N
+// + i of a slice's table region, so that the union addresses a row with one
+// multiply-add.
 #include <algorithm>
 #include <atomic>
 #include <vector>
@@ -26,40 +27,31 @@ namespace vga {
 namespace {
 
 // One warp per node.  WRITE: write node v's lookups for table scheme `scheme`
-// at lk[lk_off[v] ...]; otherwise store their number in cnt[v] (the scheme
-// chosen for the graph is counted by validation at load instead).
+// at lk[lk_off[v] ...] (SwarRuns, 128 bytes per step) and check that their
+// number is the one counted at validation (*bad = 1 otherwise); without WRITE,
+// store their number in cnt[v] (the scheme chosen for the graph is counted by
+// validation at load instead).
 template <bool WRITE>
 __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes, uint32_t n,
                                    int scheme, const uint64_t *__restrict__ lk_off, uint32_t *__restrict__ lk,
-                                   uint32_t *__restrict__ cnt) {
-    __shared__ uint32_t s_ids[8][128];
+                                   uint32_t *__restrict__ cnt, int *__restrict__ bad) {
+    __shared__ uint32_t s_runs[8][3 * SwarRuns::kRunsCap];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint32_t *ids = s_ids[wib];
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
     const uint32_t v = (uint32_t)warp;
-    uint64_t pos = off[v];
-    const uint64_t end = off[v + 1];
-    uint32_t base = 0;
-    RunTracker rt;
-    rt.scheme = scheme;
-    rt.out = WRITE ? lk_off[v] : 0;
-    while (pos < end) {
-        int advance = 0;
-        uint32_t next = 0;
-        bool unused = false;
-        const int c = decode_window4<uint32_t, false>(bytes, pos, end, base, lane, ids, advance, next, false, 0, 0,
-                                                      unused);
-        if (c == 0) break;  // cannot happen on a validated graph
-        __syncwarp();
-        rt.window<WRITE>(ids, c, lane, n, lk);
-        __syncwarp();
-        base = next;
-        pos += (uint64_t)advance;
+    const uint64_t pos = off[v], end = off[v + 1];
+    SwarRuns r;
+    r.scheme = scheme;
+    r.out = WRITE ? lk_off[v] : 0;
+    for (uint64_t w0 = pos & ~3ull; w0 < end; w0 += 128)
+        r.window<WRITE>(bytes, w0, pos, end, lane, n, lk, s_runs[wib]);
+    r.finish<WRITE>(lane, n, lk);
+    if (lane == 0) {
+        if (WRITE && r.out != lk_off[v + 1]) atomicExch(bad, 1);
+        if (!WRITE) cnt[v] = (uint32_t)r.out;
     }
-    rt.finish<WRITE>(lane, n, lk);
-    if (!WRITE && lane == 0) cnt[v] = (uint32_t)rt.out;
 }
 
 }  // namespace
@@ -110,7 +102,7 @@ int ensure_run_lookups(const vga_graph *g, int scheme, cudaStream_t stream) {
             DeviceBuffer d_cnt;
             VGA_TRY(d_cnt.alloc(4 * (size_t)n));
             run_lookups_kernel<false><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, scheme, nullptr,
-                                                                         nullptr, d_cnt.as<uint32_t>());
+                                                                         nullptr, d_cnt.as<uint32_t>(), nullptr);
             count_launch();
             VGA_CHECK_CUDA(cudaGetLastError());
             VGA_CHECK_CUDA(cudaMemcpyAsync(h_cnt.data(), d_cnt.ptr, 4 * (size_t)n, cudaMemcpyDeviceToHost, stream));
@@ -120,7 +112,9 @@ int ensure_run_lookups(const vga_graph *g, int scheme, cudaStream_t stream) {
         L.total = L.h_off[n];
     }
     const uint64_t total = L.total;
-    DeviceBuffer d_off, d_lk;
+    DeviceBuffer d_off, d_lk, d_bad;
+    VGA_TRY(d_bad.alloc(4));
+    VGA_CHECK_CUDA(cudaMemsetAsync(d_bad.ptr, 0, 4, stream));
     VGA_TRY(d_off.alloc(8 * ((size_t)n + 1)));
     VGA_TRY(d_lk.alloc(4 * ((size_t)total + 4)));  // + one 16-byte group: TMA copies round up to whole groups
     VGA_CHECK_CUDA(cudaMemsetAsync(d_lk.as<uint8_t>() + 4 * total, 0, 16, stream));
@@ -128,11 +122,17 @@ int ensure_run_lookups(const vga_graph *g, int scheme, cudaStream_t stream) {
     if (n) {
         run_lookups_kernel<true><<<blocks, warps * 32, 0, stream>>>(g->d_offsets, g->d_bytes, n, scheme,
                                                                     d_off.as<uint64_t>(), d_lk.as<uint32_t>(),
-                                                                    nullptr);
+                                                                    nullptr, d_bad.as<int>());
         count_launch();
         VGA_CHECK_CUDA(cudaGetLastError());
     }
+    int bad = 0;
+    VGA_CHECK_CUDA(cudaMemcpyAsync(&bad, d_bad.ptr, 4, cudaMemcpyDeviceToHost, stream));
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    if (bad) {
+        set_error("internal: the lookup write pass disagrees with the lookup counts of scheme %d", scheme);
+        return VGA_ECORRUPT;
+    }
     L.d_off = static_cast<uint64_t *>(d_off.release());
     L.d_lk = static_cast<uint32_t *>(d_lk.release());
     L.ready = true;

@@ -1,7 +1,7 @@
-// runs.cuh -- LEB128 window decoding with run tracking for the run-aware
-// union's range lookups (see runs.cu): shared by graph validation, which
-// checks the format and counts every node's lookups in one pass, and the pass
-// that writes them.
+// runs.cuh -- run tracking over LEB128 lists for the run-aware union's range
+// lookups (see runs.cu): the lane-serial window scan of graph validation,
+// which checks the format and counts every node's lookups in one pass, and the
+// byte-mask run extractor of the pass that writes them (SwarRuns).
 #pragma once
 
 #include "vga_common.cuh"
@@ -13,229 +13,228 @@ namespace {
 // the widest kept window not longer than the run (scheme 0: 2^floor(log2 L)
 // up to 16; scheme 1: 1, 4 or 16).  ceil(L / w) windows cover it, the last
 // one ending at the run's end.
-__device__ __forceinline__ void run_window(uint32_t L, int scheme, uint32_t &w, uint32_t &slot) {
+__device__ __forceinline__ void run_window(uint32_t L, int scheme, uint32_t &w, uint32_t &slot, uint32_t &k) {
     if (scheme == 0) {
-        const uint32_t k = L < 16u ? 31u - __clz(L) : 4u;
-        w = 1u << k;
+        k = L < 16u ? 31u - __clz(L) : 4u;
         slot = k;
     } else {
         slot = L < 4u ? 0u : (L < 16u ? 1u : 2u);
-        w = 1u << (2u * slot);
+        k = 2u * slot;
     }
+    w = 1u << k;
+}
+__device__ __forceinline__ void run_window(uint32_t L, int scheme, uint32_t &w, uint32_t &slot) {
+    uint32_t k;
+    run_window(L, scheme, w, slot, k);
 }
 
-// Number of lookups covering the run [a, a + L).
+// Number of lookups covering the run [a, a + L): ceil(L / w), w = 2^k.
 __device__ __forceinline__ uint32_t run_lookup_count(uint32_t L, int scheme) {
-    uint32_t w, slot;
-    run_window(L, scheme, w, slot);
-    return (L + w - 1u) / w;
+    uint32_t w, slot, k;
+    run_window(L, scheme, w, slot, k);
+    return (L + w - 1u) >> k;
 }
 
 // Lookups covering the run [a, a + L) as table row indices slot * n + i.
 __device__ __forceinline__ void run_lookup_write(uint32_t a, uint32_t L, uint32_t n, int scheme, uint32_t *out) {
-    uint32_t w, slot;
-    run_window(L, scheme, w, slot);
-    const uint32_t c = (L + w - 1u) / w;
+    uint32_t w, slot, k;
+    run_window(L, scheme, w, slot, k);
+    const uint32_t c = (L + w - 1u) >> k;
     const uint32_t base = slot * n + a;
     for (uint32_t j = 0; j + 1u < c; j++) out[j] = base + w * j;
     out[c - 1u] = base + L - w;
 }
 
-// Window decoder of the lookup write pass: each lane takes 4 bytes, so a warp
-// decodes 128 bytes per step, and the ids come out in order for RunTracker
-// (one id per lane per 32, so each run's lookups are written by one lane with
-// little divergence; the lane-serial scan_window16 below is faster for
-// validation but not for writing).  The window starts at a varint boundary `pos`; lane L
-// holds window bytes 4L .. 4L+3 (two aligned 32-bit loads per lane shared
-// through a shuffle, then a funnel shift; the byte buffer carries 256 bytes
-// of padding).  Every varint that ends in the window is assembled from at
-// most 5 bytes (its own lane and the one before), the deltas are prefix-
-// summed across the warp, and the ids are written in order to ids[0 ..
-// count).  Returns count; advance = bytes consumed up to the window's last
-// complete varint (0 if none); next_base = its id.  CHECK also tests every
-// rule of the format (varint of at most 5 bytes and 32 bits, no zero delta
-// after a list's first entry, id < n, id != self) and sets fail on any
-// break; list_start says the window begins the node's list.  (Validation
-// uses scan_window16; this decoder serves the write pass on validated
-// graphs.)
-template <class Id, bool CHECK>
-__device__ __forceinline__ int decode_window4(const uint8_t *__restrict__ bytes, uint64_t pos, uint64_t end,
-                                              Id base, int lane, uint32_t *ids, int &advance, Id &next_base,
-                                              bool list_start, uint64_t n, uint64_t self, bool &fail) {
-    const uint64_t a0 = pos & ~3ull;
-    const uint32_t *aw = reinterpret_cast<const uint32_t *>(bytes + a0);
-    const uint32_t w = __ldg(aw + lane);
-    uint32_t wn = __shfl_down_sync(0xffffffffu, w, 1);
-    if (lane == 31) wn = __ldg(aw + 32);
-    const uint32_t word = __funnelshift_r(w, wn, (uint32_t)(pos & 3ull) * 8u);
-    const uint32_t prev_word = __shfl_up_sync(0xffffffffu, word, 1);
-    const uint32_t pw = lane ? prev_word : 0u;  // window bytes 4L-4 .. 4L-1 (none before the window)
-    // terminator bits of this lane's bytes inside [pos, end): bit 7 clear
-    const uint64_t rem64 = end - pos;
-    const int rem = rem64 < 128u ? (int)rem64 : 128;
-    const int mine = min(max(rem - 4 * lane, 0), 4);
-    const uint32_t hb = ~word & 0x80808080u;
-    uint32_t tm = ((hb >> 7) | (hb >> 14) | (hb >> 21) | (hb >> 28)) & ((1u << mine) - 1u);
-    // last terminator before this lane's bytes (window position), -1 if none
-    int pt = tm ? 4 * lane + (31 - __clz(tm)) : -1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pt, o);
-        if (lane >= o) pt = max(pt, t);
-    }
-    const int last_all = __shfl_sync(0xffffffffu, pt, 31);
-    int prev = __shfl_up_sync(0xffffffffu, pt, 1);
-    if (lane == 0) prev = -1;
-    // assemble this lane's varints
-    uint32_t val[4];
-    Id lane_sum = 0;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        val[k] = 0;
-        if ((tm >> k) & 1u) {
-            const int q = 4 * lane + k;  // terminator position
-            const int len = q - prev;    // bytes prev+1 .. q
-            uint64_t v = 0;
-            // the varint's bytes, first (least significant group) lowest, taken from
-            // the previous lane's word and this one; then its 7-bit groups packed
-            const int sb = prev + 1 - 4 * lane + 4;  // first byte within (pw, word): 0 .. 7
-            if (len <= 4) {
-                const uint32_t x = (sb < 4 ? __funnelshift_r(pw, word, 8u * (uint32_t)sb) : word >> (8 * (sb - 4))) &
-                                   (0xFFFFFFFFu >> (32 - 8 * len));
-                v = (x & 0x7Fu) | ((x >> 1) & 0x3F80u) | ((x >> 2) & 0x1FC000u) | ((x >> 3) & 0xFE00000u);
-            } else if (len == 5) {
-                const uint64_t x = ((((uint64_t)word << 32) | pw) >> (8 * sb)) & 0xFFFFFFFFFFull;
-                v = (x & 0x7Full) | ((x >> 1) & (0x7Full << 7)) | ((x >> 2) & (0x7Full << 14)) |
-                    ((x >> 3) & (0x7Full << 21)) | ((x >> 4) & (0x7Full << 28));
-            } else {
-                bad = true;
-            }
-            if (v > 0xFFFFFFFFull) bad = true;
-            val[k] = (uint32_t)v;
-            lane_sum += (Id)(uint32_t)v;
-            prev = q;
-        }
-    }
-    // prefix sums of the deltas and of the varint counts across lanes
-    Id incl = lane_sum;
-    int cnt_incl = __popc(tm);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Id t = __shfl_up_sync(0xffffffffu, incl, o);
-        const int c = __shfl_up_sync(0xffffffffu, cnt_incl, o);
-        if (lane >= o) {
-            incl += t;
-            cnt_incl += c;
-        }
-    }
-    Id id = base + incl - lane_sum;
-    int idx = cnt_incl - __popc(tm);
-    bool f = bad;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if ((tm >> k) & 1u) {
-            id += (Id)val[k];
-            if (CHECK) {
-                if (val[k] == 0u && !(list_start && idx == 0)) f = true;  // duplicate neighbour
-                if ((uint64_t)id >= n || (uint64_t)id == self) f = true;
-            }
-            ids[idx++] = (uint32_t)id;
-        }
-    }
-    if (CHECK) fail = __any_sync(0xffffffffu, f);
-    advance = last_all + 1;
-    next_base = base + __shfl_sync(0xffffffffu, incl, 31);
-    return __shfl_sync(0xffffffffu, cnt_incl, 31);
+// Four flag bits from the top bits of a word's bytes (bit k = bit 7 of byte k).
+__device__ __forceinline__ uint32_t byte_tops(uint32_t w) {
+    return (((w & 0x80808080u) >> 7) * 0x00204081u) >> 21 & 0xFu;
 }
 
-// Runs of consecutive ids across a node's decoded windows.  Per window the
-// warp passes the window's ids in order in ids[0 .. c), c <= 128; lane L looks
-// at ids 4L .. 4L+3.  A run starts at an id that does not follow the one
-// before it; a run is complete once the next start is seen (in this window or
-// a later one).  `out` counts the lookups emitted so far (WRITE: written at
-// lk + out, in order of the runs).
-struct RunTracker {
-    uint32_t run_a = 0, run_len = 0;  // the run still open at the end of the last window
-    uint64_t out = 0;
+// Run extraction for the lookup write pass, 128 bytes of a validated list per
+// warp step, without decoding every varint.  Lane L takes the aligned word at
+// window start + 4 L.  A byte ends a varint when its top bit is clear; a
+// varint continues the current run exactly when it is the single byte 0x01
+// following another varint's last byte (a delta of 1), except the list's first
+// varint, which is an absolute id and always starts a run.  Only the varints
+// that start runs are assembled (from this lane's word and the one before);
+// warp scans of the deltas and of the varint counts give each start its id
+// and its index, the next start in a later lane comes from a suffix minimum,
+// and each lane emits the lookups of the runs that end in this window (lane 0
+// also those of the run carried into it).  State carried across windows, the
+// same in every lane: the id before the window, the open run, the word before
+// the window and whether the list's first varint is still ahead.
+struct SwarRuns {
+    uint32_t id_base = 0;              // id of the last varint before the window (0 before the first)
+    uint32_t run_a = 0, run_len = 0;   // the open run: first id and ids so far (run_len 0: none)
+    uint32_t prev_word = 0;            // the 4 bytes before the window
+    bool first_pending = true;         // the list's first varint not reached yet
+    uint64_t out = 0;                  // lookups emitted so far (WRITE: next index into lk)
+    int scheme = 0;
 
-    int scheme = 0;  // table scheme of the lookups
+    // runs completed in one window: at most 4 per lane and the carried one
+    static constexpr uint32_t kRunsCap = 132;
 
+    // `runs`: this warp's 3 x kRunsCap words of shared memory (WRITE).
     template <bool WRITE>
-    __device__ __forceinline__ void window(const uint32_t *ids, int c, int lane, uint32_t n, uint32_t *lk) {
-        constexpr int kNone = 0x7fffffff;
-        const int j0 = 4 * lane;
-        uint32_t id[4];
-        uint32_t smask = 0;  // run starts among this lane's ids
-        uint32_t prev = (j0 > 0 && j0 <= c) ? ids[j0 - 1] : 0u;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int j = j0 + k;
-            id[k] = 0;
-            if (j < c) {
-                id[k] = ids[j];
-                const bool start = (j == 0) ? !(run_len > 0 && id[k] == run_a + run_len) : (id[k] != prev + 1u);
-                if (start) smask |= 1u << k;
-                prev = id[k];
+    __device__ __forceinline__ void window(const uint8_t *__restrict__ bytes, uint64_t w0, uint64_t pos,
+                                           uint64_t end, int lane, uint32_t n, uint32_t *lk, uint32_t *runs) {
+        constexpr uint32_t kNone = 0xffffffffu;
+        const uint64_t p0 = w0 + 4ull * (uint32_t)lane;
+        // the byte buffer carries 256 bytes of padding past the last list
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(bytes + p0);
+        uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+        if (lane == 0) pw = prev_word;
+        prev_word = __shfl_sync(0xffffffffu, w, 31);
+        // bytes of this lane inside [pos, end)
+        const uint32_t lo = pos > p0 ? (pos - p0 < 4u ? (uint32_t)(pos - p0) : 4u) : 0u;
+        const uint32_t hi = end > p0 ? (end - p0 < 4u ? (uint32_t)(end - p0) : 4u) : 0u;
+        const uint32_t in4 = hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+        const uint32_t top = byte_tops(w), ptop = byte_tops(pw);
+        const uint32_t T = in4 & ~top;                                   // varint ends
+        const uint32_t one = byte_tops(__vcmpeq4(w, 0x01010101u));        // bytes equal to 0x01
+        const uint32_t prevT = ((~top << 1) | (~ptop >> 3 & 1u)) & 0xFu;  // the byte before ends a varint
+        uint32_t firstbit = 0;
+        if (first_pending) {
+            const uint32_t any = __ballot_sync(0xffffffffu, T != 0u);
+            if (any) {
+                first_pending = false;
+                if (lane == __ffs(any) - 1) firstbit = T & (0u - T);
             }
         }
-        const int fs = smask ? j0 + __ffs(smask) - 1 : kNone;
-        const int ls = smask ? j0 + 31 - __clz(smask) : -1;
-        // first start at or after each lane (suffix minimum), the window's last start
-        int m = fs, last = ls;
+        const uint32_t C = T & one & prevT & ~firstbit;  // delta 1: the run goes on
+        const uint32_t S = T & ~C;                       // run starts
+        // values of the starts, from the 8 bytes (pw, w)
+        const uint64_t w8 = ((uint64_t)w << 32) | pw;
+        const uint32_t ends8 = ((~top & 0xFu) << 4) | (~ptop & 0xFu);
+        uint32_t val[4];
+        uint32_t dsum = __popc(C);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            val[k] = 0;
+            if ((S >> k) & 1u) {
+                const int t = 4 + k;
+                const uint32_t before = ends8 & ((1u << t) - 1u);
+                const int sb = before ? 32 - __clz(before) : 0;  // first byte of the varint
+                const int len = min(t - sb + 1, 5);               // at most 5 in a validated list
+                const uint64_t x = (w8 >> (8 * sb)) & (0xFFFFFFFFFFull >> (8 * (5 - len)));
+                val[k] = (uint32_t)((x & 0x7Full) | ((x >> 1) & 0x3F80ull) | ((x >> 2) & 0x1FC000ull) |
+                                    ((x >> 3) & 0xFE00000ull) | ((x >> 4) & 0xF0000000ull));
+                dsum += val[k];
+            }
+        }
+        // scans: deltas (ids) and varint counts
+        uint32_t incl_d = dsum, incl_t = __popc(T);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_down_sync(0xffffffffu, m, o);
-            if (lane + o < 32) m = min(m, t);
-            last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+            const uint32_t a = __shfl_up_sync(0xffffffffu, incl_d, o);
+            const uint32_t b = __shfl_up_sync(0xffffffffu, incl_t, o);
+            if (lane >= o) {
+                incl_d += a;
+                incl_t += b;
+            }
         }
-        const int first = __shfl_sync(0xffffffffu, m, 0);
-        int after = __shfl_down_sync(0xffffffffu, m, 1);  // first start in later lanes
+        const uint32_t vbase = incl_t - __popc(T);  // varints of the window before this lane
+        const uint32_t total_t = __shfl_sync(0xffffffffu, incl_t, 31);
+        // index of this lane's first start, then the first start in later lanes
+        const uint32_t fsv = S ? vbase + __popc(T & ((S & (0u - S)) - 1u)) : kNone;
+        uint32_t m = fsv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_down_sync(0xffffffffu, m, o);
+            if (lane + o < 32) m = min(m, x);
+        }
+        const uint32_t first_sv = __shfl_sync(0xffffffffu, m, 0);
+        uint32_t after = __shfl_down_sync(0xffffffffu, m, 1);
         if (lane == 31) after = kNone;
-        // lookups of this lane's complete runs (and, on lane 0, of the carried run)
-        const bool carried = run_len > 0 && first != kNone;
-        const uint32_t carried_len = carried ? run_len + (uint32_t)first : 0u;
-        uint32_t my = (lane == 0 && carried) ? run_lookup_count(carried_len, scheme) : 0u;
-        uint32_t len[4];
+        // ids and indices of this lane's starts, and the lookups of the runs they end
+        uint32_t sid[4], six[4], nix[4];
+        uint32_t last_id = 0, last_ix = 0;       // this lane's last start
+        uint32_t rid = id_base + incl_d - dsum;  // id of the varint before this lane's first
+        uint32_t my = 0;
+        const bool carried = run_len > 0 && first_sv != kNone;
+        const uint32_t carried_len = carried ? run_len + first_sv : 0u;
+        if (lane == 0 && carried) my += run_lookup_count(carried_len, scheme);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            len[k] = 0;
-            if ((smask >> k) & 1u) {
-                const uint32_t later = smask & ~((2u << k) - 1u);
-                const int next = later ? j0 + __ffs(later) - 1 : after;
-                if (next != kNone) {
-                    len[k] = (uint32_t)(next - (j0 + k));
-                    my += run_lookup_count(len[k], scheme);
-                }
+            sid[k] = six[k] = nix[k] = kNone;
+            if ((C >> k) & 1u) rid += 1u;
+            if ((S >> k) & 1u) {
+                rid += val[k];
+                sid[k] = rid;
+                six[k] = vbase + __popc(T & ((1u << k) - 1u));
+                const uint32_t later = S & ~((2u << k) - 1u);
+                nix[k] = later ? vbase + __popc(T & ((later & (0u - later)) - 1u)) : after;
+                if (nix[k] != kNone) my += run_lookup_count(nix[k] - six[k], scheme);
+                last_id = sid[k];
+                last_ix = six[k];
             }
         }
-        uint32_t incl = my;
+        uint32_t incl_o = my;
+        uint32_t nruns = (lane == 0 && carried) ? 1u : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) nruns += (sid[k] != kNone && nix[k] != kNone) ? 1u : 0u;
+        uint32_t incl_r = nruns;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+            const uint32_t x = __shfl_up_sync(0xffffffffu, incl_o, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl_r, o);
+            if (lane >= o) {
+                incl_o += x;
+                incl_r += y;
+            }
         }
-        if (WRITE) {
-            uint64_t at = out + (incl - my);
+        const uint32_t total_o = __shfl_sync(0xffffffffu, incl_o, 31);
+        if (WRITE && total_o) {
+            // the window's completed runs in order into `runs` (first id, length,
+            // first lookup), then every lane writes lookups o = lane, lane + 32, ...
+            // of the window, finding its run by binary search: consecutive lanes
+            // store consecutive lookups
+            uint32_t slot = incl_r - nruns, at = incl_o - my;
             if (lane == 0 && carried) {
-                run_lookup_write(run_a, carried_len, n, scheme, lk + at);
+                runs[slot] = run_a;
+                runs[kRunsCap + slot] = carried_len;
+                runs[2 * kRunsCap + slot] = at;
                 at += run_lookup_count(carried_len, scheme);
+                slot++;
             }
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                if (len[k]) {
-                    run_lookup_write(id[k], len[k], n, scheme, lk + at);
-                    at += run_lookup_count(len[k], scheme);
+                if (sid[k] != kNone && nix[k] != kNone) {
+                    const uint32_t L = nix[k] - six[k];
+                    runs[slot] = sid[k];
+                    runs[kRunsCap + slot] = L;
+                    runs[2 * kRunsCap + slot] = at;
+                    at += run_lookup_count(L, scheme);
+                    slot++;
                 }
+            __syncwarp();
+            const uint32_t total_r = __shfl_sync(0xffffffffu, incl_r, 31);
+            for (uint32_t o = lane; o < total_o; o += 32) {
+                uint32_t lo_r = 0, span = total_r;  // last run whose first lookup is <= o
+                while (span > 1) {
+                    const uint32_t half = span >> 1;
+                    if (runs[2 * kRunsCap + lo_r + half] <= o) lo_r += half;
+                    span -= half;
+                }
+                const uint32_t a = runs[lo_r], L = runs[kRunsCap + lo_r], j = o - runs[2 * kRunsCap + lo_r];
+                uint32_t w, sl, lw;
+                run_window(L, scheme, w, sl, lw);
+                const uint32_t c = (L + w - 1u) >> lw;
+                lk[out + o] = sl * n + (j + 1u < c ? a + w * j : a + L - w);
+            }
+            __syncwarp();
         }
-        out += __shfl_sync(0xffffffffu, incl, 31);
-        // the window's last start opens a run that may continue
-        if (last >= 0) {
-            run_a = ids[last];
-            run_len = (uint32_t)(c - last);
-        } else {
-            run_len += (uint32_t)c;
+        out += total_o;
+        // the window's last start opens the run carried onward
+        const uint32_t with = __ballot_sync(0xffffffffu, S != 0u);
+        if (with) {
+            const int hl = 31 - __clz(with);
+            run_a = __shfl_sync(0xffffffffu, last_id, hl);
+            run_len = total_t - __shfl_sync(0xffffffffu, last_ix, hl);
+        } else if (run_len > 0) {
+            run_len += total_t;
         }
+        id_base += __shfl_sync(0xffffffffu, incl_d, 31);
     }
 
     // Close the node's last run.
