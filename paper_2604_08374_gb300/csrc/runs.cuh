@@ -252,7 +252,7 @@ struct SwarRuns {
 // every lane).
 struct RunCarry {
     uint32_t run_a = 0, run_len = 0;  // the run still open (run_len 0: none)
-    uint64_t out = 0;                 // lookups emitted so far (WRITE: next index into lk)
+    uint64_t out = 0;                 // lookups counted so far
 };
 
 struct Window16 {
@@ -266,17 +266,17 @@ struct Window16 {
 // walks them in order, assembling the varints that end there (a varint that
 // began in the previous lane gets that lane's trailing bytes by a shuffle).
 // Warp scans give every lane the index and id of its first varint and the
-// first run start after it; each lane then counts (and, WRITE, writes) the
-// lookups of the runs that start among its varints, in run order.  A varint
+// first run start after it; each lane then counts the lookups of the runs
+// that start among its varints, in run order.  A varint
 // is a run start unless its delta is 1 (the id right after the previous one);
 // the first id of the list always starts a run.  base is the id before the
 // window (updated to the last id in it); rc carries the open run.  CHECK
 // tests every rule of the format (varint of at most 5 bytes and 32 bits, no
 // zero delta after the list's first entry, id < n, id != self).
-template <bool CHECK, bool WRITE>
+template <bool CHECK>
 __device__ __forceinline__ Window16 scan_window16(const uint8_t *__restrict__ bytes, uint64_t pos, uint64_t end,
                                                   uint64_t &base, bool list_start, uint32_t n, uint32_t self,
-                                                  int scheme, uint32_t *lk, RunCarry &rc, int lane) {
+                                                  int scheme, RunCarry &rc, int lane) {
     constexpr int kNone = 0x7fffffff;
     Window16 W;
     const uint64_t A = pos & ~15ull;
@@ -415,31 +415,6 @@ __device__ __forceinline__ Window16 scan_window16(const uint8_t *__restrict__ by
         const uint32_t t = __shfl_up_sync(0xffffffffu, my_incl, o);
         if (lane >= o) my_incl += t;
     }
-    if (WRITE) {
-        uint64_t at = rc.out + (my_incl - my);
-        if (lane == 0 && carried) {
-            run_lookup_write(rc.run_a, rc.run_len + (uint32_t)first, n, scheme, lk + at);
-            at += run_lookup_count(rc.run_len + (uint32_t)first, scheme);
-        }
-        uint64_t idw = id0;
-        int ix = idx0, px = -1;
-        uint32_t pid = 0;
-#pragma unroll
-        for (int i = 0; i < 16; i++)
-            if ((tm >> i) & 1u) {
-                idw += i == first_i ? val_first : val_at[i];
-                if ((smask >> i) & 1u) {
-                    if (px >= 0) {
-                        run_lookup_write(pid, (uint32_t)(ix - px), n, scheme, lk + at);
-                        at += run_lookup_count((uint32_t)(ix - px), scheme);
-                    }
-                    px = ix;
-                    pid = (uint32_t)idw;
-                }
-                ix++;
-            }
-        if (px >= 0 && after != kNone) run_lookup_write(pid, (uint32_t)(after - px), n, scheme, lk + at);
-    }
     rc.out += __shfl_sync(0xffffffffu, my_incl, 31);
     // 4. the window's last start opens a run that may continue
     if (last >= 0) {
@@ -457,10 +432,8 @@ __device__ __forceinline__ Window16 scan_window16(const uint8_t *__restrict__ by
 }
 
 // Close a node's last run (after its last window).
-template <bool WRITE>
-__device__ __forceinline__ void finish_runs(RunCarry &rc, int lane, uint32_t n, int scheme, uint32_t *lk) {
+__device__ __forceinline__ void finish_runs(RunCarry &rc, int scheme) {
     if (rc.run_len > 0) {
-        if (WRITE && lane == 0) run_lookup_write(rc.run_a, rc.run_len, n, scheme, lk + rc.out);
         rc.out += run_lookup_count(rc.run_len, scheme);
         rc.run_len = 0;
     }

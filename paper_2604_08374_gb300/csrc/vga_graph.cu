@@ -40,7 +40,7 @@ __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t 
     bool ok = true;
     RunCarry rc;
     while (pos < end) {
-        const Window16 W = scan_window16<true, false>(bytes, pos, end, base, cnt == 0, n, v, scheme, nullptr, rc, lane);
+        const Window16 W = scan_window16<true>(bytes, pos, end, base, cnt == 0, n, v, scheme, rc, lane);
         if (W.count == 0 || W.fail) {  // a varint runs past the node's range, or a rule is broken
             ok = false;
             break;
@@ -48,7 +48,7 @@ __global__ void validate_kernel(const uint64_t *__restrict__ off, const uint8_t 
         cnt += (uint32_t)W.count;
         pos += W.advance;
     }
-    finish_runs<false>(rc, lane, n, scheme, nullptr);
+    finish_runs(rc, scheme);
     if (lane == 0) {
         degree[v] = ok ? cnt : 0;
         lk_count[v] = ok ? (uint32_t)rc.out : 0u;
