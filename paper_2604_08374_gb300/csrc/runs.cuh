@@ -103,34 +103,35 @@ struct SwarRuns {
         }
         const uint32_t C = T & one & prevT & ~firstbit;  // delta 1: the run goes on
         const uint32_t S = T & ~C;                       // run starts
-        // values of the starts, from the 8 bytes (pw, w)
+        // values of the starts, from the 8 bytes (pw, w); the loops below walk
+        // only the set bits of S (most lanes hold none or one start)
         const uint64_t w8 = ((uint64_t)w << 32) | pw;
         const uint32_t ends8 = ((~top & 0xFu) << 4) | (~ptop & 0xFu);
-        uint32_t val[4];
+        auto start_value = [&](int k) -> uint32_t {
+            const int t = 4 + k;
+            const uint32_t before = ends8 & ((1u << t) - 1u);
+            const int sb = before ? 32 - __clz(before) : 0;  // first byte of the varint
+            const int len = min(t - sb + 1, 5);               // at most 5 in a validated list
+            const uint64_t x = (w8 >> (8 * sb)) & (0xFFFFFFFFFFull >> (8 * (5 - len)));
+            return (uint32_t)((x & 0x7Full) | ((x >> 1) & 0x3F80ull) | ((x >> 2) & 0x1FC000ull) |
+                              ((x >> 3) & 0xFE00000ull) | ((x >> 4) & 0xF0000000ull));
+        };
         uint32_t dsum = __popc(C);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            val[k] = 0;
-            if ((S >> k) & 1u) {
-                const int t = 4 + k;
-                const uint32_t before = ends8 & ((1u << t) - 1u);
-                const int sb = before ? 32 - __clz(before) : 0;  // first byte of the varint
-                const int len = min(t - sb + 1, 5);               // at most 5 in a validated list
-                const uint64_t x = (w8 >> (8 * sb)) & (0xFFFFFFFFFFull >> (8 * (5 - len)));
-                val[k] = (uint32_t)((x & 0x7Full) | ((x >> 1) & 0x3F80ull) | ((x >> 2) & 0x1FC000ull) |
-                                    ((x >> 3) & 0xFE00000ull) | ((x >> 4) & 0xF0000000ull));
-                dsum += val[k];
-            }
-        }
-        // scans: deltas (ids) and varint counts
-        uint32_t incl_d = dsum, incl_t = __popc(T);
+        for (uint32_t ms = S; ms; ms &= ms - 1u) dsum += start_value(__ffs(ms) - 1);
+        // scans: deltas (ids), varint counts, and run entries (this lane's
+        // starts, plus the carried run on lane 0)
+        const bool has_carry = run_len > 0;  // a run is open (it may stay open)
+        const uint32_t nent = __popc(S) + ((lane == 0 && has_carry) ? 1u : 0u);
+        uint32_t incl_d = dsum, incl_t = __popc(T), incl_e = nent;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t a = __shfl_up_sync(0xffffffffu, incl_d, o);
             const uint32_t b = __shfl_up_sync(0xffffffffu, incl_t, o);
+            const uint32_t c = __shfl_up_sync(0xffffffffu, incl_e, o);
             if (lane >= o) {
                 incl_d += a;
                 incl_t += b;
+                incl_e += c;
             }
         }
         const uint32_t vbase = incl_t - __popc(T);  // varints of the window before this lane
@@ -146,71 +147,70 @@ struct SwarRuns {
         const uint32_t first_sv = __shfl_sync(0xffffffffu, m, 0);
         uint32_t after = __shfl_down_sync(0xffffffffu, m, 1);
         if (lane == 31) after = kNone;
-        // ids and indices of this lane's starts, and the lookups of the runs they end
-        uint32_t sid[4], six[4], nix[4];
-        uint32_t last_id = 0, last_ix = 0;       // this lane's last start
-        uint32_t rid = id_base + incl_d - dsum;  // id of the varint before this lane's first
-        uint32_t my = 0;
-        const bool carried = run_len > 0 && first_sv != kNone;
+        // run entries in window order into `runs` (first id, length, then its
+        // lookup count; the window's last start stays open: no lookups yet)
+        const bool carried = has_carry && first_sv != kNone;
         const uint32_t carried_len = carried ? run_len + first_sv : 0u;
-        if (lane == 0 && carried) my += run_lookup_count(carried_len, scheme);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            sid[k] = six[k] = nix[k] = kNone;
-            if ((C >> k) & 1u) rid += 1u;
-            if ((S >> k) & 1u) {
-                rid += val[k];
-                sid[k] = rid;
-                six[k] = vbase + __popc(T & ((1u << k) - 1u));
-                const uint32_t later = S & ~((2u << k) - 1u);
-                nix[k] = later ? vbase + __popc(T & ((later & (0u - later)) - 1u)) : after;
-                if (nix[k] != kNone) my += run_lookup_count(nix[k] - six[k], scheme);
-                last_id = sid[k];
-                last_ix = six[k];
+        uint32_t slot = incl_e - nent;
+        uint32_t my = 0;
+        uint32_t last_id = 0, last_ix = 0;  // this lane's last start
+        if (lane == 0 && has_carry) {
+            const uint32_t c = carried ? run_lookup_count(carried_len, scheme) : 0u;
+            if (WRITE) {
+                runs[slot] = run_a;
+                runs[kRunsCap + slot] = carried_len;
+                runs[2 * kRunsCap + slot] = c;
+            }
+            my += c;
+            slot++;
+        }
+        {
+            uint32_t rid = id_base + incl_d - dsum;  // id of the varint before this lane's first
+            uint32_t cbits = C;
+            for (uint32_t ms = S; ms; ms &= ms - 1u) {
+                const int k = __ffs(ms) - 1;
+                const uint32_t below = (1u << k) - 1u;
+                rid += __popc(cbits & below) + start_value(k);
+                cbits &= ~((2u << k) - 1u);
+                const uint32_t ix = vbase + __popc(T & below);
+                const uint32_t later = ms & ~((2u << k) - 1u);
+                const uint32_t nx = later ? vbase + __popc(T & ((later & (0u - later)) - 1u)) : after;
+                const uint32_t c = nx != kNone ? run_lookup_count(nx - ix, scheme) : 0u;
+                if (WRITE) {
+                    runs[slot] = rid;
+                    runs[kRunsCap + slot] = nx != kNone ? nx - ix : 0u;
+                    runs[2 * kRunsCap + slot] = c;
+                }
+                my += c;
+                slot++;
+                last_id = rid;
+                last_ix = ix;
             }
         }
         uint32_t incl_o = my;
-        uint32_t nruns = (lane == 0 && carried) ? 1u : 0u;
-#pragma unroll
-        for (int k = 0; k < 4; k++) nruns += (sid[k] != kNone && nix[k] != kNone) ? 1u : 0u;
-        uint32_t incl_r = nruns;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(0xffffffffu, incl_o, o);
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl_r, o);
-            if (lane >= o) {
-                incl_o += x;
-                incl_r += y;
-            }
+            if (lane >= o) incl_o += x;
         }
         const uint32_t total_o = __shfl_sync(0xffffffffu, incl_o, 31);
         if (WRITE && total_o) {
-            // the window's completed runs in order into `runs` (first id, length,
-            // first lookup), then every lane writes lookups o = lane, lane + 32, ...
-            // of the window, finding its run by binary search: consecutive lanes
-            // store consecutive lookups
-            uint32_t slot = incl_r - nruns, at = incl_o - my;
-            if (lane == 0 && carried) {
-                runs[slot] = run_a;
-                runs[kRunsCap + slot] = carried_len;
-                runs[2 * kRunsCap + slot] = at;
-                at += run_lookup_count(carried_len, scheme);
-                slot++;
+            // each entry's lookup count becomes its first lookup, then every lane
+            // writes lookups o = lane, lane + 32, ... of the window, finding its
+            // run by binary search (the last entry whose first lookup is <= o: an
+            // entry without lookups shares its offset with the next one, or is
+            // the window's last, past every o): consecutive lanes store
+            // consecutive lookups
+            uint32_t at = incl_o - my;
+            for (uint32_t e = incl_e - nent; e < incl_e; e++) {
+                const uint32_t c = runs[2 * kRunsCap + e];
+                runs[2 * kRunsCap + e] = at;
+                at += c;
             }
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (sid[k] != kNone && nix[k] != kNone) {
-                    const uint32_t L = nix[k] - six[k];
-                    runs[slot] = sid[k];
-                    runs[kRunsCap + slot] = L;
-                    runs[2 * kRunsCap + slot] = at;
-                    at += run_lookup_count(L, scheme);
-                    slot++;
-                }
             __syncwarp();
-            const uint32_t total_r = __shfl_sync(0xffffffffu, incl_r, 31);
+            const uint32_t total_e = __shfl_sync(0xffffffffu, incl_e, 31);
             for (uint32_t o = lane; o < total_o; o += 32) {
-                uint32_t lo_r = 0, span = total_r;  // last run whose first lookup is <= o
+                uint32_t lo_r = 0, span = total_e;
                 while (span > 1) {
                     const uint32_t half = span >> 1;
                     if (runs[2 * kRunsCap + lo_r + half] <= o) lo_r += half;
