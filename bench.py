@@ -82,7 +82,8 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=150, help="requests per offered load")
     ap.add_argument("--serve-pool", type=int, default=64)
-    ap.add_argument("--lane-priority", type=int, default=0, help="server: 1 favours the solo lane, -1 the batched")
+    ap.add_argument("--lane-priority", type=int, default=0,
+                    help="server: 1 favours the solo lane, -1 the batched")
     ap.add_argument("--solo-nodes", type=int, default=0, help="server: solo-lane threshold (0 = library default)")
     ap.add_argument("--batched-share", type=int, default=0,
                     help="server: percent of the batched lane's CTAs kept while a solo analysis runs (0 = all)")

@@ -371,7 +371,8 @@ typedef struct vga_server_config {
     int max_batch;              /* requests advanced together in the batched lane (0: 256) */
     int solo_nodes;             /* graphs above this many nodes use the solo lane (0: 32768) */
     int lane_priority;          /* 0: lanes equal; 1: solo lane's stream gets the higher
-                                   priority; -1: batched lane's does                          */
+                                   priority; -1: batched lane's does (other values:
+                                   VGA_EINVAL)                                                */
     int batched_share;          /* percent of the batched lane's union CTAs kept while a
                                    solo-lane analysis runs, leaving the other SMs to it
                                    (0 or 100: no limit)                                       */

@@ -304,6 +304,10 @@ int vga_server_create(const vga_server_config *cfg, vga_server **out) {
     if (S->cfg.hbm_budget_bytes == 0) S->cfg.hbm_budget_bytes = 150ull << 30;
     if (S->cfg.max_batch <= 0) S->cfg.max_batch = 256;
     if (S->cfg.solo_nodes == 0) S->cfg.solo_nodes = 32768;
+    if (S->cfg.lane_priority < -1 || S->cfg.lane_priority > 1) {
+        set_error("vga_server_create: lane_priority = %d is outside -1..1", S->cfg.lane_priority);
+        return VGA_EINVAL;
+    }
     if (S->cfg.batched_share < 0 || S->cfg.batched_share > 100) {
         set_error("vga_server_create: batched_share = %d is outside 0..100", S->cfg.batched_share);
         return VGA_EINVAL;

@@ -69,10 +69,11 @@ def _check(vga, reqs, results):
         assert out["latency_s"] >= out["queued_s"] >= 0
 
 
-@pytest.mark.parametrize("solo_nodes", [3000, 1 << 30])
-def test_mixed_requests_match_solo_runs(vga, pool, solo_nodes):
+@pytest.mark.parametrize("solo_nodes,lane_priority", [(3000, 0), (1 << 30, 0), (3000, 1), (3000, -1)])
+def test_mixed_requests_match_solo_runs(vga, pool, solo_nodes, lane_priority):
     reqs = _requests(pool, 40, seed=solo_nodes % 97)
-    with vga.Server(hbm_budget_bytes=8 << 30, max_batch=16, solo_nodes=solo_nodes) as srv:
+    with vga.Server(hbm_budget_bytes=8 << 30, max_batch=16, solo_nodes=solo_nodes,
+                    lane_priority=lane_priority) as srv:
         ids = [None] * len(reqs)
 
         def client(lo, hi, delay):
@@ -125,3 +126,10 @@ def test_server_errors(vga, pool):
         ref = oracle.hyperball(off, b, 4, 0)
         assert out["iterations"] == ref["iterations"]
         assert np.array_equal(out["mean_depth"], ref["mean_depth"])
+
+
+def test_server_rejects_bad_lane_settings(vga):
+    for kw in (dict(lane_priority=2), dict(lane_priority=-2), dict(batched_share=101)):
+        with pytest.raises(vga.VgaError) as e:
+            vga.Server(hbm_budget_bytes=1 << 20, **kw)
+        assert e.value.status == vga.VGA_EINVAL
