@@ -172,12 +172,14 @@ int vga_visibility_count(int W, int H, const uint8_t *obst, uint32_t *n_nodes);
 typedef struct vga_tuning {
     int slice_bytes;     /* registers per union slice: power of two in [16, min(m, 1024)] */
     int warps_per_cta;   /* union kernel CTA size in warps: 1..16 (0: 4 in mode 2, 8 in 1) */
-    int l2_budget_mb;    /* L2 share the auto slice width aims at (default: 60 % of L2)   */
+    int l2_budget_mb;    /* L2 share the auto slice width aims at (default: 3/4 of the L2
+                            in mode 2, 60 % in mode 1)                                    */
     int union_mode;      /* 0 auto (= 2), 1 one gather per neighbour, 2 per run of
                             consecutive ids through a sparse table of range maxima; both
                             give the same registers bit for bit.  Mode 2 builds, on a
-                            graph's first use, a lookup list held by the graph (~4 bytes
-                            per run, about 0.65 byte per edge on city graphs).            */
+                            graph's first use, a lookup list held by the graph (4 bytes a
+                            lookup, one or a few lookups a run: about 0.66 byte per edge
+                            on city graphs with the 5-row table, 0.83 with the 3-row one). */
     int register_bits;   /* 0 or 8: uint8 registers; 4: the paper's packed format (Sec. 3.3,
                             two registers per byte, rho clamped to 15, p >= 5).  4-bit
                             runs are not bit-comparable with 8-bit ones wherever a rho
