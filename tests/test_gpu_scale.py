@@ -109,3 +109,31 @@ def test_city_config_sampled(vga):
     n, T = _sampled_checks(vga, workloads.city(2), p=10, d=3, n_sample=24, min_edges=4_000_000_000,
                            max_edges=5_000_000_000)
     assert abs(n - 236_000) / 236_000 < 0.005
+
+
+@pytest.mark.slow
+def test_city_variants_agree(vga):
+    # At full size, in the benchmark's launch configuration, every exact variant
+    # of the run-aware path gives the same result bit for bit: pass 1 as a
+    # scatter or as a union, change tracking automatic (the fifth pass
+    # tracked), off, or forced in every pass; at d = 3 and unlimited depth.
+    torch = pytest.importorskip("torch")
+    g = vga.vga_visibility_build(workloads.city(2))
+    try:
+        n = g.n_nodes
+        for d in (3, 0):
+            outs = []
+            for first, track in ((0, 0), (1, 1), (2, 2)):
+                md = torch.empty(n, dtype=torch.float64, device="cuda")
+                ball = torch.empty_like(md)
+                it = vga.hyperball_run_dev(g, 10, d, 0, md, ball, union_mode=2, first_pass=first,
+                                           track_changes=track)
+                outs.append((it, md.cpu().numpy(), ball.cpu().numpy()))
+            it0, md0, ball0 = outs[0]
+            assert it0 == (3 if d == 3 else 5)
+            for it, md, ball in outs[1:]:
+                assert it == it0
+                assert np.array_equal(md, md0, equal_nan=True)
+                assert np.array_equal(ball, ball0)
+    finally:
+        g.free()
