@@ -198,14 +198,15 @@ typedef struct vga_tuning {
                             policy window on the stream, with the process's persisting L2
                             set-aside raised to cover it; both are put back afterwards.
                             0: off (default; the lookup stream is evict-first anyway)      */
-    int first_pass;      /* mode 2: how pass 1 of Eq. hll-union is computed.  Every counter
-                            then holds only its own node, so register j of the result is
-                            the largest rho among the node's and its neighbours' hashes with
+    int first_pass;      /* how pass 1 of Eq. hll-union is computed.  Every counter then
+                            holds only its own node, so register j of the result is the
+                            largest rho among the node's and its neighbours' hashes with
                             index j.  2: that scatter, one launch for all slices (each warp
-                            folds the hashes of its node's neighbour runs into m cells of
-                            shared memory; p <= 13); 1: the union kernel, like every later
-                            pass; 0: automatic (2 wherever allowed).  Same registers bit
-                            for bit.                                                       */
+                            folds the hashes of its node's neighbours, found through the
+                            range lookups in mode 2 or by decoding the CSR in mode 1, into
+                            m cells of shared memory; p <= 13); 1: the union kernel, like
+                            every later pass; 0: automatic (2 wherever allowed).  Same
+                            registers bit for bit.                                         */
     int track_changes;   /* mode 2, at most 32 slices: change tracking.  Each pass records
                             which (node, slice) pairs changed; a node needs the next pass in
                             a slice only if one of its neighbours changed there (otherwise

@@ -430,6 +430,62 @@ struct KeyFmt {
 };
 constexpr int kKey16MaxP = 10;
 
+// Pack the scatter's register cells into register words and store them for
+// slices [s0, s1) of node v (by word-wise atomic max for a split hub's chunk:
+// next[v] holds no register above the result when the pass starts); *flag is
+// set when a stored register exceeds the node's own counter (key `own`), and
+// with chg given chg[s][v] = 1 for each slice where one does.
+template <bool NIB, class K>
+__device__ __forceinline__ void fp_store(uint32_t own, const uint32_t *cells, uint32_t m, uint32_t v, uint32_t n,
+                                         int s_log2, uint32_t s0, uint32_t s1, bool hub, uint8_t *__restrict__ nxt,
+                                         int lane, uint32_t *flag, int *err, uint8_t *chg) {
+    using KF = KeyFmt<K>;
+    // pack: 32-bit word k holds registers 4k .. 4k+3 (bytes), or 8k .. 8k+7
+    // (nibbles, the low nibble first)
+    const uint32_t per_word = NIB ? 8u : 4u, words = m / per_word;
+    const uint32_t own_j = KF::j(own), own_rho = KF::rho(own);
+    const uint32_t S = 1u << s_log2;
+    bool changed = false;
+    for (uint32_t k = lane; k < words; k += 32) {
+        uint32_t w;
+        if (NIB) {
+            const uint4 a = reinterpret_cast<const uint4 *>(cells)[2 * k];
+            const uint4 b = reinterpret_cast<const uint4 *>(cells)[2 * k + 1];
+            w = a.x | a.y << 4 | a.z << 8 | a.w << 12 | b.x << 16 | b.y << 20 | b.z << 24 | b.w << 28;
+        } else {
+            const uint4 a = reinterpret_cast<const uint4 *>(cells)[k];
+            w = a.x | a.y << 8 | a.z << 16 | a.w << 24;
+        }
+        const uint32_t byte = 4u * k, sl = byte >> s_log2;
+        if (sl < s0 || sl >= s1) continue;
+        const uint32_t mine = own_j / per_word == k ? own_rho << ((32u / per_word) * (own_j % per_word)) : 0u;
+        changed |= w != mine;
+        if (chg && w != mine) chg[(uint64_t)(sl - s0) * n + v] = 1u;  // lanes of one slice store the same byte
+        uint32_t *dst =
+            reinterpret_cast<uint32_t *>(nxt + (((uint64_t)(sl - s0) * n + v) << s_log2) + (byte & (S - 1u)));
+        if (hub)
+            atomic_max_word<NIB>(dst, w, err);
+        else
+            *dst = w;
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) {
+        if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
+    }
+}
+
+// Zero the warp's m register cells and put the node's own key in; returns it.
+template <class K>
+__device__ __forceinline__ uint32_t fp_init(uint32_t *cells, uint32_t m, const K *__restrict__ keys, uint32_t v,
+                                            int lane) {
+    using KF = KeyFmt<K>;
+    for (uint32_t k = lane; k < m / 4u; k += 32) reinterpret_cast<uint4 *>(cells)[k] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    const uint32_t own = __ldg(keys + v);
+    if (lane == 0) cells[KF::j(own)] = KF::rho(own);
+    __syncwarp();
+    return own;
+}
+
 // First pass of Eq. hll-union (t = 1) as a scatter.  After the initialisation
 // (Alg. 1) every counter holds one register, the node's key (node_key), so
 // register j of next[v] is the largest rho among the keys of v and its
@@ -458,11 +514,7 @@ __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t
     using KF = KeyFmt<K>;
     const uint32_t m = 1u << p;
     const uint32_t v = it.v & ~kHubChunk;
-    for (uint32_t k = lane; k < m / 4u; k += 32) reinterpret_cast<uint4 *>(cells)[k] = make_uint4(0, 0, 0, 0);
-    __syncwarp();
-    const uint32_t own = __ldg(keys + v);
-    if (lane == 0) cells[KF::j(own)] = KF::rho(own);
-    __syncwarp();
+    const uint32_t own = fp_init<K>(cells, m, keys, v, lane);
     const int rows = table_rows(scheme);
     const uint64_t e = it.b + it.cnt;
     uint32_t r_next = (it.b + (uint64_t)lane < e) ? __ldcs(lk + it.b + lane) : 0u;
@@ -503,37 +555,36 @@ __device__ __forceinline__ void first_pass_item(const RunItem it, const uint32_t
             __syncwarp();
         }
     }
-    // pack: 32-bit word k holds registers 4k .. 4k+3 (bytes), or 8k .. 8k+7
-    // (nibbles, the low nibble first)
-    const uint32_t per_word = NIB ? 8u : 4u, words = m / per_word;
-    const uint32_t own_j = KF::j(own), own_rho = KF::rho(own);
-    const uint32_t S = 1u << s_log2;
-    bool changed = false;
-    for (uint32_t k = lane; k < words; k += 32) {
-        uint32_t w;
-        if (NIB) {
-            const uint4 a = reinterpret_cast<const uint4 *>(cells)[2 * k];
-            const uint4 b = reinterpret_cast<const uint4 *>(cells)[2 * k + 1];
-            w = a.x | a.y << 4 | a.z << 8 | a.w << 12 | b.x << 16 | b.y << 20 | b.z << 24 | b.w << 28;
-        } else {
-            const uint4 a = reinterpret_cast<const uint4 *>(cells)[k];
-            w = a.x | a.y << 8 | a.z << 16 | a.w << 24;
+    fp_store<NIB, K>(own, cells, m, v, n, s_log2, s0, s1, (it.v & kHubChunk) != 0, nxt, lane, flag, err, chg);
+}
+
+// First pass as a scatter for the per-neighbour variant, which has no range
+// lookups: the warp decodes node v's list 32 bytes at a time (decode_window;
+// ids of a run come out on consecutive lanes) and folds the keys of the
+// decoded ids into its register cells, then stores like first_pass_item.
+template <bool NIB, class K>
+__device__ __forceinline__ void first_pass_csr(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes,
+                                               const K *__restrict__ keys, uint32_t v, uint32_t n, int p, int s_log2,
+                                               uint32_t s0, uint32_t s1, uint8_t *__restrict__ nxt, uint32_t *cells,
+                                               int lane, uint32_t *flag, int *err, uint8_t *chg = nullptr) {
+    using KF = KeyFmt<K>;
+    const uint32_t m = 1u << p;
+    const uint32_t own = fp_init<K>(cells, m, keys, v, lane);
+    uint64_t pos = off[v];
+    const uint64_t end = off[v + 1];
+    uint32_t base = 0;
+    while (pos < end) {
+        const WindowDecode<uint32_t> r = decode_window<uint32_t>(bytes, pos, end, base, lane);
+        if (r.term_mask == 0) break;  // cannot happen on a validated graph; guarantees progress
+        if ((r.term_mask >> lane) & 1u) {
+            const uint32_t key = __ldg(keys + r.id);
+            atomicMax(cells + KF::j(key), KF::rho(key));
         }
-        const uint32_t byte = 4u * k, sl = byte >> s_log2;
-        if (sl < s0 || sl >= s1) continue;
-        const uint32_t mine = own_j / per_word == k ? own_rho << ((32u / per_word) * (own_j % per_word)) : 0u;
-        changed |= w != mine;
-        if (chg && w != mine) chg[(uint64_t)(sl - s0) * n + v] = 1u;  // lanes of one slice store the same byte
-        uint32_t *dst =
-            reinterpret_cast<uint32_t *>(nxt + (((uint64_t)(sl - s0) * n + v) << s_log2) + (byte & (S - 1u)));
-        if (it.v & kHubChunk)
-            atomic_max_word<NIB>(dst, w, err);
-        else
-            *dst = w;
+        base = r.next_base;
+        pos += (uint64_t)r.advance;
     }
-    if (__any_sync(0xffffffffu, changed) && lane == 0) {
-        if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
-    }
+    __syncwarp();
+    fp_store<NIB, K>(own, cells, m, v, n, s_log2, s0, s1, false, nxt, lane, flag, err, chg);
 }
 
 // A work item whose node has no neighbour that changed in this slice during

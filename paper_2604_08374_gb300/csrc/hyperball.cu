@@ -63,6 +63,24 @@ __global__ void hb_init_kernel(uint8_t *__restrict__ regs, uint32_t n, int p, in
     }
 }
 
+// First pass of the per-neighbour variant as a scatter (first_pass_csr), one
+// warp per node; each warp holds m words of shared memory (its register cells).
+template <bool NIB, class K>
+__global__ void __launch_bounds__(128) hb_first_pass_csr_kernel(const uint64_t *__restrict__ off,
+                                                                const uint8_t *__restrict__ bytes,
+                                                                const K *__restrict__ keys, uint32_t n, int p,
+                                                                int s_log2, uint8_t *__restrict__ nxt,
+                                                                uint32_t *__restrict__ flags) {
+    extern __shared__ __align__(16) uint32_t s_cells[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= n) return;
+    const uint32_t m = 1u << p;
+    first_pass_csr<NIB, K>(off, bytes, keys, (uint32_t)warp, n, p, s_log2, 0u, 0xffffffffu, nxt,
+                           s_cells + (uint64_t)wib * m, lane, flags, reinterpret_cast<int *>(flags + 2));
+}
+
 // First pass of Eq. hll-union as a scatter of the nodes' keys (first_pass_item),
 // one warp per work item; all slices in one launch.  Each warp holds m + 32
 // words of shared memory (its register cells, then its lookup stage).
@@ -357,7 +375,7 @@ struct Plan {
     uint32_t hub_req = 0;  // runs mode: requested hub threshold (0 = automatic)
     uint32_t hub = 0;      // runs mode: nodes with more lookups than this are split across warps
     RunItemList items;     // runs mode: the union's work list for `hub`
-    bool first_scatter = false;  // runs mode: pass 1 by hb_first_pass_kernel (the keys live in the table region)
+    bool first_scatter = false;  // pass 1 by the scatter of the nodes' keys (kept at off_tab)
     int track = 0;               // runs mode, slices <= 32: change tracking (0 off, 1 automatic, 2 every pass)
     uint64_t n = 0;
     // workspace layout (byte offsets, 256-aligned)
@@ -467,9 +485,9 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         set_error("first_pass = %d must be 0 (automatic), 1 (gather) or 2 (scatter)", first);
         return VGA_EINVAL;
     }
-    const bool scatter_ok = P->mode == kModeRuns && p <= kFirstPassMaxP;
+    const bool scatter_ok = p <= kFirstPassMaxP;
     if (first == 2 && !scatter_ok) {
-        set_error("first_pass = 2 (scatter) needs union mode 2 and p <= %d", kFirstPassMaxP);
+        set_error("first_pass = 2 (scatter) needs p <= %d", kFirstPassMaxP);
         return VGA_EINVAL;
     }
     P->first_scatter = scatter_ok && first != 1;
@@ -482,8 +500,11 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
     P->off_sum = o;   o = align256(o + 8 * P->n);
     P->off_lc = o;    o = align256(o + 8 * ((uint64_t)P->m + 1));
     P->off_flags = o; o = align256(o + 64);
+    // the table region; pass 1's scatter keeps the nodes' keys there (mode 1 has
+    // no table region otherwise)
     P->off_tab = o;
     if (P->mode == kModeRuns) o = align256(o + (uint64_t)table_rows(P->scheme) * P->n * (uint64_t)S);
+    else if (P->first_scatter) o = align256(o + 4 * P->n);
     const int track = tune ? tune->track_changes : 0;
     if (track < 0 || track > 2) {
         set_error("track_changes = %d must be 0 (automatic), 1 (off) or 2 (every pass)", track);
@@ -653,10 +674,14 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const void *keys
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
         const int most = kFirstPassWarps * ((1 << kFirstPassMaxP) + 32) * 4;
-        const void *fns[4] = {reinterpret_cast<const void *>(hb_first_pass_kernel<false, uint16_t>),
+        const void *fns[8] = {reinterpret_cast<const void *>(hb_first_pass_kernel<false, uint16_t>),
                               reinterpret_cast<const void *>(hb_first_pass_kernel<false, uint32_t>),
                               reinterpret_cast<const void *>(hb_first_pass_kernel<true, uint16_t>),
-                              reinterpret_cast<const void *>(hb_first_pass_kernel<true, uint32_t>)};
+                              reinterpret_cast<const void *>(hb_first_pass_kernel<true, uint32_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_csr_kernel<false, uint16_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_csr_kernel<false, uint32_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_csr_kernel<true, uint16_t>),
+                              reinterpret_cast<const void *>(hb_first_pass_csr_kernel<true, uint32_t>)};
         for (const void *f : fns)
             if (attr_err == cudaSuccess)
                 attr_err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
@@ -668,15 +693,21 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const void *keys
         VGA_CHECK_CUDA(cudaEventCreate(&pt.stop));
         VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
     }
-    const unsigned blocks = (unsigned)((P.items.count + kFirstPassWarps - 1) / kFirstPassWarps);
+    const bool runs = P.mode == kModeRuns;
+    const uint64_t units = runs ? P.items.count : P.n;  // work items, or nodes in mode 1
+    const unsigned blocks = (unsigned)((units + kFirstPassWarps - 1) / kFirstPassWarps);
     const int s_log2 = __builtin_ctz((unsigned)P.S);
-    const uint32_t *lk = g->lk[P.scheme].d_lk;
+    const uint32_t *lk = runs ? g->lk[P.scheme].d_lk : nullptr;
     const uint32_t n = (uint32_t)P.n;
     const bool k16 = P.p <= kKey16MaxP;
-#define VGA_FP(NIBV, KT)                                                                                          \
-    hb_first_pass_kernel<NIBV, KT><<<blocks, kFirstPassWarps * 32, smem, stream>>>(                              \
-        P.items.items, P.items.count, lk, static_cast<const KT *>(keys), n, P.p, P.scheme, s_log2, s0, s1, nxt, \
-        flags, chg)
+#define VGA_FP(NIBV, KT)                                                                                            \
+    if (runs)                                                                                                       \
+        hb_first_pass_kernel<NIBV, KT><<<blocks, kFirstPassWarps * 32, smem, stream>>>(                            \
+            P.items.items, P.items.count, lk, static_cast<const KT *>(keys), n, P.p, P.scheme, s_log2, s0, s1, nxt, \
+            flags, chg);                                                                                            \
+    else                                                                                                            \
+        hb_first_pass_csr_kernel<NIBV, KT><<<blocks, kFirstPassWarps * 32, smem, stream>>>(                        \
+            g->d_offsets, g->d_bytes, static_cast<const KT *>(keys), n, P.p, s_log2, nxt, flags)
     if (blocks) {
         if (P.nib) {
             if (k16) VGA_FP(true, uint16_t);
@@ -1043,6 +1074,7 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     s->seed = seed;
     s->shard = shard;
     s->n_shards = n_shards;
+    if (P.mode != kModeRuns) P.first_scatter = false;  // a mode-1 shard has no table region for the keys
     s->all_slices = (uint32_t)P.slices;
     s->s0 = (uint32_t)((uint64_t)shard * P.slices / n_shards);
     s->s1 = (uint32_t)((uint64_t)(shard + 1) * P.slices / n_shards);

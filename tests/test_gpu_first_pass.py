@@ -6,7 +6,8 @@ register cells instead of gathering register rows.  Both ways must give the
 oracle's registers bit for bit after every pass (the later passes start from
 the scattered registers), across p = 4 .. 13, both table schemes, 8- and 4-bit
 registers, slice widths from 16 to 1024 bytes, split hubs and register-range
-shards; p above 13 and the per-neighbour union fall back to the gather.
+shards, in both union variants (the per-neighbour one decodes the CSR for the
+scatter); p above 13 falls back to the gather.
 """
 import numpy as np
 import pytest
@@ -141,14 +142,27 @@ def test_first_pass_isolated_and_tiny_graphs(vga):
     assert_same_run(got, ref)
 
 
+@pytest.mark.parametrize("seed,p,d,bits,S", [(1, 4, 0, 8, 16), (2, 8, 0, 8, 64), (3, 10, 3, 8, 0), (4, 12, 2, 8, 256),
+                                              (5, 13, 1, 8, 0), (1, 10, 0, 4, 32), (2, 6, 0, 4, 16)])
+def test_first_pass_scatter_per_neighbour(vga, seed, p, d, bits, S):
+    # the per-neighbour variant decodes the CSR itself for the scatter
+    off, b, _ = tiny_graph(seed)
+    ref = oracle.hyperball(off, b, p, d, seed=seed * 17 + 3, trace=12, reg_bits=bits)
+    with vga.vga_graph_load(off, b) as g:
+        for first in (2, 1):
+            got = vga.hyperball_run_trace(g, p, d, seed=seed * 17 + 3, max_trace=12, slice_bytes=S, union_mode=1,
+                                          register_bits=0 if bits == 8 else bits, first_pass=first)
+            assert_same_run(got, ref)
+
+
 def test_first_pass_fallbacks_and_errors(vga):
     off, b, _ = tiny_graph(2)
     ref = oracle.hyperball(off, b, 14, 2, seed=8, trace=2)
     with vga.vga_graph_load(off, b) as g:
-        # p = 14 and the per-neighbour union take the gather for pass 1
+        # p = 14 takes the gather for pass 1 in both variants
         assert_same_run(vga.hyperball_run_trace(g, 14, 2, seed=8, max_trace=2, union_mode=2), ref)
         assert_same_run(vga.hyperball_run_trace(g, 14, 2, seed=8, max_trace=2, union_mode=1), ref)
-        for kw in (dict(p=14, union_mode=2, first_pass=2), dict(p=10, union_mode=1, first_pass=2),
+        for kw in (dict(p=14, union_mode=2, first_pass=2), dict(p=14, union_mode=1, first_pass=2),
                    dict(p=10, union_mode=2, first_pass=3), dict(p=10, union_mode=2, first_pass=-1)):
             p = kw.pop("p")
             with pytest.raises(vga.VgaError) as e:
