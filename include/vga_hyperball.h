@@ -207,12 +207,12 @@ typedef struct vga_tuning {
                             m cells of shared memory; p <= 13); 1: the union kernel, like
                             every later pass; 0: automatic (2 wherever allowed).  Same
                             registers bit for bit.                                         */
-    int track_changes;   /* mode 2, at most 32 slices: change tracking.  Each pass records
-                            which (node, slice) pairs changed; a node needs the next pass in
-                            a slice only if one of its neighbours changed there (otherwise
-                            its registers already hold the maximum), which is found through
-                            the range lookups before the pass, the other nodes keeping their
-                            registers.  0: automatic (a pass is tracked when the one before
+    int track_changes;   /* at most 32 slices: change tracking.  Each pass records which
+                            (node, slice) pairs changed; a node needs the next pass in a
+                            slice only if one of its neighbours changed there (otherwise its
+                            registers already hold the maximum), which is found before the
+                            pass through the range lookups (mode 2) or by decoding the CSR
+                            (mode 1), the other nodes keeping their registers.  0: automatic (a pass is tracked when the one before
                             changed fewer than 1 % of the pairs, e.g. the last passes of an
                             unlimited-depth run); 1: off; 2: every pass from the second.
                             Same registers bit for bit.                                    */

@@ -228,7 +228,8 @@ __device__ __forceinline__ void union_store(const typename RegFmt<NIB>::Acc (&ac
 template <int S, bool NIB = false>
 __device__ __forceinline__ void union_node_edges(const uint64_t *__restrict__ off, const uint8_t *__restrict__ bytes,
                                                  const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
-                                                 uint32_t v, uint32_t *ids, int lane, uint32_t *flag) {
+                                                 uint32_t v, uint32_t *ids, int lane, uint32_t *flag,
+                                                 uint8_t *chg = nullptr) {
     using Sh = GatherShape<S>;
     const int g = lane / Sh::G, sub = lane % Sh::G;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -247,7 +248,7 @@ __device__ __forceinline__ void union_node_edges(const uint64_t *__restrict__ of
         base = r.next_base;
         pos += (uint64_t)r.advance;
     }
-    union_store<S, NIB>(acc, cur, nxt, v, lane, flag);
+    union_store<S, NIB>(acc, cur, nxt, v, lane, flag, chg);
 }
 
 // ---------------------------------------------------------------------------

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(128) hb_first_pass_csr_kernel(const uint64_t *
                                                                 const uint8_t *__restrict__ bytes,
                                                                 const K *__restrict__ keys, uint32_t n, int p,
                                                                 int s_log2, uint8_t *__restrict__ nxt,
-                                                                uint32_t *__restrict__ flags) {
+                                                                uint32_t *__restrict__ flags,
+                                                                uint8_t *__restrict__ chg) {
     extern __shared__ __align__(16) uint32_t s_cells[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(128) hb_first_pass_csr_kernel(const uint64_t *
     if (warp >= n) return;
     const uint32_t m = 1u << p;
     first_pass_csr<NIB, K>(off, bytes, keys, (uint32_t)warp, n, p, s_log2, 0u, 0xffffffffu, nxt,
-                           s_cells + (uint64_t)wib * m, lane, flags, reinterpret_cast<int *>(flags + 2));
+                           s_cells + (uint64_t)wib * m, lane, flags, reinterpret_cast<int *>(flags + 2), chg);
 }
 
 // First pass of Eq. hll-union as a scatter of the nodes' keys (first_pass_item),
@@ -107,13 +108,19 @@ template <int S, bool NIB>
 __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restrict__ off,
                                                        const uint8_t *__restrict__ bytes,
                                                        const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt,
-                                                       uint32_t n, uint32_t *__restrict__ flags) {
+                                                       uint32_t n, uint32_t *__restrict__ flags,
+                                                       const uint32_t *__restrict__ need, int s,
+                                                       uint8_t *__restrict__ chg) {
     extern __shared__ uint32_t s_ids[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
-    union_node_edges<S, NIB>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags);
+    if (need && !((need[warp] >> s) & 1u)) {  // a change-tracked pass: no neighbour changed this slice
+        keep_item<S, NIB>(cur, nxt, (uint32_t)warp, false, lane, reinterpret_cast<int *>(flags + 2));
+        return;
+    }
+    union_node_edges<S, NIB>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags, chg);
 }
 
 // Run-aware Eq. hll-union for one register slice, one warp per work item
@@ -183,11 +190,12 @@ __global__ void hb_count_kernel(const uint32_t *__restrict__ words, uint64_t n_w
 // slice, whether a node of the window [i, i + w) changed slice s, w being the
 // window width of the slot in the table scheme (the rows and row indices of
 // the table of range maxima, so that a range lookup addresses both).
-__global__ void hb_ortab_kernel(const uint8_t *__restrict__ chg, uint32_t n, int slices, int scheme,
+// `rows` rows of the scheme are built (1: the per-node masks alone, which the
+// per-neighbour variant ORs over decoded ids).
+__global__ void hb_ortab_kernel(const uint8_t *__restrict__ chg, uint32_t n, int slices, int scheme, int rows,
                                 uint32_t *__restrict__ ortab) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int rows = table_rows(scheme);
     uint32_t acc = 0;
     int slot = 0;
     for (uint32_t j = 0; j < (1u << kRunLevels) && slot < rows; j++) {
@@ -230,6 +238,31 @@ __global__ void __launch_bounds__(256) hb_need_kernel(const RunItem *__restrict_
         else
             need[it.v] = acc;
     }
+}
+
+// need[v] for the per-neighbour variant: the warp decodes node v's list
+// (decode_window) and ORs the change masks (`masks`, one u32 per node) of the
+// decoded ids, stopping once every slice is needed.
+__global__ void __launch_bounds__(256) hb_need_csr_kernel(const uint64_t *__restrict__ off,
+                                                          const uint8_t *__restrict__ bytes, uint32_t n,
+                                                          const uint32_t *__restrict__ masks, uint32_t all,
+                                                          uint32_t *__restrict__ need) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= n) return;
+    uint64_t pos = off[warp];
+    const uint64_t end = off[warp + 1];
+    uint32_t base = 0, acc = 0;
+    while (pos < end) {
+        const WindowDecode<uint32_t> r = decode_window<uint32_t>(bytes, pos, end, base, lane);
+        if (r.term_mask == 0) break;  // cannot happen on a validated graph; guarantees progress
+        if ((r.term_mask >> lane) & 1u) acc |= __ldg(masks + r.id);
+        if (__reduce_or_sync(0xffffffffu, acc) == all) break;
+        base = r.next_base;
+        pos += (uint64_t)r.advance;
+    }
+    acc = __reduce_or_sync(0xffffffffu, acc);
+    if (lane == 0) need[warp] = acc;
 }
 
 // The slice's table region (table_item: T_0 and the scheme's levels), B rows
@@ -510,9 +543,9 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         set_error("track_changes = %d must be 0 (automatic), 1 (off) or 2 (every pass)", track);
         return VGA_EINVAL;
     }
-    const bool track_ok = P->mode == kModeRuns && P->slices <= kTrackMaxSlices;
+    const bool track_ok = P->slices <= kTrackMaxSlices;
     if (track == 2 && !track_ok) {
-        set_error("track_changes = 2 needs union mode 2 and at most %d slices (have %d)", kTrackMaxSlices, P->slices);
+        set_error("track_changes = 2 needs at most %d slices (have %d)", kTrackMaxSlices, P->slices);
         return VGA_EINVAL;
     }
     P->track = !track_ok || track == 1 ? 0 : track == 2 ? 2 : 1;
@@ -520,7 +553,8 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         P->chg_bytes = align256((uint64_t)P->slices * P->n);
         P->off_chg = o;   o = align256(o + P->chg_bytes);
         P->off_need = o;  o = align256(o + 4 * P->n);
-        P->off_ortab = o; o = align256(o + 4ull * table_rows(P->scheme) * P->n);
+        P->off_ortab = o;  // range-OR table (mode 2), or the per-node change masks (mode 1)
+        o = align256(o + 4ull * (P->mode == kModeRuns ? table_rows(P->scheme) : 1) * P->n);
     }
     P->total = o;
     return VGA_OK;
@@ -604,7 +638,7 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
             P.items.items, P.items.count, g->lk[P.scheme].d_lk, c, tab, x, (uint32_t)P.n, flags, need, s, chg);
     } else {
         hb_union_kernel<SS, NIB><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
-                                                                    flags);
+                                                                    flags, need, s, chg);
     }
     count_launch();
 }
@@ -707,7 +741,7 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const void *keys
             flags, chg);                                                                                            \
     else                                                                                                            \
         hb_first_pass_csr_kernel<NIBV, KT><<<blocks, kFirstPassWarps * 32, smem, stream>>>(                        \
-            g->d_offsets, g->d_bytes, static_cast<const KT *>(keys), n, P.p, s_log2, nxt, flags)
+            g->d_offsets, g->d_bytes, static_cast<const KT *>(keys), n, P.p, s_log2, nxt, flags, chg)
     if (blocks) {
         if (P.nib) {
             if (k16) VGA_FP(true, uint16_t);
@@ -742,13 +776,19 @@ static int launch_need(const Plan &P, const vga_graph *g, const uint8_t *chg, ui
         VGA_CHECK_CUDA(cudaEventCreate(&pt.stop));
         VGA_CHECK_CUDA(cudaEventRecord(pt.start, stream));
     }
-    hb_ortab_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(chg, (uint32_t)P.n, P.slices, P.scheme,
-                                                                       ortab);
+    const bool runs = P.mode == kModeRuns;
+    hb_ortab_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, stream>>>(
+        chg, (uint32_t)P.n, P.slices, P.scheme, runs ? table_rows(P.scheme) : 1, ortab);
     count_launch();
-    VGA_CHECK_CUDA(cudaMemsetAsync(need, 0, 4 * P.n, stream));
     const uint32_t all = P.slices >= 32 ? 0xffffffffu : (1u << P.slices) - 1u;
-    hb_need_kernel<<<(unsigned)((P.items.count + 7) / 8), 256, 0, stream>>>(P.items.items, P.items.count,
-                                                                            g->lk[P.scheme].d_lk, ortab, all, need);
+    if (runs) {
+        VGA_CHECK_CUDA(cudaMemsetAsync(need, 0, 4 * P.n, stream));
+        hb_need_kernel<<<(unsigned)((P.items.count + 7) / 8), 256, 0, stream>>>(
+            P.items.items, P.items.count, g->lk[P.scheme].d_lk, ortab, all, need);
+    } else {
+        hb_need_csr_kernel<<<(unsigned)((P.n + 7) / 8), 256, 0, stream>>>(g->d_offsets, g->d_bytes, (uint32_t)P.n,
+                                                                          ortab, all, need);
+    }
     count_launch();
     VGA_CHECK_CUDA(cudaGetLastError());
     if (timings) {

@@ -3,9 +3,9 @@
 A tracked pass recomputes node v in slice s only if one of v's neighbours
 changed slice s in the previous pass; every other node keeps its registers.
 Forcing tracking in every pass from the second (track_changes = 2) must still
-give the oracle's registers bit for bit after every pass, across both table
-schemes, slice widths, 8- and 4-bit registers, both first-pass methods and
-split hubs; the automatic rule must track the late passes of unlimited-depth
+give the oracle's registers bit for bit after every pass, across both union
+variants, both table schemes, slice widths, 8- and 4-bit registers, both
+first-pass methods and split hubs; the automatic rule must track the late passes of unlimited-depth
 runs and give the same results.
 """
 import numpy as np
@@ -83,6 +83,18 @@ def test_tracked_every_pass_bit_exact(vga, name, p, d, bits, S, levels, hub, fir
     assert_same_run(got, ref)
 
 
+@pytest.mark.parametrize("name,p,bits,S,first", [("tiny1", 10, 8, 0, 0), ("tiny3", 8, 8, 16, 1), ("comb", 8, 8, 32, 2),
+                                                  ("tiny2", 10, 4, 16, 0), ("rect96", 10, 8, 128, 0)])
+def test_tracked_per_neighbour(vga, name, p, bits, S, first):
+    # the per-neighbour variant finds the nodes to recompute by decoding the CSR
+    off, b = graph(name)
+    ref = oracle.hyperball(off, b, p, 0, seed=99, trace=16, reg_bits=bits)
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, p, 0, seed=99, max_trace=16, slice_bytes=S, union_mode=1,
+                                      register_bits=0 if bits == 8 else bits, first_pass=first, track_changes=2)
+    assert_same_run(got, ref)
+
+
 def test_automatic_tracking_on_unlimited_depth(vga):
     # On the ~42.7k-cell workload the fourth pass changes about 0.3 % of the
     # (node, slice) pairs, so the automatic rule tracks the fifth; the run must
@@ -121,7 +133,7 @@ def test_tracking_off_when_not_possible_and_errors(vga):
         # tracking stays off and the run is unchanged
         assert_same_run(vga.hyperball_run_trace(g, 12, 0, seed=3, max_trace=12, slice_bytes=16, union_mode=2), ref)
         for kw in (dict(p=12, slice_bytes=16, union_mode=2, track_changes=2),
-                   dict(p=10, union_mode=1, track_changes=2),
+                   dict(p=12, slice_bytes=16, union_mode=1, track_changes=2),
                    dict(p=10, union_mode=2, track_changes=3),
                    dict(p=10, union_mode=2, track_changes=-1)):
             p = kw.pop("p")
