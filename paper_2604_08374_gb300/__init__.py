@@ -573,11 +573,12 @@ class Shard:
 
 def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, slice_bytes: int = 0,
                      warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
-                     hub_lookups: int = 0, table_levels: int = 0, first_pass: int = 0) -> Shard:
+                     hub_lookups: int = 0, table_levels: int = 0, first_pass: int = 0,
+                     track_changes: int = 0) -> Shard:
     h = C.c_void_p()
     _check(lib().vga_shard_create(g.handle, p, seed, shard, n_shards,
                                   _tuning(slice_bytes, warps_per_cta, 0, union_mode, register_bits, hub_lookups,
-                                          table_levels, first_pass=first_pass),
+                                          table_levels, first_pass=first_pass, track_changes=track_changes),
                                   C.byref(h)))
     return Shard(h)
 

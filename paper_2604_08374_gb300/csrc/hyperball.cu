@@ -1086,6 +1086,9 @@ struct vga_shard {
     uint8_t *cur = nullptr, *nxt = nullptr, *tab = nullptr;
     double *c_prev = nullptr, *c_cur = nullptr, *sum_d = nullptr, *lc = nullptr;
     uint32_t *flags = nullptr;
+    uint8_t *chg = nullptr;                  // change tracking (P.track): change bytes of the shard's slices,
+    uint32_t *need = nullptr, *ortab = nullptr;  // need masks and the range-OR table (or per-node masks)
+    uint64_t changed_prev = ~0ull;           // (node, slice) pairs the previous pass changed here
     int t = -1;  // passes run; -1 before vga_shard_start
 };
 
@@ -1130,6 +1133,15 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     const uint64_t off_flags = o; o = align256(o + 64);
     const uint64_t off_tab = o;
     if (P.mode == kModeRuns) o = align256(o + (uint64_t)table_rows(P.scheme) * n * (uint64_t)P.S);
+    // change tracking over the shard's own slices (a slice's registers depend
+    // only on the same slice of the neighbours, so no exchange is needed)
+    uint64_t off_chg = 0, off_need = 0, off_ortab = 0;
+    if (P.track) {
+        P.chg_bytes = align256((uint64_t)P.slices * n);
+        off_chg = o;   o = align256(o + P.chg_bytes);
+        off_need = o;  o = align256(o + 4 * n);
+        off_ortab = o; o = align256(o + 4ull * (P.mode == kModeRuns ? table_rows(P.scheme) : 1) * n);
+    }
     const int rc = s->ws.alloc(o);
     if (rc != VGA_OK) {
         delete s;
@@ -1144,6 +1156,11 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     s->lc = reinterpret_cast<double *>(base + off_lc);
     s->flags = reinterpret_cast<uint32_t *>(base + off_flags);
     s->tab = base + off_tab;
+    if (P.track) {
+        s->chg = base + off_chg;
+        s->need = reinterpret_cast<uint32_t *>(base + off_need);
+        s->ortab = reinterpret_cast<uint32_t *>(base + off_ortab);
+    }
     s->zeros_off = align256(8 * n);
     s->block_bytes = s->zeros_off + align256(4 * n);
     if (P.mode == kModeRuns && n > 0) {
@@ -1218,6 +1235,7 @@ int vga_shard_start(vga_shard *s, void *partial_dev, void *stream_ptr) {
     }
     VGA_TRY(shard_partials(s, s->cur, partial_dev, stream));
     s->t = 0;
+    s->changed_prev = ~0ull;
     return VGA_OK;
 }
 
@@ -1242,15 +1260,27 @@ int vga_shard_union(vga_shard *s, void *partial_dev, uint32_t *changed, void *st
     } settle{timings};
     if (P.n > 0) {
         VGA_CHECK_CUDA(cudaMemsetAsync(s->flags, 0, 4, stream));
+        const bool tracked = s->chg && s->t >= 1 &&
+                             (P.track == 2 || (double)s->changed_prev < kTrackBelow * (double)P.n * P.slices);
+        if (tracked) VGA_TRY(launch_need(P, s->g, s->chg, s->ortab, s->need, stream, profiling ? &timings : nullptr));
+        if (s->chg) {
+            VGA_CHECK_CUDA(cudaMemsetAsync(s->chg, 0, P.chg_bytes, stream));
+            VGA_CHECK_CUDA(cudaMemsetAsync(s->flags + 4, 0, 8, stream));
+        }
         if (s->t == 0 && P.first_scatter)
-            VGA_TRY(launch_first_pass(P, s->g, s->tab, s->nxt, s->s0, s->s1,
-                                      s->flags, stream, profiling ? &timings : nullptr));
+            VGA_TRY(launch_first_pass(P, s->g, s->tab, s->nxt, s->s0, s->s1, s->flags, stream,
+                                      profiling ? &timings : nullptr, s->chg));
         else
-            VGA_TRY(launch_union(P, s->g, s->cur, s->nxt, s->tab, s->flags, stream, profiling ? &timings : nullptr));
+            VGA_TRY(launch_union(P, s->g, s->cur, s->nxt, s->tab, s->flags, stream, profiling ? &timings : nullptr,
+                                 tracked ? s->need : nullptr, s->chg));
+        if (s->chg) VGA_TRY(launch_count(P, s->chg, s->flags, stream));
     }
     VGA_TRY(shard_partials(s, s->nxt, partial_dev, stream));
+    uint64_t n_changed = 0;
     VGA_CHECK_CUDA(cudaMemcpyAsync(h, s->flags, 12, cudaMemcpyDeviceToHost, stream));
+    if (s->chg) VGA_CHECK_CUDA(cudaMemcpyAsync(&n_changed, s->flags + 4, 8, cudaMemcpyDeviceToHost, stream));
     VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    s->changed_prev = n_changed;
     if (h[2] & 1u) {
         set_error("vga_shard_union: a bounded wait for a TMA copy ran out in pass %d", s->t + 1);
         return VGA_ETIMEOUT;

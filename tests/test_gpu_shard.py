@@ -50,6 +50,10 @@ CASES = [
     ("rect60", 8, 0, 2, 0, dict(slice_bytes=16, register_bits=4)),
     ("tiny1", 10, 2, 4, 0, dict(slice_bytes=32, hub_lookups=3)),
     ("tiny3", 12, 3, 2, 0, dict()),
+    # change tracking over each shard's own slices (forced in every pass from the second)
+    ("tiny1", 8, 0, 3, 0, dict(slice_bytes=16, track_changes=2)),
+    ("rect60", 8, 0, 2, 0, dict(slice_bytes=32, union_mode=1, track_changes=2)),
+    ("tiny3", 10, 0, 4, 1, dict(slice_bytes=64, track_changes=2, hub_lookups=5)),
 ]
 
 
@@ -93,3 +97,28 @@ def test_shard_layout_and_errors(vga, graphs):
         with pytest.raises(vga.VgaError) as e:
             vga.vga_shard_create(g, 8, 0, args[0], args[1], slice_bytes=16)
         assert e.value.status == vga.VGA_EINVAL
+
+
+def test_sharded_automatic_tracking_medium(vga):
+    # on the ~42.7k-cell workload the fifth pass is tracked by every shard and
+    # the sharded run equals the unsharded one bit for bit
+    torch = pytest.importorskip("torch")
+    from paper_2604_08374_gb300.sharded import hyperball_run_sharded_local
+    g = vga.vga_visibility_build(workloads.medium(seed=3))
+    try:
+        it0, md0, ball0 = _alone(vga, torch, g, 10, 0, 5, 0, slice_bytes=128)
+        md = torch.empty(g.n_nodes, dtype=torch.float64, device="cuda")
+        ball = torch.empty_like(md)
+        vga.vga_profile_reset()
+        vga.vga_profile_enable(True)
+        try:
+            it = hyperball_run_sharded_local(g, 10, 0, 5, 2, md, ball, slice_bytes=128)
+            prof = vga.vga_profile_read()
+        finally:
+            vga.vga_profile_enable(False)
+    finally:
+        g.free()
+    assert it == it0 >= 4
+    assert prof["tracked_launches"] > 0
+    assert np.array_equal(md.cpu().numpy(), md0, equal_nan=True)
+    assert np.array_equal(ball.cpu().numpy(), ball0)
