@@ -62,8 +62,9 @@ __global__ void batch_init_kernel(JobDev *jobs, const uint64_t *__restrict__ nod
 }
 
 // Pass 1 of the jobs in fjobs[0 .. n) (all of precision p, all fresh) as the
-// scatter of their nodes' keys (first_pass_item), one warp per work item of
-// the concatenated work lists; the jobs' union launch skips them in pass 1.
+// scatter of their nodes' keys, one warp per work item of the concatenated
+// work lists (first_pass_item; a per-neighbour job's units are its nodes,
+// first_pass_csr); the jobs' union launch skips them in pass 1.
 template <class K>
 __global__ void __launch_bounds__(kFirstPassWarps * 32) batch_first_pass_kernel(JobDev *jobs,
                                                                                const uint32_t *__restrict__ fjobs,
@@ -79,10 +80,14 @@ __global__ void __launch_bounds__(kFirstPassWarps * 32) batch_first_pass_kernel(
     for (uint64_t x = (uint64_t)blockIdx.x * kFirstPassWarps + wib; x < total; x += warps) {
         const int k = find_job(fstart, n, x);
         JobDev &J = jobs[fjobs[k]];
-        const RunItem it = J.items[x - fstart[k]];
-        first_pass_item<false, K>(it, J.lk, reinterpret_cast<const K *>(J.tab), J.n, J.p, J.scheme,
-                               __ffs(J.S) - 1, 0u, (uint32_t)J.slices, J.regs[1], cells, cells + m, lane, &J.changed,
-                               error);
+        if (J.mode == 2)
+            first_pass_item<false, K>(J.items[x - fstart[k]], J.lk, reinterpret_cast<const K *>(J.tab), J.n, J.p,
+                                      J.scheme, __ffs(J.S) - 1, 0u, (uint32_t)J.slices, J.regs[1], cells, cells + m,
+                                      lane, &J.changed, error);
+        else  // per-neighbour job: the work units are its nodes, the scatter decodes the CSR
+            first_pass_csr<false, K>(J.off, J.bytes, reinterpret_cast<const K *>(J.tab), (uint32_t)(x - fstart[k]),
+                                     J.n, J.p, __ffs(J.S) - 1, 0u, (uint32_t)J.slices, J.regs[1], cells, lane,
+                                     &J.changed, error);
     }
 }
 
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         const int k = find_job(item_start, n_jobs, item);
         JobDev &J = jobs[gjobs[k]];
         if (J.state != 0) continue;
-        if (RUNS && J.first && J.t == 0) continue;  // pass 1 was the scatter (engine_start)
+        if (J.first && J.t == 0) continue;  // pass 1 was the scatter (engine_start)
         const uint32_t ublocks = (J.units + kEngineBlock - 1) / kEngineBlock;
         const uint64_t per_slice = (uint64_t)ublocks + (RUNS ? (uint64_t)J.tblocks : 0);
         const uint64_t r = item - item_start[k];
@@ -270,6 +275,8 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
     if (L.mode == 2) {
         o = align256(o + (uint64_t)table_rows(scheme) * n * m);
         o = align256(o + 4ull * L.slices);
+    } else if (p <= kFirstPassMaxP) {
+        o = align256(o + 4ull * n);  // the keys of pass 1's scatter
     }
     L.bytes = o;
     return L;
@@ -295,10 +302,11 @@ int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const
         J.scheme = L.scheme;
         J.items = list.items;
         J.units = (uint32_t)list.count;
-        J.first = p <= kFirstPassMaxP ? 1 : 0;
     } else {
         J.units = g->n;
+        if (p <= kFirstPassMaxP) J.tab = ws + o;  // the keys of pass 1's scatter (job_layout)
     }
+    J.first = p <= kFirstPassMaxP ? 1 : 0;
     J.off = g->d_offsets;
     J.bytes = g->d_bytes;
     J.comp = g->d_comp;
