@@ -69,7 +69,8 @@ template <bool NIB, class K>
 __global__ void __launch_bounds__(128) hb_first_pass_csr_kernel(const uint64_t *__restrict__ off,
                                                                 const uint8_t *__restrict__ bytes,
                                                                 const K *__restrict__ keys, uint32_t n, int p,
-                                                                int s_log2, uint8_t *__restrict__ nxt,
+                                                                int s_log2, uint32_t s0, uint32_t s1,
+                                                                uint8_t *__restrict__ nxt,
                                                                 uint32_t *__restrict__ flags,
                                                                 uint8_t *__restrict__ chg) {
     extern __shared__ __align__(16) uint32_t s_cells[];
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(128) hb_first_pass_csr_kernel(const uint64_t *
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n) return;
     const uint32_t m = 1u << p;
-    first_pass_csr<NIB, K>(off, bytes, keys, (uint32_t)warp, n, p, s_log2, 0u, 0xffffffffu, nxt,
+    first_pass_csr<NIB, K>(off, bytes, keys, (uint32_t)warp, n, p, s_log2, s0, s1, nxt,
                            s_cells + (uint64_t)wib * m, lane, flags, reinterpret_cast<int *>(flags + 2), chg);
 }
 
@@ -741,7 +742,7 @@ static int launch_first_pass(const Plan &P, const vga_graph *g, const void *keys
             flags, chg);                                                                                            \
     else                                                                                                            \
         hb_first_pass_csr_kernel<NIBV, KT><<<blocks, kFirstPassWarps * 32, smem, stream>>>(                        \
-            g->d_offsets, g->d_bytes, static_cast<const KT *>(keys), n, P.p, s_log2, nxt, flags, chg)
+            g->d_offsets, g->d_bytes, static_cast<const KT *>(keys), n, P.p, s_log2, s0, s1, nxt, flags, chg)
     if (blocks) {
         if (P.nib) {
             if (k16) VGA_FP(true, uint16_t);
@@ -1117,7 +1118,6 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     s->seed = seed;
     s->shard = shard;
     s->n_shards = n_shards;
-    if (P.mode != kModeRuns) P.first_scatter = false;  // a mode-1 shard has no table region for the keys
     s->all_slices = (uint32_t)P.slices;
     s->s0 = (uint32_t)((uint64_t)shard * P.slices / n_shards);
     s->s1 = (uint32_t)((uint64_t)(shard + 1) * P.slices / n_shards);
@@ -1131,8 +1131,9 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
     const uint64_t off_sum = o;   o = align256(o + 8 * n);
     const uint64_t off_lc = o;    o = align256(o + 8 * ((uint64_t)P.m + 1));
     const uint64_t off_flags = o; o = align256(o + 64);
-    const uint64_t off_tab = o;
+    const uint64_t off_tab = o;  // the table region, or (mode 1) the keys of pass 1's scatter
     if (P.mode == kModeRuns) o = align256(o + (uint64_t)table_rows(P.scheme) * n * (uint64_t)P.S);
+    else if (P.first_scatter) o = align256(o + 4 * n);
     // change tracking over the shard's own slices (a slice's registers depend
     // only on the same slice of the neighbours, so no exchange is needed)
     uint64_t off_chg = 0, off_need = 0, off_ortab = 0;
