@@ -7,6 +7,11 @@
 - The estimator against closed forms: an empty counter gives 0, a counter
   holding one element gives m ln(m/(m-1)) (linear counting), a counter whose
   registers all equal r >= 1 gives alpha_m m 2^r (raw estimate, V = 0).
+- The switch between the two regimes: counters built so that the raw estimate
+  is exactly 2.5 m, one double either side of it, and at fixed ratios from
+  1.2 m to 5.5 m; linear counting m ln(m/V) is returned exactly when E <= 2.5 m
+  (with V > 0), so a threshold of 2 m, 3 m or 5 m, or a strict comparison,
+  fails.
 - Its accuracy against exact counts: the relative error's RMS over many
   counters stays within the standard error 1.04/sqrt(m) quoted in Sec. 2.3
   (with a 1.5x margin), and its mean shows no bias beyond that.
@@ -135,3 +140,104 @@ def test_accumulate_rounds_each_step():
     assert oracle.accumulate(9.0, 2, 30.0, 10.0) == 49.0
     a, t, c1, c0 = 0.1, 3, 0.7, 0.3
     assert oracle.accumulate(a, t, c1, c0) == a + t * (c1 - c0)
+
+
+# --- the estimator's regime switch (Sec. 2.3 and Sec. 3.3: small-range linear
+# counting below 2.5 m) --------------------------------------------------------
+#
+# A counter's raw estimate is E = alpha_m m^2 / Z with Z = sum_j 2^-M[j].  The
+# oracle forms Z exactly as the integer S = Z 2^K (K = 65 - p) and rounds it
+# once, so any double Z that is a multiple of 2^-K can be realised by a counter:
+# V zero registers give V 2^K, and the remaining S - V 2^K is split into m - V
+# powers of two 2^(K - M), one per register of value M in 1..K.  That lets a test
+# put E exactly at 2.5 m, or one double either side of it, and check which of
+# the two formulas the oracle returns.
+
+def _counter_with_sum(S: int, V: int, p: int) -> np.ndarray:
+    """Registers of m = 2^p with V zeros and sum_j 2^(K - M[j]) == S exactly."""
+    m, K = 1 << p, 65 - p
+    R = S - V * (1 << K)
+    assert R >= m - V
+    terms = []  # exponents e of 2^e, each in [0, K - 1]
+    for e in range(R.bit_length()):
+        if (R >> e) & 1:
+            if e <= K - 1:
+                terms.append(e)
+            else:
+                terms.extend([K - 1] * (1 << (e - K + 1)))
+    terms.sort()
+    while len(terms) < m - V:  # split the largest power until every register has one
+        e = terms.pop()
+        assert e > 0
+        terms.extend([e - 1, e - 1])
+        terms.sort()
+    assert len(terms) == m - V, "the sum has more binary digits than registers"
+    reg = np.zeros(m, np.uint8)
+    reg[V:] = [K - e for e in terms]
+    rng = np.random.default_rng(p)
+    rng.shuffle(reg)
+    assert sum(1 << (K - int(x)) for x in reg) == S
+    return reg
+
+
+def _z_where_raw_estimate_is(p: int, pick, near: float = 2.5, grid: int = 0):
+    """The double Z (a multiple of 2^-K) nearest alpha_m m / near for which
+    pick(alpha_m m^2 / Z, 2.5 m) holds; with grid > 0 the start is rounded to
+    a multiple of 2^-grid (fewer binary digits to spread over the registers)."""
+    m, K = 1 << p, 65 - p
+    alpha_mm = oracle.hll_alpha(p) * m * m
+    thr = 2.5 * m
+    z = alpha_mm / (near * m)
+    if grid:
+        z = round(z * 2 ** grid) / 2 ** grid
+    for direction in (0, 1):
+        zz = z
+        for _ in range(64):
+            if pick(alpha_mm / zz, thr):
+                S = int(zz * 2 ** K)
+                assert S == zz * 2 ** K
+                return zz, S
+            zz = math.nextafter(zz, math.inf if direction else 0.0)
+    raise AssertionError("no Z found")
+
+
+@pytest.mark.parametrize("p", [6, 8, 10, 12, 14, 16])
+def test_estimator_switches_to_linear_counting_at_exactly_two_and_a_half_m(p):
+    m = 1 << p
+    V = m // 8
+    alpha_mm = oracle.hll_alpha(p) * m * m
+    lc = m * math.log(m / V)
+    # E == 2.5 m exactly: the small-range rule applies (E <= 2.5 m and V > 0)
+    z, S = _z_where_raw_estimate_is(p, lambda e, t: e == t)
+    reg = _counter_with_sum(S, V, p)
+    assert alpha_mm / z == 2.5 * m
+    assert oracle.hll_estimate(reg, p) == pytest.approx(lc, rel=1e-15)
+    # one double above the threshold: the raw estimate, not linear counting
+    z, S = _z_where_raw_estimate_is(p, lambda e, t: e > t and e < t * (1 + 1e-12))
+    reg = _counter_with_sum(S, V, p)
+    assert oracle.hll_estimate(reg, p) == alpha_mm / z
+    assert lc < 2.5 * m < oracle.hll_estimate(reg, p)
+    # one double below: linear counting again
+    z, S = _z_where_raw_estimate_is(p, lambda e, t: e < t and e > t * (1 - 1e-12))
+    reg = _counter_with_sum(S, V, p)
+    assert oracle.hll_estimate(reg, p) == pytest.approx(lc, rel=1e-15)
+
+
+@pytest.mark.parametrize("p", [6, 10, 14])
+@pytest.mark.parametrize("ratio", [1.2, 2.0, 2.2, 2.45, 2.55, 3.0, 4.0, 5.5])
+def test_estimator_regime_on_both_sides_of_the_threshold(p, ratio):
+    # counters with V = m/8 zeros whose raw estimate sits at ratio x m: linear
+    # counting below 2.5 m, the raw estimate above (kills a threshold of 2 m,
+    # 3 m or 5 m as well as one read off the linear-counting value itself)
+    m = 1 << p
+    V = 3 * m // 8 if ratio < 2 else m // 8  # Z <= V + (m - V) / 2 bounds how few zeros fit
+    alpha_mm = oracle.hll_alpha(p) * m * m
+    z, S = _z_where_raw_estimate_is(p, lambda e, t: True, near=ratio, grid=16)
+    if V >= z:
+        pytest.skip("needs more zero registers than Z allows")
+    reg = _counter_with_sum(S, V, p)
+    got = oracle.hll_estimate(reg, p)
+    if ratio < 2.5:
+        assert got == pytest.approx(m * math.log(m / V), rel=1e-15)
+    else:
+        assert got == alpha_mm / z
