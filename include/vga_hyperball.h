@@ -290,17 +290,29 @@ int hyperball_run_dev(const vga_graph *g, int p, int d, uint64_t seed, int conv_
  *
  *   Arguments are those of hyperball_run_dev without workspace or tuning;
  *   outputs are device pointers (N doubles each, may be NULL).
- *   Size limit: hyperball_workspace_bytes(g, p) must not exceed 64 MiB
- *   (67,108,864 bytes), about N <= 32,000 nodes at p = 10 or N <= 125,000 at
- *   p = 8; larger requests return VGA_EINVAL with a message naming both sizes.
+ *   The run always uses the per-neighbour union (union_mode 1) with register
+ *   slices of min(m, 1024) bytes and 8-bit registers; results are bit for bit
+ *   those of hyperball_run_dev.
+ *   Size limit: with m = 2^p, s = max(1, m / 1024) slices and A(x) = x rounded
+ *   up to a multiple of 256, the run needs
+ *       2 A(N m) + 3 A(8 N) + A(8 (m + 1)) + 256
+ *       + A(4 N)                      if p <= 13 (first-pass keys)
+ *       + A(s N) + 2 A(4 N)           if p <= 15 (change tracking)
+ *   bytes, which must not exceed 64 MiB (67,108,864 bytes): about N <= 32,000
+ *   nodes at p = 10 or N <= 122,000 at p = 8.  This is the per-neighbour
+ *   workspace; hyperball_workspace_bytes sizes the automatic (usually
+ *   run-aware, larger) plan and may exceed 64 MiB for a run that fits here.
+ *   Larger requests return VGA_EINVAL with a message naming both sizes.
  *   The graph must live on the current device.
- *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture begins.
+ *   Set-up: the first call on each device (and again after the device's
+ *   context has been destroyed and re-created, e.g. by cudaDeviceReset) looks
+ *   up the array's device address (cudaGetSymbolAddress) with that device
+ *   current; make that first call before any stream capture begins.
  *   Sharing: every call on a device uses the same array, and it keeps the last
  *   call's contents; each call clears what must start at zero itself.  Calls
  *   whose work overlaps on the GPU (other streams, other host threads) race on
- *   the array and corrupt each other's results: serialise them.
+ *   the array and corrupt each other's results: serialise them.  A call that
+ *   fails after launching work waits for that work before it returns.
  */
 int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int conv_mode, double *mean_depth_dev,
                           double *ball_size_dev, int *iterations, void *stream);
@@ -467,7 +479,9 @@ typedef struct vga_profile {
                                      + 2 x N x slice bytes, summed                        */
     int slice_bytes;              /* slice width of the last timed launch                 */
     int union_mode;               /* union variant of the last timed launch (1 or 2)      */
-    int reserved[2];
+    int table_rows;               /* rows per node it gathered from: the table scheme's
+                                     (mode 2) or 1 (mode 1)                               */
+    int reserved;
     uint64_t first_pass_launches; /* first passes computed by the scatter (vga_tuning.
                                      first_pass), timed apart from the union slices       */
     double first_pass_ms;         /* their summed device time                             */
@@ -496,9 +510,16 @@ int vga_profile_read(vga_profile *out);
  *   gathers         total chunks gathered (one timed launch after a warm-up).
  *   consumer        1: xor the loaded words (the gather bandwidth itself; sized
  *                   below the L2 this is the L2 gather roofline); 0: fold them
- *                   with the union kernel's bytewise max (its loop's ceiling).
+ *                   with the union kernel's bytewise max (its loop's ceiling);
+ *                   2: no gather at all -- a coalesced stream of 16-byte loads
+ *                   over the buffer (consecutive threads on consecutive words,
+ *                   L2-only caching, 4 CTAs of 512 threads per SM), repeated
+ *                   until about gathers x chunk_bytes bytes have been read:
+ *                   the shape-independent L2 read ceiling of a buffer that
+ *                   fits in L2.
  *   stream          cudaStream_t or NULL.
- *   gb_per_s        out: gathers x chunk_bytes / kernel time.
+ *   gb_per_s        out: bytes read / kernel time (gathers x chunk_bytes for
+ *                   consumers 0 and 1).
  */
 int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, int consumer, void *stream,
                      double *gb_per_s);

@@ -56,7 +56,7 @@ class VgaServerStats(C.Structure):
 class VgaProfile(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("union_launches", C.c_uint64), ("union_ms", C.c_double),
                 ("union_edges", C.c_uint64), ("union_gather_bytes", C.c_uint64), ("union_hbm_bytes", C.c_uint64),
-                ("slice_bytes", C.c_int), ("union_mode", C.c_int), ("reserved", C.c_int * 2),
+                ("slice_bytes", C.c_int), ("union_mode", C.c_int), ("table_rows", C.c_int), ("reserved", C.c_int),
                 ("first_pass_launches", C.c_uint64), ("first_pass_ms", C.c_double),
                 ("first_pass_edges", C.c_uint64), ("tracked_launches", C.c_uint64), ("tracked_ms", C.c_double)]
 
@@ -490,7 +490,9 @@ def vga_bench_gather(resident_bytes: int, chunk_bytes: int, gathers: int, consum
     """Gather bandwidth (GB/s) with the union kernel's access pattern.
 
     consumer=1 xors the loaded words (the L2 gather roofline when the buffer
-    fits in L2); consumer=0 folds them with the union's bytewise max."""
+    fits in L2); consumer=0 folds them with the union's bytewise max;
+    consumer=2 streams the buffer with coalesced loads instead (the
+    shape-independent L2 read ceiling)."""
     out = C.c_double()
     _check(lib().vga_bench_gather(resident_bytes, chunk_bytes, gathers, consumer, _stream_ptr(stream),
                                   C.byref(out)))

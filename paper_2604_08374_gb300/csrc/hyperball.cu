@@ -15,6 +15,9 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "hb_device.cuh"
 
 namespace vga {
@@ -325,6 +328,34 @@ __global__ void __launch_bounds__(512) gather_bench_kernel(const uint8_t *__rest
     if (lane == 0) out[warp] = x_acc;
 }
 
+// Shape-independent L2 read ceiling: every thread streams 16-byte words of an
+// L2-resident buffer, consecutive threads on consecutive words (whole 128-byte
+// lines per 8 lanes), grid-stride, R passes over the buffer, 8 loads in flight
+// per thread, cached in L2 only (ld.global.cg) so that L1 hits cannot inflate
+// the figure.  The loaded words are xored into one word per warp.
+__global__ void __launch_bounds__(512) stream_bench_kernel(const uint4 *__restrict__ buf, uint64_t words,
+                                                           uint32_t passes, uint32_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (uint32_t r = 0; r < passes; r++) {
+        uint64_t i = t0;
+        for (; i + 7 * stride < words; i += 8 * stride) {
+            uint4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) x[u] = __ldcg(buf + i + u * stride);
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc ^= x[u].x ^ x[u].y ^ x[u].z ^ x[u].w;
+        }
+        for (; i < words; i += stride) {
+            const uint4 x = __ldcg(buf + i);
+            acc ^= x.x ^ x.y ^ x.z ^ x.w;
+        }
+    }
+    acc = __reduce_xor_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0) out[t0 >> 5] = acc;
+}
+
 // HLL estimate of every node, then Eq. sumD (estimate_node); flags[1]
 // records the paper's convergence test max_v(c_t - c_{t-1}) > 0.5.
 __global__ void hb_estimate_kernel(const uint8_t *__restrict__ regs, uint32_t n, int p, int S, int t,
@@ -620,7 +651,7 @@ static ProfileState &prof() {
 struct PendingTiming {
     cudaEvent_t start, stop;
     uint64_t edges, gather_bytes, hbm_bytes;
-    int S, mode;
+    int S, mode, rows;
     bool first;    // the first pass's scatter (hb_first_pass_kernel), not a union slice
     bool tracked;  // a union slice of a change-tracked pass (its work depends on the changes)
 };
@@ -691,6 +722,7 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
             }
             pt.S = P.S;
             pt.mode = P.mode;
+            pt.rows = P.mode == kModeRuns ? table_rows(P.scheme) : 1;
             pt.tracked = need != nullptr;
             timings->push_back(pt);
         }
@@ -840,6 +872,7 @@ static void settle_timings(std::vector<PendingTiming> &timings, bool to_profile,
             ps.acc.union_hbm_bytes += pt.hbm_bytes;
             ps.acc.slice_bytes = pt.S;
             ps.acc.union_mode = pt.mode;
+            ps.acc.table_rows = pt.rows;
         }
         cudaEventDestroy(pt.start);
         cudaEventDestroy(pt.stop);
@@ -1035,24 +1068,63 @@ namespace {
 // every GPU the library is used on holds these bytes from module load until the
 // process exits.  Host code must not use its name as a pointer: on the host it
 // is only a stand-in for the device symbol, and the device address is looked up
-// once per device with cudaGetSymbolAddress.
+// with cudaGetSymbolAddress once per device context.
 // ---------------------------------------------------------------------------
 constexpr uint64_t kStaticScratchBytes = 64ull << 20;  // 64 MiB
 __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-void *g_static_addr[kMaxDevices] = {nullptr};
+// Per device: the context the address was looked up in (by its unique ID, which
+// a context created later never reuses) and the address.  A device reset or a
+// released and re-created primary context loads the module again, possibly at
+// another address, so a cached address is used only in the context it came from.
+struct StaticScratchSlot {
+    unsigned long long ctx_id = 0;
+    void *addr = nullptr;
+};
+StaticScratchSlot g_static_slot[kMaxDevices];
 
-// Device address of g_static_scratch on the current device, looked up on the
-// first call made with that device current.
+// ID of the context current on this thread, through driver entry points that
+// the runtime hands out (no link against the driver library needed).
+int current_context_id(unsigned long long *id) {
+    static std::once_flag once;
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q{};
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS) {
+        set_error("hyperball_run_noalloc: cannot identify the current CUDA context");
+        return VGA_ECUDA;
+    }
+    return VGA_OK;
+}
+
+// Device address of g_static_scratch on the current device (`dev`), looked up
+// on the first call made in each of that device's contexts.
 int static_scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("hyperball_run_noalloc: device %d is beyond the supported %d devices", dev, kMaxDevices);
         return VGA_EINVAL;
     }
+    // binds the device's primary context to this thread (created if needed), so
+    // that the context queried below is the one the kernels will run in
+    VGA_CHECK_CUDA(cudaSetDevice(dev));
+    unsigned long long id = 0;
+    VGA_TRY(current_context_id(&id));
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    StaticScratchSlot &slot = g_static_slot[dev];
+    if (!slot.addr || slot.ctx_id != id) {
         void *addr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
         if (e != cudaSuccess || !addr) {
@@ -1060,9 +1132,10 @@ int static_scratch_address(int dev, void **out) {
                       cudaGetErrorString(e));
             return VGA_ECUDA;
         }
-        g_static_addr[dev] = addr;
+        slot.addr = addr;
+        slot.ctx_id = id;
     }
-    *out = g_static_addr[dev];
+    *out = slot.addr;
     return VGA_OK;
 }
 
@@ -1367,16 +1440,54 @@ int vga_profile_read(vga_profile *out) {
     return VGA_OK;
 }
 
+// vga_bench_gather consumer 2: the coalesced L2 stream (stream_bench_kernel)
+// over resident_bytes, repeated until about `bytes` have been read; full
+// occupancy (4 CTAs of 512 threads per SM).
+static int bench_stream(uint64_t resident_bytes, uint64_t bytes, cudaStream_t stream, double *gb_per_s) {
+    const uint64_t words = resident_bytes / 16;
+    if (words == 0) {
+        set_error("vga_bench_gather: buffer below 16 bytes");
+        return VGA_EINVAL;
+    }
+    int dev = 0, sms = 0;
+    VGA_CHECK_CUDA(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t blocks = (uint32_t)std::max(1, sms) * 4, threads = 512;
+    const uint32_t passes = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(1u << 20, bytes / (words * 16)));
+    DeviceBuffer buf, out;
+    VGA_TRY(buf.alloc(words * 16));
+    VGA_TRY(out.alloc((uint64_t)blocks * threads / 32 * 4));
+    VGA_CHECK_CUDA(cudaMemsetAsync(buf.ptr, 0x5A, words * 16, stream));
+    cudaEvent_t e0, e1;
+    VGA_CHECK_CUDA(cudaEventCreate(&e0));
+    VGA_CHECK_CUDA(cudaEventCreate(&e1));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; rep++) {  // warm-up (also brings the buffer into L2), then the timed launch
+        VGA_CHECK_CUDA(cudaEventRecord(e0, stream));
+        stream_bench_kernel<<<blocks, threads, 0, stream>>>(buf.as<uint4>(), words, passes, out.as<uint32_t>());
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+        VGA_CHECK_CUDA(cudaEventRecord(e1, stream));
+        VGA_CHECK_CUDA(cudaEventSynchronize(e1));
+        VGA_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *gb_per_s = (double)words * 16.0 * (double)passes / ((double)ms * 1e-3) / 1e9;
+    return VGA_OK;
+}
+
 int vga_bench_gather(uint64_t resident_bytes, int chunk_bytes, uint64_t gathers, int consumer, void *stream_ptr,
                      double *gb_per_s) {
     clear_error();
     const int S = chunk_bytes;
     if (!gb_per_s || S < 16 || S > 1024 || (S & (S - 1)) || resident_bytes < (uint64_t)S ||
-        resident_bytes / (uint64_t)S > 0xFFFFFFFFull || gathers == 0 || (consumer != 0 && consumer != 1)) {
+        resident_bytes / (uint64_t)S > 0xFFFFFFFFull || gathers == 0 || consumer < 0 || consumer > 2) {
         set_error("vga_bench_gather: bad arguments");
         return VGA_EINVAL;
     }
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    if (consumer == 2) return bench_stream(resident_bytes, (uint64_t)S * gathers, stream, gb_per_s);
     const uint32_t rows = (uint32_t)(resident_bytes / (uint64_t)S);
     const int warps = 8;
     int sms = 0;
@@ -1435,15 +1546,22 @@ int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int c
         set_error("hyperball_run_noalloc: null graph");
         return VGA_EINVAL;
     }
+    if (p < 4 || p > 16) {
+        set_error("hyperball_run_noalloc: precision p = %d is outside 4..16", p);
+        return VGA_EINVAL;
+    }
     int dev = -1;
     VGA_CHECK_CUDA(cudaGetDevice(&dev));
     if (dev != g->device) {
         set_error("hyperball_run_noalloc: the graph lives on device %d but device %d is current", g->device, dev);
         return VGA_EINVAL;
     }
-    // the per-neighbour union: the run-aware one would allocate its lookup list
+    // The per-neighbour union (the run-aware one would allocate its lookup
+    // list) at one fixed slice width, so that the scratch size depends on N and
+    // p alone, as the header states it, and not on an installed tuning table.
     vga_tuning per_edge{};
     per_edge.union_mode = kModePerEdge;
+    per_edge.slice_bytes = (int)std::min<uint32_t>(1u << p, 1024u);
     Plan P;
     VGA_TRY(make_plan(g, p, &per_edge, &P));
     if (P.total > kStaticScratchBytes) {
@@ -1457,8 +1575,13 @@ int hyperball_run_noalloc(const vga_graph *g, int p, int d, uint64_t seed, int c
     // run_impl zeroes the registers, sum_d and the flags itself and overwrites
     // everything else before reading it, so stale contents of the shared scratch
     // from an earlier call cannot leak into this one.
-    return run_impl(g, p, d, seed, conv_mode, mean_depth_dev, ball_size_dev, iterations, scratch, kStaticScratchBytes,
-                    static_cast<cudaStream_t>(stream), &per_edge, nullptr, nullptr, -1);
+    const int rc = run_impl(g, p, d, seed, conv_mode, mean_depth_dev, ball_size_dev, iterations, scratch,
+                            kStaticScratchBytes, static_cast<cudaStream_t>(stream), &per_edge, nullptr, nullptr, -1);
+    // A failure part-way leaves kernels queued that still write the shared
+    // array: wait for them, so that a caller who orders calls on the host
+    // cannot start the next one while they run.
+    if (rc != VGA_OK) cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    return rc;
 }
 
 int hyperball_workspace_bytes(const vga_graph *g, int p, uint64_t *bytes) {

@@ -128,6 +128,40 @@ def test_hyperball_bit_exact(vga, seed, p, d, S, warps, conv, mode):
     assert_same_run(got, ref)
 
 
+_regime_graph = {}
+
+
+def regime_graph():
+    # 60 x 60, 40 rectangles with sides 2..8: N = 2655 > 2.5 x 1024, and the
+    # balls grow past 2.5 m over passes 2 and 3 (every node crosses at p = 10)
+    if not _regime_graph:
+        obst = workloads.random_rectangles(60, 60, 40, (2, 8), seed=1)
+        _regime_graph["g"] = oracle.build_graph(obst)
+    return _regime_graph["g"]
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("p", [9, 10])
+def test_estimator_regime_switch_every_node(vga, p, mode):
+    # The estimator takes linear counting while E <= 2.5 m and the raw estimate
+    # above it (Sec. 2.3, Sec. 3.3).  On this graph every node's counter passes
+    # from one regime to the other inside the traced passes, and many sit
+    # within 2 % of the threshold; every node and pass is compared.
+    off, b, cells = regime_graph()
+    m = 1 << p
+    ref = oracle.hyperball(off, b, p, 0, seed=5, trace=12)
+    alpha_mm = oracle.hll_alpha(p) * m * m
+    lc_side = [alpha_mm / np.sum(np.ldexp(1.0, -r.astype(np.int64)), axis=1) <= 2.5 * m
+               for r in ref["regs"][: ref["iterations"] + 1]]
+    crossed = np.zeros(len(cells), bool)
+    for a, b_ in zip(lc_side, lc_side[1:]):
+        crossed |= a & ~b_
+    assert crossed.all(), "every node should cross from linear counting to the raw estimate"
+    with vga.vga_graph_load(off, b) as g:
+        got = vga.hyperball_run_trace(g, p, 0, seed=5, max_trace=12, union_mode=mode)
+    assert_same_run(got, ref)
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("grid", ["open40x30", "open1x300", "comb"])
 def test_long_runs(vga, grid, mode):
@@ -504,8 +538,10 @@ def test_load_from_device_buffers(vga):
 
 @pytest.mark.parametrize("S", [16, 64, 128, 1024])
 def test_gather_microbenchmark(vga, S):
-    for consumer in (0, 1):
+    for consumer in (0, 1, 2):
         gbs = vga.vga_bench_gather(64 << 20, S, 1 << 22, consumer=consumer)
         assert 100.0 < gbs < 1e6
     with pytest.raises(vga.VgaError):
         vga.vga_bench_gather(64 << 20, 48, 1 << 20)
+    with pytest.raises(vga.VgaError):
+        vga.vga_bench_gather(64 << 20, S, 1 << 20, consumer=3)
