@@ -97,6 +97,8 @@ def parse_args():
                     help="pass 1: 0 automatic (scatter), 1 the union's gather, 2 the scatter")
     ap.add_argument("--track-changes", type=int, default=0, choices=[0, 1, 2],
                     help="change tracking: 0 automatic, 1 off, 2 every pass from the second")
+    ap.add_argument("--group-nodes", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="grouped union: nodes per group (0 automatic = 4, 1 one node per warp)")
     ap.add_argument("--table-levels", type=int, default=0, choices=[0, 3, 5],
                     help="run-aware table rows per node: 5 (windows 1..16), 3 (1, 4, 16), 0 = automatic")
     ap.add_argument("--sharded", action="store_true",
@@ -423,7 +425,8 @@ def run_ours(args, dist: Dist):
                                              warps_per_cta=args.warps, union_mode=args.union_mode,
                                              register_bits=0 if args.register_bits == 8 else args.register_bits,
                                              hub_lookups=args.hub_lookups, table_levels=args.table_levels,
-                                             first_pass=args.first_pass, track_changes=args.track_changes)
+                                             first_pass=args.first_pass, track_changes=args.track_changes,
+                                             group_nodes=args.group_nodes)
         # a forced slice width or table scheme sizes its own workspace
         forced = args.slice_bytes or args.table_levels
         return vga.hyperball_run_dev(g, args.p, d, args.seed, md, ball, workspace=None if forced else ws,
@@ -433,7 +436,7 @@ def run_ours(args, dist: Dist):
                                      register_bits=0 if args.register_bits == 8 else args.register_bits,
                                      hub_lookups=args.hub_lookups, table_levels=args.table_levels,
                                      l2_window=args.l2_window, first_pass=args.first_pass,
-                                     track_changes=args.track_changes)
+                                     track_changes=args.track_changes, group_nodes=args.group_nodes)
 
     for _ in range(args.warmup):
         step(args.d)
@@ -478,7 +481,9 @@ def run_ours(args, dist: Dist):
     src_bytes = N * S * (prof["table_rows"] if mode == 2 else 1)
     l2_stream = vga.vga_bench_gather(max(src_bytes, 1 << 20), S, 64_000_000_000 // S, consumer=2, stream=stream)
     achieved = gather_per_launch / (avg_ms / 1e3) / 1e9
-    kernel_name = f"hb_union_runs_kernel<{S}>" if mode == 2 else f"hb_union_kernel<{S}>"
+    grouped = mode == 2 and args.group_nodes != 1
+    kernel_name = (f"hb_union_groups_kernel<{S}>" if grouped else f"hb_union_runs_kernel<{S}>") if mode == 2 \
+        else f"hb_union_kernel<{S}>"
     traffic, traffic_note = recorded_traffic(kernel_name, args.config)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
@@ -511,6 +516,9 @@ def run_ours(args, dist: Dist):
                                "what": "same microbenchmark folding with the union's bytewise max (no decode)"},
         "algorithmic_bytes_per_launch": gather_per_launch,
         "algorithmic_bytes_definition": (
+            ("distinct table rows of the grouped lookup lists (groups of "
+             f"{args.group_nodes or 4} consecutive nodes, each shared row gathered once) plus the split hubs' "
+             "lookups, x slice_bytes, per slice launch (table build included in the timed launch)") if grouped else
             "range lookups x slice_bytes register-row gathers per slice launch (sparse-table build included in the "
             "timed launch); a lookup covers a run of consecutive neighbour ids" if mode == 2 else
             "E x slice_bytes neighbour-register gathers per slice launch"),
@@ -656,7 +664,7 @@ def run_ours(args, dist: Dist):
             "config": {"workload": CONFIGS[args.config]["name"], "p": args.p, "d": args.d, "seed": args.seed,
                        "N": N, "E": E, "csr_bytes": B, "slice_bytes": S, "union_mode": mode, "order": args.order,
                        "register_bits": args.register_bits, "table_levels": args.table_levels or "auto",
-                       "l2_window": args.l2_window,
+                       "l2_window": args.l2_window, "group_nodes": args.group_nodes or ("auto (4)" if mode == 2 else None),
                        "first_pass": {0: "auto", 1: "gather", 2: "scatter"}[args.first_pass],
                        "track_changes": {0: "auto", 1: "off", 2: "every pass"}[args.track_changes],
                        "autotune": tuned,

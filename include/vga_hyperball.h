@@ -216,6 +216,15 @@ typedef struct vga_tuning {
                             changed fewer than 1 % of the pairs, e.g. the last passes of an
                             unlimited-depth run); 1: off; 2: every pass from the second.
                             Same registers bit for bit.                                    */
+    int group_nodes;     /* mode 2: nodes per group of the grouped union.  Consecutive nodes
+                            see nearly the same runs, so their lookup lists share entries;
+                            each group of this many consecutive (non-hub) nodes gets, on
+                            first use, a merged list of its distinct rows sorted by the set
+                            of its nodes that need them (held by the graph: 4 bytes a
+                            distinct row, about 0.5 byte per edge on city graphs), and one
+                            warp gathers each distinct row once.  2, 4 or 8; 1: one node per
+                            warp from its own lookups; 0: automatic (4).  Split hubs stay
+                            per node.  Same registers bit for bit.                         */
 } vga_tuning;
 
 /*

@@ -33,7 +33,7 @@ class VgaTuning(C.Structure):
     _fields_ = [("slice_bytes", C.c_int), ("warps_per_cta", C.c_int), ("l2_budget_mb", C.c_int),
                 ("union_mode", C.c_int), ("register_bits", C.c_int), ("hub_lookups", C.c_int),
                 ("table_levels", C.c_int), ("l2_window", C.c_int), ("first_pass", C.c_int),
-                ("track_changes", C.c_int)]
+                ("track_changes", C.c_int), ("group_nodes", C.c_int)]
 
 
 class VgaJob(C.Structure):
@@ -164,14 +164,15 @@ def _ptr(a) -> int | None:
 
 
 def _tuning(slice_bytes=0, warps_per_cta=0, l2_budget_mb=0, union_mode=0, register_bits=0, hub_lookups=0,
-            table_levels=0, l2_window=0, first_pass=0, track_changes=0):
+            table_levels=0, l2_window=0, first_pass=0, track_changes=0, group_nodes=0):
     if not (slice_bytes or warps_per_cta or l2_budget_mb or union_mode or register_bits or hub_lookups
-            or table_levels or l2_window or first_pass or track_changes):
+            or table_levels or l2_window or first_pass or track_changes or group_nodes):
         return None
     t = VgaTuning()
     t.slice_bytes, t.warps_per_cta, t.l2_budget_mb, t.union_mode = slice_bytes, warps_per_cta, l2_budget_mb, union_mode
     t.register_bits, t.hub_lookups, t.table_levels = register_bits, hub_lookups, table_levels
     t.l2_window, t.first_pass, t.track_changes = l2_window, first_pass, track_changes
+    t.group_nodes = group_nodes
     return C.pointer(t)
 
 
@@ -326,14 +327,15 @@ def hyperball_run_dev(g: Graph, p: int, d: int, seed: int, mean_depth_dev, ball_
                       workspace=None, stream=None, slice_bytes: int = 0, warps_per_cta: int = 0,
                       l2_budget_mb: int = 0, union_mode: int = 0, register_bits: int = 0,
                       hub_lookups: int = 0, table_levels: int = 0, l2_window: int = 0,
-                      first_pass: int = 0, track_changes: int = 0) -> int:
+                      first_pass: int = 0, track_changes: int = 0, group_nodes: int = 0) -> int:
     """Algorithm 1 into device tensors (float64, N each); returns passes run."""
     it = C.c_int()
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().hyperball_run_dev(g.handle, p, d, seed, conv_mode, _ptr(mean_depth_dev), _ptr(ball_size_dev),
                                    C.byref(it), _ptr(workspace), ws_bytes, _stream_ptr(stream),
                                    _tuning(slice_bytes, warps_per_cta, l2_budget_mb, union_mode, register_bits,
-                                           hub_lookups, table_levels, l2_window, first_pass, track_changes)))
+                                           hub_lookups, table_levels, l2_window, first_pass, track_changes,
+                                           group_nodes)))
     return it.value
 
 
@@ -351,7 +353,7 @@ def hyperball_run_noalloc(g: Graph, p: int, d: int, seed: int, mean_depth_dev, b
 def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int = 0, max_trace: int = 8,
                         slice_bytes: int = 0, warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
                         hub_lookups: int = 0, table_levels: int = 0, first_pass: int = 0,
-                        track_changes: int = 0):
+                        track_changes: int = 0, group_nodes: int = 0):
     """Run with per-pass register and estimate dumps (bit-exact checks).
 
     Returns dict(mean_depth, ball, iterations, regs[(max_trace+1), N, m], c[(max_trace+1), N])."""
@@ -366,7 +368,7 @@ def hyperball_run_trace(g: Graph, p: int, d: int, seed: int = 0, conv_mode: int 
                                      _tuning(slice_bytes, warps_per_cta, union_mode=union_mode,
                                              register_bits=register_bits, hub_lookups=hub_lookups,
                                              table_levels=table_levels, first_pass=first_pass,
-                                             track_changes=track_changes)))
+                                             track_changes=track_changes, group_nodes=group_nodes)))
     return {"mean_depth": md[:n], "ball": ball[:n], "iterations": it.value,
             "regs": regs[: (max_trace + 1) * n * m].reshape(max_trace + 1, n, m),
             "c": cc[: (max_trace + 1) * n].reshape(max_trace + 1, n)}
@@ -576,11 +578,12 @@ class Shard:
 def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, slice_bytes: int = 0,
                      warps_per_cta: int = 0, union_mode: int = 0, register_bits: int = 0,
                      hub_lookups: int = 0, table_levels: int = 0, first_pass: int = 0,
-                     track_changes: int = 0) -> Shard:
+                     track_changes: int = 0, group_nodes: int = 0) -> Shard:
     h = C.c_void_p()
     _check(lib().vga_shard_create(g.handle, p, seed, shard, n_shards,
                                   _tuning(slice_bytes, warps_per_cta, 0, union_mode, register_bits, hub_lookups,
-                                          table_levels, first_pass=first_pass, track_changes=track_changes),
+                                          table_levels, first_pass=first_pass, track_changes=track_changes,
+                                          group_nodes=group_nodes),
                                   C.byref(h)))
     return Shard(h)
 

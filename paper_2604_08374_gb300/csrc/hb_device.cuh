@@ -352,18 +352,6 @@ __device__ __forceinline__ void union_range_runs(const uint32_t *__restrict__ lk
     }
 }
 
-// Run-aware union of the whole node v: next[v] = max(cur[v], max over v's
-// lookups lk[lk_off[v] .. lk_off[v+1]) of their table rows).
-template <int S, bool NIB = false>
-__device__ __forceinline__ void union_node_runs(const uint64_t *__restrict__ lk_off, const uint32_t *__restrict__ lk,
-                                                const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab,
-                                                uint8_t *__restrict__ nxt, uint32_t n, uint32_t v, LkStage &st,
-                                                uint32_t &phase, int lane, uint32_t *flag, int *err) {
-    typename RegFmt<NIB>::Acc acc[4 * GatherShape<S>::V4] = {};
-    union_range_runs<S, NIB>(lk, tab, lk_off[v], lk_off[v + 1], st, phase, lane, acc, err);
-    union_store<S, NIB>(acc, cur, nxt, v, lane, flag);
-}
-
 // Word-wise register max into next[v] for the chunks of a split hub:
 // *p = max(*p, val) field by field, by compare-and-swap.  Every successful
 // swap by another chunk only raises fields, so the loop ends after a few
@@ -416,6 +404,187 @@ __device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc 
         if (chg) chg[v] = 1u;
     }
 }
+
+// ---------------------------------------------------------------------------
+// Lean row gather of the single-graph run-aware union.  Each lane moves CH
+// bytes of a row (16, or 32 from S = 1024 on), G lanes cover a row, P rows
+// share one warp-wide load, U rows per lane are in flight, and a lane group
+// takes U consecutive entries of the staged lookup chunk, read as one vector
+// from shared memory.  Compared with GatherShape this halves the accumulator
+// registers (fewer bytes per lane) and keeps the same bytes in flight, so more
+// warps fit an SM; full steps carry no bounds checks.
+// ---------------------------------------------------------------------------
+template <int S>
+struct LeanShape {
+    static constexpr int CH = S >= 1024 ? 32 : 16;
+    static constexpr int G = S / CH;
+    static constexpr int P = 32 / G;
+    static constexpr int V4 = CH / 16;
+    static constexpr int U = V4 == 1 ? 4 : 2;
+};
+
+// Fold the rows of entries buf[lo .. hi) of a 16-byte-aligned staged chunk
+// into acc; base = the table region plus this lane's byte offset in a row.
+template <int S, bool NIB>
+__device__ __forceinline__ void lean_fold(const uint8_t *__restrict__ base, const uint32_t *buf, int lo, int hi, int g,
+                                          typename RegFmt<NIB>::Acc (&acc)[4 * LeanShape<S>::V4]) {
+    using Sh = LeanShape<S>;
+    using F = RegFmt<NIB>;
+    constexpr int STEP = Sh::P * Sh::U;
+    auto step = [&](int kb, bool check) {
+        uint32_t r[Sh::U];
+        if constexpr (Sh::U == 4) {
+            const uint4 t = *reinterpret_cast<const uint4 *>(buf + kb);
+            r[0] = t.x;
+            r[1] = t.y;
+            r[2] = t.z;
+            r[3] = t.w;
+        } else {
+            const uint2 t = *reinterpret_cast<const uint2 *>(buf + kb);
+            r[0] = t.x;
+            r[1] = t.y;
+        }
+        uint4 x[Sh::U][Sh::V4];
+#pragma unroll
+        for (int u = 0; u < Sh::U; u++) {
+            if (!check || (kb + u >= lo && kb + u < hi)) {
+                load_row_chunk<Sh::V4>(base + (uint64_t)r[u] * S, x[u]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < Sh::V4; q++) x[u][q] = make_uint4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < Sh::U; u += 2)
+#pragma unroll
+            for (int q = 0; q < Sh::V4; q++) {
+                F::fold2(acc[4 * q + 0], x[u][q].x, x[u + 1][q].x);
+                F::fold2(acc[4 * q + 1], x[u][q].y, x[u + 1][q].y);
+                F::fold2(acc[4 * q + 2], x[u][q].z, x[u + 1][q].z);
+                F::fold2(acc[4 * q + 3], x[u][q].w, x[u + 1][q].w);
+            }
+    };
+    // a step covers STEP entries from a multiple of U: a head step that may
+    // start below lo, full steps, a tail step that may end past hi (the
+    // entries outside [lo, hi) are read from the stage but not gathered)
+    int k0 = lo & ~(Sh::U - 1);
+    if (k0 < lo) {
+        const int kb = k0 + g * Sh::U;
+        if (kb < hi) step(kb, true);
+        k0 += STEP;
+    }
+    for (; k0 + STEP <= hi; k0 += STEP) step(k0 + g * Sh::U, false);
+    if (k0 < hi) {
+        const int kb = k0 + g * Sh::U;
+        if (kb < hi) step(kb, true);
+    }
+}
+
+// The split accumulators as register bytes, folded over the warp's P lane
+// groups: every lane ends with the maximum of its CH-byte part of the row.
+template <int S, bool NIB>
+__device__ __forceinline__ void lean_finish(const typename RegFmt<NIB>::Acc (&acc)[4 * LeanShape<S>::V4],
+                                            uint4 (&out)[LeanShape<S>::V4]) {
+    using Sh = LeanShape<S>;
+    using F = RegFmt<NIB>;
+#pragma unroll
+    for (int q = 0; q < Sh::V4; q++)
+        out[q] = make_uint4(F::word(acc[4 * q + 0]), F::word(acc[4 * q + 1]), F::word(acc[4 * q + 2]),
+                            F::word(acc[4 * q + 3]));
+#pragma unroll
+    for (int o = Sh::G; o < 32; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < Sh::V4; q++) {
+            uint4 y;
+            y.x = __shfl_xor_sync(0xffffffffu, out[q].x, o);
+            y.y = __shfl_xor_sync(0xffffffffu, out[q].y, o);
+            y.z = __shfl_xor_sync(0xffffffffu, out[q].z, o);
+            y.w = __shfl_xor_sync(0xffffffffu, out[q].w, o);
+            out[q] = F::max4(out[q], y);
+        }
+}
+
+// Store node v's slice row: max(its gathered maximum nb, cur[v]) into next[v]
+// (by word-wise atomic max for a split hub's chunk, see union_store_hub),
+// setting *flag, and chg[v] when given, if a register changed.  Lanes of
+// group 0 hold the row; every lane takes part in the vote.
+template <int S, bool NIB>
+__device__ __forceinline__ void lean_store(const uint4 (&nb)[LeanShape<S>::V4], const uint8_t *__restrict__ cur,
+                                           uint8_t *__restrict__ nxt, uint32_t v, int lane, bool hub, uint32_t *flag,
+                                           int *err, uint8_t *chg) {
+    using Sh = LeanShape<S>;
+    const int g = lane / Sh::G, sub = lane % Sh::G;
+    bool changed = false;
+    if (g == 0) {
+        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
+        uint4 *dst = reinterpret_cast<uint4 *>(nxt + (uint64_t)v * S + sub * Sh::CH);
+#pragma unroll
+        for (int q = 0; q < Sh::V4; q++) {
+            const uint4 o4 = __ldg(own + q);
+            const uint4 res = RegFmt<NIB>::max4(nb[q], o4);
+            if (hub) {
+                uint32_t *d = reinterpret_cast<uint32_t *>(dst + q);
+                atomic_max_word<NIB>(d + 0, res.x, err);
+                atomic_max_word<NIB>(d + 1, res.y, err);
+                atomic_max_word<NIB>(d + 2, res.z, err);
+                atomic_max_word<NIB>(d + 3, res.w, err);
+            } else {
+                dst[q] = res;
+            }
+            changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
+        }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) {
+        if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
+        if (chg) chg[v] = 1u;
+    }
+}
+
+// Streaming of an item's entries src[b .. e) through the warp's TMA stage, in
+// chunks of kLkChunk entries counted from a0 = b rounded down to a multiple
+// of 4 (the entries before b in that 16-byte group must be readable): the
+// kernel calls stage_start once, then for chunk c = 0, 1, ...: stage_acquire,
+// its own processing of buf(c), stage_release.  Chunk c holds entries
+// [a0 + c kLkChunk, ...) of src.  Bounded waits; a wait that runs out sets
+// *err.  (Explicit loops in the kernels, not a callback: the compiler keeps
+// the fold's state in registers that way.)
+struct StageStream {
+    const uint32_t *src;
+    uint64_t a0;
+    uint32_t total;   // entries from a0, rounded up to a multiple of 4
+    uint32_t chunks;
+    __device__ __forceinline__ StageStream(const uint32_t *src_, uint64_t b, uint64_t e)
+        : src(src_), a0(b & ~3ull), total(0), chunks(0) {
+        if (e > b) {
+            total = (uint32_t)(((e + 3) & ~3ull) - a0);
+            chunks = (total + kLkChunk - 1) / kLkChunk;
+        }
+    }
+    __device__ __forceinline__ void load(LkStage &st, uint32_t c) const {
+        const uint32_t s0 = c * kLkChunk;
+        lk_bulk_load(st, (int)(c & 1u), src + a0 + s0, min(total - s0, (uint32_t)kLkChunk) * 4u);
+    }
+    __device__ __forceinline__ void start(LkStage &st, int lane) const {
+        if (lane == 0)
+            for (uint32_t c = 0; c < 2 && c < chunks; c++) load(st, c);
+    }
+    // wait for chunk c (every lane observes the barrier phase itself: acquire for its reads)
+    __device__ __forceinline__ const uint32_t *acquire(LkStage &st, uint32_t c, uint32_t &phase, int *err,
+                                                       int lane) const {
+        const int slot = (int)(c & 1u);
+        if (!__all_sync(0xffffffffu, lk_wait(st, slot, (phase >> slot) & 1u))) {
+            if (lane == 0) atomicExch(err, 1);
+            lk_wait(st, slot, (phase >> slot) & 1u);  // give an in-flight copy a last chance
+        }
+        phase ^= 1u << slot;
+        return st.buf[slot];
+    }
+    // chunk c consumed: its buffer takes chunk c + 2
+    __device__ __forceinline__ void release(LkStage &st, uint32_t c, int lane) const {
+        __syncwarp();
+        if (lane == 0 && c + 2 < chunks) load(st, c + 2);
+    }
+};
 
 // Keys of the first pass's scatter: node_key repacked as j << KeyFmt<K>::RHO_BITS
 // | rho.  16-bit keys (p <= 10: j < 2^10, rho <= 61 < 2^6) halve the bytes the

@@ -127,42 +127,166 @@ __global__ void __launch_bounds__(512) hb_union_kernel(const uint64_t *__restric
     union_node_edges<S, NIB>(off, bytes, cur, nxt, (uint32_t)warp, s_ids + wib * 32, lane, flags, chg);
 }
 
+// Register cap of the run-aware union kernels: 64 registers a thread lets 8
+// CTAs of 4 warps share an SM (measured faster than the uncapped ~70 on the
+// city workload), and a CTA of up to 1024 threads still launches.
+#define VGA_UNION_MAXNREG 64
+
 // Run-aware Eq. hll-union for one register slice, one warp per work item
-// (RunItem: a whole node, or one chunk of a split hub), lookups staged by TMA,
-// after the slice's sparse table has been built.  flags[2] records a bounded
-// wait that ran out.  With need given (a change-tracked pass), a node whose
-// bit `s` is clear keeps its registers (keep_item); with chg given, changed
-// nodes are recorded in it (the slice's change bytes).
+// (RunItem: a whole node, or one chunk of a split hub), after the slice's
+// table region has been built: the item's range lookups stream through the
+// warp's TMA stage and each lookup's table row is gathered (lean_fold).
+// flags[2] records a bounded wait that ran out.  With need given (a
+// change-tracked pass), a node whose bit `s` is clear keeps its registers
+// (keep_item); with chg given, changed nodes are recorded in it (the slice's
+// change bytes).
 template <int S, bool NIB>
-__global__ void __launch_bounds__(512) hb_union_runs_kernel(const RunItem *__restrict__ items, uint64_t n_items,
-                                                            const uint32_t *__restrict__ lk,
-                                                            const uint8_t *__restrict__ cur,
-                                                            const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt,
-                                                            uint32_t n, uint32_t *__restrict__ flags,
-                                                            const uint32_t *__restrict__ need, int s,
-                                                            uint8_t *__restrict__ chg) {
+__global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_runs_kernel(
+    const RunItem *__restrict__ items, uint64_t n_items, const uint32_t *__restrict__ lk,
+    const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt, uint32_t n,
+    uint32_t *__restrict__ flags, const uint32_t *__restrict__ need, int s, uint8_t *__restrict__ chg) {
+    using Sh = LeanShape<S>;
     extern __shared__ __align__(128) unsigned char s_dyn[];
-    LkStage *stages = reinterpret_cast<LkStage *>(s_dyn);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (warp >= n_items) return;
     const RunItem it = items[warp];
-    if (need && !((need[it.v & ~kHubChunk] >> s) & 1u)) {
-        keep_item<S, NIB>(cur, nxt, it.v & ~kHubChunk, (it.v & kHubChunk) != 0, lane,
-                          reinterpret_cast<int *>(flags + 2));
+    const uint32_t v = it.v & ~kHubChunk;
+    const bool hub = (it.v & kHubChunk) != 0;
+    int *err = reinterpret_cast<int *>(flags + 2);
+    if (need && !((need[v] >> s) & 1u)) {
+        keep_item<S, NIB>(cur, nxt, v, hub, lane, err);
         return;
     }
-    LkStage &st = stages[wib];
+    LkStage &st = reinterpret_cast<LkStage *>(s_dyn)[wib];
     lk_stage_init(st, lane);
     uint32_t phase = 0;
+    typename RegFmt<NIB>::Acc acc[4 * Sh::V4] = {};
+    const int g = lane / Sh::G;
+    const uint8_t *base = tab + (lane % Sh::G) * Sh::CH;
+    const StageStream ss(lk, it.b, it.b + it.cnt);
+    const uint32_t off_b = (uint32_t)(it.b - ss.a0), off_e = off_b + it.cnt;
+    ss.start(st, lane);
+    for (uint32_t c = 0; c < ss.chunks; c++) {
+        const uint32_t *buf = ss.acquire(st, c, phase, err, lane);
+        const uint32_t s0 = c * kLkChunk;
+        const uint32_t lo = max(off_b, s0), hi = min(off_e, s0 + (uint32_t)kLkChunk);
+        if (hi > lo) lean_fold<S, NIB>(base, buf, (int)(lo - s0), (int)(hi - s0), g, acc);
+        ss.release(st, c, lane);
+    }
+    uint4 nb[Sh::V4];
+    lean_finish<S, NIB>(acc, nb);
+    lean_store<S, NIB>(nb, cur, nxt, v, lane, hub, flags, err, chg);
+}
+
+// Grouped run-aware Eq. hll-union for one register slice, one warp per group
+// of NODES consecutive nodes (GroupItem; runs.cu builds the lists): the
+// group's distinct rows stream through the warp's TMA stage class by class;
+// each class's rows are gathered and folded into one accumulator, which at the
+// class's end is reduced over the warp and max-merged into the shared-memory
+// partial rows of the class's nodes.  Finally every node's partial is maxed
+// with its own registers and stored (lean_store).  The maximum over each
+// node's rows is that over its own lookup list, so the registers equal those
+// of hb_union_runs_kernel bit for bit.  With need given, a group none of whose
+// nodes needs slice `s` keeps its registers; otherwise all its nodes are
+// recomputed (a node that needed nothing gets its own registers back).
+// Shared memory per warp: an LkStage, then NODES rows of S bytes.
+template <int S, bool NIB, int NODES>
+__global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_groups_kernel(
+    const GroupItem *__restrict__ items, uint64_t n_items, const uint32_t *__restrict__ rows,
+    const uint2 *__restrict__ cls, const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab,
+    uint8_t *__restrict__ nxt, uint32_t *__restrict__ flags, const uint32_t *__restrict__ need, int s,
+    uint8_t *__restrict__ chg) {
+    using Sh = LeanShape<S>;
+    using F = RegFmt<NIB>;
+    constexpr int W16 = S / 16;  // uint4 words of a slice row
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    const int nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    LkStage &st = reinterpret_cast<LkStage *>(s_dyn)[wib];
+    uint4 *part = reinterpret_cast<uint4 *>(s_dyn + (size_t)nw * sizeof(LkStage)) + (size_t)wib * NODES * W16;
+    const uint64_t warp = (uint64_t)blockIdx.x * nw + wib;
+    if (warp >= n_items) return;
+    const GroupItem &gi = items[warp];  // node ids are read again where needed, not held in registers
+    const uint32_t cnt = gi.cnt, nc = gi.nc;
+    const uint64_t cls0 = gi.cls;
     int *err = reinterpret_cast<int *>(flags + 2);
-    typename RegFmt<NIB>::Acc acc[4 * GatherShape<S>::V4] = {};
-    union_range_runs<S, NIB>(lk, tab, it.b, it.b + it.cnt, st, phase, lane, acc, err);
-    if (it.v & kHubChunk)
-        union_store_hub<S, NIB>(acc, cur, nxt, it.v & ~kHubChunk, lane, flags, err, chg);
-    else
-        union_store<S, NIB>(acc, cur, nxt, it.v, lane, flags, chg);
+    if (need) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < NODES; j++) {
+            const uint32_t v = gi.node[j];
+            any |= v != 0xffffffffu && ((need[v] >> s) & 1u);
+        }
+        if (!any) {
+#pragma unroll
+            for (int j = 0; j < NODES; j++) {
+                const uint32_t v = gi.node[j];
+                if (v != 0xffffffffu) keep_item<S, NIB>(cur, nxt, v, false, lane, err);
+            }
+            return;
+        }
+    }
+    for (int q = lane; q < NODES * W16; q += 32) part[q] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    lk_stage_init(st, lane);
+    uint32_t phase = 0;
+    typename F::Acc acc[4 * Sh::V4] = {};
+    const int g = lane / Sh::G, sub = lane % Sh::G;
+    const uint8_t *base = tab + sub * Sh::CH;
+    if (cnt > 0) {
+        uint32_t ci = 0;
+        uint2 cd = cls[cls0];  // {node mask, rows} of the current class
+        uint32_t cend = cd.y;  // group entry where the current class ends
+        const StageStream ss(rows, gi.b, gi.b + cnt);  // gi.b is a multiple of 4
+        ss.start(st, lane);
+        for (uint32_t c = 0; c < ss.chunks; c++) {
+            const uint32_t *buf = ss.acquire(st, c, phase, err, lane);
+            const uint32_t s0 = c * kLkChunk;
+            uint32_t lo = s0;
+            const uint32_t hi = min(cnt, s0 + (uint32_t)kLkChunk);
+            while (lo < hi) {  // warp-uniform: split the chunk at class ends
+                const uint32_t seg = min(hi, cend);
+                if (seg > lo) lean_fold<S, NIB>(base, buf, (int)(lo - s0), (int)(seg - s0), g, acc);
+                lo = seg;
+                if (lo == cend) {  // the class is complete
+                    uint4 w[Sh::V4];
+                    lean_finish<S, NIB>(acc, w);
+                    if (g == 0) {
+#pragma unroll
+                        for (int j = 0; j < NODES; j++)
+                            if ((cd.x >> j) & 1u)
+#pragma unroll
+                                for (int q = 0; q < Sh::V4; q++) {
+                                    uint4 &pp = part[j * W16 + sub * Sh::V4 + q];
+                                    pp = F::max4(pp, w[q]);
+                                }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = typename F::Acc{};
+                    if (++ci < nc) {
+                        cd = cls[cls0 + ci];
+                        cend += cd.y;
+                    } else {
+                        cend = 0xffffffffu;  // past the last entry: no further class end
+                    }
+                }
+            }
+            ss.release(st, c, lane);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NODES; j++) {
+        const uint32_t v = gi.node[j];
+        if (v == 0xffffffffu) break;
+        uint4 nb[Sh::V4];
+#pragma unroll
+        for (int q = 0; q < Sh::V4; q++) nb[q] = part[j * W16 + sub * Sh::V4 + q];
+        lean_store<S, NIB>(nb, cur, nxt, v, lane, false, flags, err, chg);
+    }
 }
 
 // Change-tracked passes.  The union of pass t records, per slice s, which nodes
@@ -440,6 +564,8 @@ struct Plan {
     uint32_t hub_req = 0;  // runs mode: requested hub threshold (0 = automatic)
     uint32_t hub = 0;      // runs mode: nodes with more lookups than this are split across warps
     RunItemList items;     // runs mode: the union's work list for `hub`
+    int group = 0;         // runs mode: nodes per group of the grouped union (0: one node per warp)
+    GroupList groups;      // runs mode with group > 0: the grouped lookup lists for `hub`
     bool first_scatter = false;  // pass 1 by the scatter of the nodes' keys (kept at off_tab)
     int track = 0;               // runs mode, slices <= 32: change tracking (0 off, 1 automatic, 2 every pass)
     uint64_t n = 0;
@@ -449,6 +575,10 @@ struct Plan {
 };
 
 static uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Group size of the grouped run-aware union when the caller leaves it open:
+// four consecutive nodes (measured fastest of 2, 4 and 8 on the city graph).
+constexpr int kGroupAutoNodes = 4;
 
 // Change tracking keeps one bit per slice in a 32-bit mask per node.
 constexpr int kTrackMaxSlices = 32;
@@ -556,6 +686,12 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         return VGA_EINVAL;
     }
     P->first_scatter = scatter_ok && first != 1;
+    const int grp = tune ? tune->group_nodes : 0;
+    if (grp != 0 && grp != 1 && grp != 2 && grp != 4 && grp != 8) {
+        set_error("group_nodes = %d must be 0 (automatic), 1 (one node per warp), 2, 4 or 8", grp);
+        return VGA_EINVAL;
+    }
+    P->group = P->mode != kModeRuns || grp == 1 ? 0 : grp == 0 ? kGroupAutoNodes : grp;
     const uint64_t regs = (uint64_t)P->n * P->node_bytes;
     uint64_t o = 0;
     P->off_cur = o;   o = align256(o + regs);
@@ -666,8 +802,32 @@ static void launch_union_slice(const Plan &P, const vga_graph *g, const uint8_t 
         const unsigned table_blocks = (unsigned)((P.n + TableShape<SS>::B - 1) / TableShape<SS>::B);
         hb_table_kernel<SS, NIB><<<table_blocks, 256, 0, stream>>>(c, tab, (uint32_t)P.n, P.scheme);
         count_launch();
-        hb_union_runs_kernel<SS, NIB><<<item_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
-            P.items.items, P.items.count, g->lk[P.scheme].d_lk, c, tab, x, (uint32_t)P.n, flags, need, s, chg);
+        if (!P.group) {
+            hb_union_runs_kernel<SS, NIB><<<item_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage), stream>>>(
+                P.items.items, P.items.count, g->lk[P.scheme].d_lk, c, tab, x, (uint32_t)P.n, flags, need, s, chg);
+        } else {
+            // split hubs (the first items of the work list) per node, then the groups
+            if (P.items.hub_items) {
+                const unsigned hub_blocks = (unsigned)((P.items.hub_items + P.warps - 1) / P.warps);
+                hb_union_runs_kernel<SS, NIB><<<hub_blocks, P.warps * 32, (size_t)P.warps * sizeof(LkStage),
+                                                stream>>>(P.items.items, P.items.hub_items, g->lk[P.scheme].d_lk, c,
+                                                          tab, x, (uint32_t)P.n, flags, need, s, chg);
+                count_launch();
+            }
+            const size_t smem = (size_t)P.warps * (sizeof(LkStage) + (size_t)P.group * SS);
+            const unsigned group_blocks = (unsigned)((P.groups.count + P.warps - 1) / P.warps);
+            auto launch_groups = [&](auto kernel) {
+                if (smem > (48u << 10))
+                    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kernel<<<group_blocks, P.warps * 32, smem, stream>>>(P.groups.items, P.groups.count, P.groups.rows,
+                                                                     P.groups.cls, c, tab, x, flags, need, s, chg);
+            };
+            if (group_blocks) {
+                if (P.group == 2) launch_groups(hb_union_groups_kernel<SS, NIB, 2>);
+                else if (P.group == 4) launch_groups(hb_union_groups_kernel<SS, NIB, 4>);
+                else launch_groups(hb_union_groups_kernel<SS, NIB, 8>);
+            }
+        }
     } else {
         hb_union_kernel<SS, NIB><<<blocks, P.warps * 32, smem, stream>>>(g->d_offsets, g->d_bytes, c, x, (uint32_t)P.n,
                                                                     flags, need, s, chg);
@@ -713,7 +873,12 @@ static int launch_union(const Plan &P, const vga_graph *g, const uint8_t *cur, u
         if (timings) {
             VGA_CHECK_CUDA(cudaEventRecord(pt.stop, stream));
             pt.edges = g->n_edges;
-            if (P.mode == kModeRuns) {
+            if (P.mode == kModeRuns && P.group) {
+                // distinct rows of the groups plus the split hubs' lookups
+                pt.gather_bytes = (P.groups.rows_used + P.groups.hub_rows) * (uint64_t)P.S;
+                pt.hbm_bytes = 4 * (P.groups.rows_used + P.groups.hub_rows) + 64 * P.groups.count +
+                               16 * P.items.hub_items + 2 * P.n * (uint64_t)P.S;
+            } else if (P.mode == kModeRuns) {
                 pt.gather_bytes = g->lk[P.scheme].total * (uint64_t)P.S;
                 pt.hbm_bytes = 4 * g->lk[P.scheme].total + 16 * P.items.count + 2 * P.n * (uint64_t)P.S;
             } else {
@@ -958,6 +1123,7 @@ static int run_impl(const vga_graph *g, int p, int d, uint64_t seed, int conv_mo
         VGA_TRY(ensure_run_lookups(g, P.scheme, stream));
         P.hub = hub_threshold(g, P.scheme, P.hub_req);
         VGA_TRY(ensure_run_items(g, P.scheme, P.hub, stream, &P.items));
+        if (P.group) VGA_TRY(ensure_group_list(g, P.scheme, P.hub, P.group, stream, &P.groups));
     }
 
     bool profiling;
@@ -1243,6 +1409,7 @@ int vga_shard_create(const vga_graph *g, int p, uint64_t seed, int shard, int n_
             P.hub = hub_threshold(g, P.scheme, P.hub_req);
             r = ensure_run_items(g, P.scheme, P.hub, 0, &P.items);
         }
+        if (r == VGA_OK && P.group) r = ensure_group_list(g, P.scheme, P.hub, P.group, 0, &P.groups);
         if (r != VGA_OK) {
             delete s;
             return r;

@@ -54,6 +54,80 @@ __global__ void run_lookups_kernel(const uint64_t *__restrict__ off, const uint8
     }
 }
 
+// Merge key of a range lookup: (window start i, slot) from its row index
+// r = slot * n + i.  Within one node's list the window starts strictly
+// increase (the runs ascend and a run's windows start at a, a + w, ...,
+// a + L - w), so every list is sorted by this key.
+__device__ __forceinline__ uint64_t lookup_key(uint32_t r, uint32_t n) {
+    uint32_t slot = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxTableRows; k++) slot += (uint64_t)r >= (uint64_t)k * n ? 1u : 0u;
+    return ((uint64_t)(r - slot * n) << 3) | slot;
+}
+
+// One thread per group of up to NODES nodes: merge the group's lookup lists by
+// key; equal keys (the same row) become one entry whose class is the set of
+// lists holding it.  Without WRITE: count the entries of every class into
+// cc[group << NODES | class].  With WRITE: from those counts, write the
+// group's class descriptors (classes in increasing mask order, empty ones
+// left out) and its rows, sorted by class, at rows[b ...].  Each thread keeps
+// 2^NODES counters or write cursors in shared memory.
+template <int NODES, bool WRITE>
+__global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t n_groups,
+                                   const uint64_t *__restrict__ lk_off, const uint32_t *__restrict__ lk, uint32_t n,
+                                   uint32_t *__restrict__ cc, uint32_t *__restrict__ rows, uint2 *__restrict__ cls) {
+    extern __shared__ uint32_t s_cnt[];
+    constexpr uint32_t C = 1u << NODES;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n_groups) return;
+    uint32_t *c = s_cnt + threadIdx.x * C;
+    const GroupItem &it = items[gid];
+    uint64_t p[NODES], e[NODES], hk[NODES];
+#pragma unroll
+    for (int j = 0; j < NODES; j++) {
+        const uint32_t v = it.node[j];
+        p[j] = v == 0xffffffffu ? 0 : lk_off[v];
+        e[j] = v == 0xffffffffu ? 0 : lk_off[v + 1];
+        hk[j] = p[j] < e[j] ? lookup_key(lk[p[j]], n) : ~0ull;
+    }
+    uint32_t *mine = cc + (gid << NODES);
+    if (WRITE) {
+        uint32_t o = 0;
+        uint64_t ci = it.cls;
+        for (uint32_t k = 1; k < C; k++) {
+            const uint32_t cnt = mine[k];
+            c[k] = o;
+            if (cnt) {
+                cls[ci++] = make_uint2(k, cnt);
+                o += cnt;
+            }
+        }
+    } else {
+        for (uint32_t k = 0; k < C; k++) c[k] = 0;
+    }
+    for (;;) {
+        uint64_t best = ~0ull;
+#pragma unroll
+        for (int j = 0; j < NODES; j++) best = hk[j] < best ? hk[j] : best;
+        if (best == ~0ull) break;
+        uint32_t mask = 0, r = 0;
+#pragma unroll
+        for (int j = 0; j < NODES; j++)
+            if (hk[j] == best) {
+                mask |= 1u << j;
+                r = lk[p[j]];
+                p[j]++;
+                hk[j] = p[j] < e[j] ? lookup_key(lk[p[j]], n) : ~0ull;
+            }
+        if (WRITE)
+            rows[it.b + c[mask]++] = r;
+        else
+            c[mask]++;
+    }
+    if (!WRITE)
+        for (uint32_t k = 0; k < C; k++) mine[k] = c[k];
+}
+
 }  // namespace
 
 uint64_t union_l2_budget(int device) {
@@ -184,6 +258,125 @@ int ensure_run_items(const vga_graph *g, int scheme, uint32_t hub_lookups, cudaS
     L.items.push_back(vga_graph::RunItemSet{hub_lookups, (uint64_t)items.size(), hub_items, hubs, d.release()});
     const vga_graph::RunItemSet &r = L.items.back();
     *out = RunItemList{static_cast<const RunItem *>(r.d_items), r.count, r.hub_items, r.hubs};
+    return VGA_OK;
+}
+
+}  // namespace vga
+
+namespace vga {
+
+int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int nodes, cudaStream_t stream,
+                      GroupList *out) {
+    if (nodes != 2 && nodes != 4 && nodes != 8) {
+        set_error("internal: group size %d", nodes);
+        return VGA_EINVAL;
+    }
+    VGA_TRY(ensure_run_lookups(g, scheme, stream));
+    std::lock_guard<std::mutex> lock(g->lk_mu);
+    if (hub_lookups == 0) hub_lookups = 1;
+    vga_graph::RunLookups &L = g->lk[scheme];
+    auto publish = [&](const vga_graph::RunLookups::GroupSet &gs) {
+        *out = GroupList{static_cast<const GroupItem *>(gs.d_items), gs.count, static_cast<const uint32_t *>(gs.d_rows),
+                         static_cast<const uint2 *>(gs.d_cls), gs.rows_used, gs.hub_rows, gs.nodes};
+    };
+    for (const vga_graph::RunLookups::GroupSet &gs : L.groups)
+        if (gs.hub_lookups == hub_lookups && gs.nodes == nodes) {
+            publish(gs);
+            return VGA_OK;
+        }
+    // groups of consecutive non-hub nodes; a group closes early rather than
+    // hold 2^31 or more lookups (its merged count stays a u32)
+    const std::vector<uint64_t> &off = L.h_off;
+    std::vector<GroupItem> items;
+    GroupItem cur{};
+    int k = 0;
+    uint64_t sum = 0, hub_rows = 0;
+    auto close = [&]() {
+        for (int j = k; j < kGroupMaxNodes; j++) cur.node[j] = 0xffffffffu;
+        items.push_back(cur);
+        cur = GroupItem{};
+        k = 0;
+        sum = 0;
+    };
+    for (uint32_t v = 0; v < g->n; v++) {
+        const uint64_t cnt = off[v + 1] - off[v];
+        if (cnt > hub_lookups) {  // split hubs stay per node
+            hub_rows += cnt;
+            continue;
+        }
+        if (k && sum + cnt >= (1ull << 31)) close();
+        cur.node[k++] = v;
+        sum += cnt;
+        if (k == nodes) close();
+    }
+    if (k) close();
+    const uint64_t ng = items.size();
+    const int threads = nodes >= 8 ? 64 : 128;
+    const size_t smem = (size_t)threads * (4u << nodes);
+    DeviceBuffer d_items, d_cc;
+    VGA_TRY(d_items.alloc(sizeof(GroupItem) * std::max<uint64_t>(ng, 1)));
+    VGA_TRY(d_cc.alloc((4ull << nodes) * std::max<uint64_t>(ng, 1)));
+    auto merge = [&](bool write, uint32_t *rows, uint2 *cls) -> int {
+        if (!ng) return VGA_OK;
+        VGA_CHECK_CUDA(cudaMemcpyAsync(d_items.ptr, items.data(), sizeof(GroupItem) * ng, cudaMemcpyHostToDevice,
+                                       stream));
+        const unsigned blocks = (unsigned)((ng + threads - 1) / threads);
+#define VGA_GM(NN)                                                                                                   \
+    if (write)                                                                                                       \
+        group_merge_kernel<NN, true><<<blocks, threads, smem, stream>>>(d_items.as<GroupItem>(), ng, L.d_off,       \
+                                                                        L.d_lk, g->n, d_cc.as<uint32_t>(), rows, cls); \
+    else                                                                                                             \
+        group_merge_kernel<NN, false><<<blocks, threads, smem, stream>>>(d_items.as<GroupItem>(), ng, L.d_off,      \
+                                                                         L.d_lk, g->n, d_cc.as<uint32_t>(), rows, cls)
+        if (nodes == 2) VGA_GM(2);
+        else if (nodes == 4) VGA_GM(4);
+        else {
+            static std::once_flag once;
+            static cudaError_t attr = cudaSuccess;
+            std::call_once(once, [] {
+                attr = cudaFuncSetAttribute(group_merge_kernel<8, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 4);
+                if (attr == cudaSuccess)
+                    attr = cudaFuncSetAttribute(group_merge_kernel<8, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 4);
+            });
+            VGA_CHECK_CUDA(attr);
+            VGA_GM(8);
+        }
+#undef VGA_GM
+        count_launch();
+        VGA_CHECK_CUDA(cudaGetLastError());
+        return VGA_OK;
+    };
+    VGA_TRY(merge(false, nullptr, nullptr));
+    std::vector<uint32_t> h_cc((size_t)ng << nodes);
+    if (ng) VGA_CHECK_CUDA(cudaMemcpyAsync(h_cc.data(), d_cc.ptr, 4 * h_cc.size(), cudaMemcpyDeviceToHost, stream));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
+    uint64_t rows_total = 0, rows_used = 0, cls_total = 0;
+    for (uint64_t i = 0; i < ng; i++) {
+        uint64_t r = 0;
+        uint32_t nc = 0;
+        for (uint32_t m = 1; m < (1u << nodes); m++) {
+            r += h_cc[(i << nodes) + m];
+            nc += h_cc[(i << nodes) + m] ? 1u : 0u;
+        }
+        items[i].b = rows_total;
+        items[i].cnt = (uint32_t)r;
+        items[i].nc = nc;
+        items[i].cls = cls_total;
+        rows_total += (r + 3) & ~3ull;  // each group's rows start on a 16-byte boundary (TMA)
+        rows_used += r;
+        cls_total += nc;
+    }
+    DeviceBuffer d_rows, d_cls;
+    VGA_TRY(d_rows.alloc(4 * (rows_total + 4)));
+    VGA_CHECK_CUDA(cudaMemsetAsync(d_rows.ptr, 0, 4 * (rows_total + 4), stream));
+    VGA_TRY(d_cls.alloc(sizeof(uint2) * std::max<uint64_t>(cls_total, 1)));
+    VGA_TRY(merge(true, d_rows.as<uint32_t>(), d_cls.as<uint2>()));
+    VGA_CHECK_CUDA(cudaStreamSynchronize(stream));  // the host vectors go out of scope
+    L.groups.push_back(vga_graph::RunLookups::GroupSet{hub_lookups, nodes, ng, rows_total, rows_used, hub_rows,
+                                                       d_items.release(), d_rows.release(), d_cls.release()});
+    publish(L.groups.back());
     return VGA_OK;
 }
 

@@ -42,6 +42,15 @@ struct vga_graph {
         std::vector<uint64_t> h_off;  // prefix sums of the counts (empty until counted)
         bool ready = false;           // d_off and d_lk built
         std::vector<RunItemSet> items;
+        // Grouped lookup lists (ensure_group_list), one per (hub threshold,
+        // group size).
+        struct GroupSet {
+            uint32_t hub_lookups;
+            int nodes;
+            uint64_t count, rows_total, rows_used, hub_rows;
+            void *d_items, *d_rows, *d_cls;
+        };
+        std::vector<GroupSet> groups;
     };
     mutable std::mutex lk_mu;
     mutable RunLookups lk[2];
@@ -148,6 +157,7 @@ struct PinnedBuffer {
 constexpr int kRunLevels = 4;  // widest window 2^4 = 16 rows
 constexpr int kTableSchemes = 2;
 __host__ __device__ constexpr int table_rows(int scheme) { return scheme == 0 ? 5 : 3; }
+constexpr int kMaxTableRows = 5;
 // r < 5 N must fit in 32 bits.
 constexpr uint64_t kRunMaxNodes = 1ull << 29;
 
@@ -177,6 +187,37 @@ struct RunItemList {
     uint32_t hubs = 0;
 };
 int ensure_run_items(const vga_graph *g, int scheme, uint32_t hub_lookups, cudaStream_t stream, RunItemList *out);
+
+// Grouped lookup lists of the run-aware union.  The non-hub nodes, in id
+// order, are cut into groups of up to kGroupMaxNodes consecutive ones;
+// adjacent cells see nearly the same runs, so their lookup lists share many
+// entries (about 40 % of a four-node group's at the city size).  Each group's
+// lists are merged once per graph into its distinct rows, each tagged with
+// its class -- the set of the group's nodes whose list holds it -- and sorted
+// by class.  The union then gathers every distinct row once and folds each
+// class into one accumulator, merged into the partial maxima of the class's
+// nodes when the class ends: the same registers, bit for bit (a max over a
+// union of sets), from fewer gathers and fewer folds.
+constexpr int kGroupMaxNodes = 8;
+struct GroupItem {
+    uint32_t node[kGroupMaxNodes];  // the group's nodes (0xffffffff past its end)
+    uint64_t b;                     // first row entry in rows[] (a multiple of 4)
+    uint32_t cnt;                   // row entries (< 2^31)
+    uint32_t nc;                    // classes
+    uint64_t cls;                   // first class in cls[] (uint2 {node mask, rows}, in row order)
+    uint64_t pad;
+};
+struct GroupList {
+    const GroupItem *items = nullptr;
+    uint64_t count = 0;
+    const uint32_t *rows = nullptr;  // row indices as in the lookup list (+ 4 zero entries)
+    const uint2 *cls = nullptr;
+    uint64_t rows_used = 0;          // row entries over all groups (without the padding)
+    uint64_t hub_rows = 0;           // lookups of the split hubs, which stay per node
+    int nodes = 0;                   // group size
+};
+int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int nodes, cudaStream_t stream,
+                      GroupList *out);
 
 // Automatic hub threshold (lookups per work item): half of one warp's even
 // share of a slice's lookups when every SM holds 64 warps, and at least 2048,

@@ -302,6 +302,11 @@ void vga_graph_free(vga_graph *g) {
         if (L.d_off) cudaFree(L.d_off);
         if (L.d_lk) cudaFree(L.d_lk);
         for (const vga_graph::RunItemSet &r : L.items) cudaFree(r.d_items);
+        for (const vga_graph::RunLookups::GroupSet &gs : L.groups) {
+            cudaFree(gs.d_items);
+            cudaFree(gs.d_rows);
+            cudaFree(gs.d_cls);
+        }
     }
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     delete g;
