@@ -124,26 +124,40 @@ __device__ __forceinline__ bool wait_tables(const uint32_t *done, uint32_t targe
 // same slice width S).  CTAs claim items from the group's queue.  Per job and
 // slice the queue holds, in run-aware jobs (RUNS), first the sparse-table
 // items (TableShape<S>::B rows each, built by the whole CTA) and then the
-// union blocks of kEngineBlock work items (work-list entries: a node, or a
-// chunk of a split hub; in per-neighbour jobs, nodes), whose warps take the
-// block's items one at a time from a shared counter, so that a long item does
+// union blocks of kEngineBlock work units (run-aware jobs: a split hub's chunk,
+// unioned per node, or a group of kEngineGroupNodes consecutive nodes, unioned
+// by the grouped union; per-neighbour jobs: a node), whose warps take the
+// block's units one at a time from a shared counter, so that a long unit does
 // not hold the others back.  A union block starts once its slice's table
 // items are done.  Table items never wait, and every table item of a slice is
-// claimed before any of its union blocks, so each wait ends.
+// claimed before any of its union blocks, so each wait ends.  Small blocks
+// (16 units) over 8-warp CTAs were measured fastest with group units: the
+// warps of a CTA wait for each other at every block's end.
+// Dynamic shared memory of a run-aware union CTA: the warps' TMA stages, their
+// groups' partial rows, then one table item's rows with their halo.
+template <int S>
+constexpr size_t engine_runs_smem() {
+    return (size_t)kEngineWarps * sizeof(LkStage) + (size_t)kEngineWarps * kEngineGroupNodes * S +
+           (size_t)TableShape<S>::R * S;
+}
+
 template <int S, bool RUNS>
 __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *jobs,
                                                                         const uint32_t *__restrict__ gjobs,
                                                                         const uint64_t *__restrict__ item_start,
                                                                         int n_jobs, uint64_t total_items,
                                                                         unsigned long long *counter, int *error) {
-    __shared__ uint32_t s_ids[kEngineWarps][32];
-    __shared__ __align__(16) uint8_t s_tab[RUNS ? TableShape<S>::R * S : 16];
-    __shared__ __align__(128) LkStage s_stage[RUNS ? kEngineWarps : 1];
+    __shared__ uint32_t s_ids[RUNS ? 1 : kEngineWarps][32];
+    extern __shared__ __align__(128) unsigned char s_dyn[];
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_next;
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    LkStage *s_stage = reinterpret_cast<LkStage *>(s_dyn);
+    uint4 *s_part = reinterpret_cast<uint4 *>(s_dyn + (size_t)kEngineWarps * sizeof(LkStage)) +
+                    (size_t)wib * kEngineGroupNodes * (S / 16);
+    uint8_t *s_tab = s_dyn + (size_t)kEngineWarps * sizeof(LkStage) + (size_t)kEngineWarps * kEngineGroupNodes * S;
     uint32_t phase = 0;  // barrier phases of this warp's TMA stage
     if (RUNS) lk_stage_init(s_stage[wib], lane);
     for (;;) {
@@ -159,7 +173,7 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
         JobDev &J = jobs[gjobs[k]];
         if (J.state != 0) continue;
         if (J.first && J.t == 0) continue;  // pass 1 was the scatter (engine_start)
-        const uint32_t ublocks = (J.units + kEngineBlock - 1) / kEngineBlock;
+        const uint32_t ublocks = (J.uunits + kEngineBlock - 1) / kEngineBlock;
         const uint64_t per_slice = (uint64_t)ublocks + (RUNS ? (uint64_t)J.tblocks : 0);
         const uint64_t r = item - item_start[k];
         const uint32_t s = (uint32_t)(r / per_slice);
@@ -187,20 +201,20 @@ __global__ void __launch_bounds__(kEngineWarps * 32) batch_union_kernel(JobDev *
             if (!s_ok) continue;
         }
         const uint32_t u0 = (uint32_t)q * kEngineBlock;
-        const uint32_t u1 = min(u0 + kEngineBlock, J.units);
+        const uint32_t u1 = min(u0 + kEngineBlock, J.uunits);
         for (;;) {
             uint32_t x = 0;
             if (lane == 0) x = atomicAdd(&s_next, 1u);
             x = u0 + __shfl_sync(0xffffffffu, x, 0);
             if (x >= u1) break;
             if (RUNS) {
-                const RunItem it = J.items[x];
-                typename RegFmt<false>::Acc acc[4 * GatherShape<S>::V4] = {};
-                union_range_runs<S>(J.lk, tab, it.b, it.b + it.cnt, s_stage[wib], phase, lane, acc, error);
-                if (it.v & kHubChunk)
-                    union_store_hub<S, false>(acc, cur, nxt, it.v & ~kHubChunk, lane, &J.changed, error);
+                if (x < J.hub_units)  // a split hub's chunk, per node
+                    union_item<S, false>(J.items[x], J.lk, cur, tab, nxt, s_stage[wib], phase, lane, &J.changed,
+                                         error, nullptr);
                 else
-                    union_store<S, false>(acc, cur, nxt, it.v, lane, &J.changed);
+                    union_group<S, false, kEngineGroupNodes>(J.groups[x - J.hub_units], J.grows, J.gcls, cur, tab,
+                                                             nxt, s_part, s_stage[wib], phase, lane, &J.changed,
+                                                             error, nullptr);
             } else {
                 union_node_edges<S>(J.off, J.bytes, cur, nxt, x, s_ids[wib], lane, &J.changed);
             }
@@ -298,12 +312,21 @@ int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const
         RunItemList list;
         VGA_TRY(ensure_run_items(g, L.scheme, hub_lookups ? hub_lookups : hub_lookups_auto(g, L.scheme), stream,
                                  &list));
+        const uint32_t hub = hub_lookups ? hub_lookups : hub_lookups_auto(g, L.scheme);
+        GroupList groups;
+        VGA_TRY(ensure_group_list(g, L.scheme, hub, kEngineGroupNodes, stream, &groups));
         J.lk = g->lk[L.scheme].d_lk;
         J.scheme = L.scheme;
         J.items = list.items;
         J.units = (uint32_t)list.count;
+        J.groups = groups.items;
+        J.grows = groups.rows;
+        J.gcls = groups.cls;
+        J.hub_units = (uint32_t)list.hub_items;
+        J.uunits = (uint32_t)(list.hub_items + groups.count);
     } else {
         J.units = g->n;
+        J.uunits = g->n;
         if (p <= kFirstPassMaxP) J.tab = ws + o;  // the keys of pass 1's scatter (job_layout)
     }
     J.first = p <= kFirstPassMaxP ? 1 : 0;
@@ -373,9 +396,31 @@ EngineArrays engine_arrays_at(uint8_t *base, int cap) {
 int group_index(int mode, int S) { return (mode == 2 ? 7 : 0) + (31 - __builtin_clz((unsigned)S)) - 4; }
 
 template <int S, bool RUNS>
+size_t union_smem() {
+    return RUNS ? engine_runs_smem<S>() : 0;
+}
+
+// Sets the run-aware union kernels' dynamic shared memory limit once.
+int union_smem_attrs() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+#define VGA_A(SS)                                                                                                 \
+    if (err == cudaSuccess)                                                                                       \
+        err = cudaFuncSetAttribute(batch_union_kernel<SS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                   (int)engine_runs_smem<SS>());
+        VGA_A(16) VGA_A(32) VGA_A(64) VGA_A(128) VGA_A(256) VGA_A(512) VGA_A(1024)
+#undef VGA_A
+    });
+    VGA_CHECK_CUDA(err);
+    return VGA_OK;
+}
+
+template <int S, bool RUNS>
 int union_grid(int sms) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_union_kernel<S, RUNS>, kEngineWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_union_kernel<S, RUNS>, kEngineWarps * 32,
+                                                  union_smem<S, RUNS>());
     return std::max(1, sms * std::max(1, per_sm));
 }
 
@@ -399,6 +444,7 @@ int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, Engine
         set_error("internal: %d jobs exceed the engine capacity %d", nj, A.cap);
         return VGA_EINVAL;
     }
+    VGA_TRY(union_smem_attrs());
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -423,7 +469,7 @@ int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, Engine
             gj.push_back(k);
             is.push_back(items);
             const JobDev &J = jobs[k];
-            items += (uint64_t)J.slices * ((uint64_t)((J.units + kEngineBlock - 1) / kEngineBlock) +
+            items += (uint64_t)J.slices * ((uint64_t)((J.uunits + kEngineBlock - 1) / kEngineBlock) +
                                            (J.mode == 2 ? (uint64_t)J.tblocks : 0));
         }
         is.push_back(items);
@@ -531,24 +577,58 @@ int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const E
 template <int S, bool RUNS>
 void launch_group(const EngineArrays &A, const EngineGroup &G, cudaStream_t stream, int grid_pct) {
     const unsigned grid = (grid_pct > 0 && grid_pct < 100) ? std::max(1u, G.grid * (unsigned)grid_pct / 100u) : G.grid;
-    batch_union_kernel<S, RUNS><<<grid, kEngineWarps * 32, 0, stream>>>(A.jobs, A.gjobs + G.gjob_off,
+    batch_union_kernel<S, RUNS><<<grid, kEngineWarps * 32, union_smem<S, RUNS>(), stream>>>(A.jobs, A.gjobs + G.gjob_off,
                                                                          A.item_start + G.item_off, G.n,
                                                                          G.total_items, A.counters + G.index, A.error);
 }
 
+EngineForks::~EngineForks() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaStream_t s : streams) cudaStreamDestroy(s);
+}
+
+int EngineForks::ensure(int n) {
+    while ((int)streams.size() < n) {
+        cudaStream_t s = nullptr;
+        VGA_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        streams.push_back(s);
+    }
+    while ((int)events.size() < n + 1) {
+        cudaEvent_t e = nullptr;
+        VGA_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        events.push_back(e);
+    }
+    return VGA_OK;
+}
+
 int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, cudaGraphConditionalHandle cond,
-                int use_cond, int grid_pct) {
+                int use_cond, int grid_pct, EngineForks *forks) {
+    // the union kernels of different slice widths touch different jobs: with
+    // forks they run side by side, so one kernel's tail overlaps the others
+    const int n_aux = forks ? (int)E.groups.size() - 1 : 0;
+    if (n_aux > 0) {
+        VGA_TRY(forks->ensure(n_aux));
+        VGA_CHECK_CUDA(cudaEventRecord(forks->events[0], stream));
+        for (int k = 0; k < n_aux; k++) VGA_CHECK_CUDA(cudaStreamWaitEvent(forks->streams[k], forks->events[0], 0));
+    }
+    int gi = 0;
     for (const EngineGroup &G : E.groups) {
+        cudaStream_t gs = (n_aux > 0 && gi > 0) ? forks->streams[gi - 1] : stream;
+        gi++;
 #define VGA_G(SS)                                                                         \
     case SS:                                                                              \
-        if (G.mode == 2) launch_group<SS, true>(A, G, stream, grid_pct);                  \
-        else launch_group<SS, false>(A, G, stream, grid_pct);                             \
+        if (G.mode == 2) launch_group<SS, true>(A, G, gs, grid_pct);                      \
+        else launch_group<SS, false>(A, G, gs, grid_pct);                                 \
         break;
         switch (G.S) {
             VGA_G(16) VGA_G(32) VGA_G(64) VGA_G(128) VGA_G(256) VGA_G(512) VGA_G(1024)
         }
 #undef VGA_G
         count_launch();
+    }
+    for (int k = 0; k < n_aux; k++) {
+        VGA_CHECK_CUDA(cudaEventRecord(forks->events[1 + k], forks->streams[k]));
+        VGA_CHECK_CUDA(cudaStreamWaitEvent(stream, forks->events[1 + k], 0));
     }
     batch_estimate_kernel<<<E.grid_warps, 256, 0, stream>>>(A.jobs, A.node_start, E.n_jobs, E.total_nodes, 0);
     count_launch();
@@ -562,7 +642,7 @@ int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, 
 
 // Capture one pass as the body of a WHILE conditional node and run it until
 // no job is running.
-int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t stream) {
+int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, EngineForks *forks) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     VGA_CHECK_CUDA(cudaGraphCreate(&graph, 0));
@@ -589,7 +669,7 @@ int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t str
     int rc = VGA_OK;
     cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        rc = engine_pass(A, E, cap, cond, 1);
+        rc = engine_pass(A, E, cap, cond, 1, 100, forks);
         cudaGraph_t captured = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &captured);
         if (rc == VGA_OK && e2 != cudaSuccess) {
@@ -699,14 +779,15 @@ int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaSt
     }
     const EngineArrays A = engine_arrays_at(ws + B.off_arrays, (int)host.size());
     EngineSet E;
+    EngineForks forks;
     VGA_TRY(engine_upload(A, host, &E, stream));
     VGA_TRY(engine_start(A, host, E, stream));
     if (use_graph) {
-        VGA_TRY(engine_run_graph(A, E, stream));
+        VGA_TRY(engine_run_graph(A, E, stream));  // forks measured slower inside the WHILE body
     } else {
         int running = 1;
         while (running) {
-            VGA_TRY(engine_pass(A, E, stream, 0, 0, 100));
+            VGA_TRY(engine_pass(A, E, stream, 0, 0, 100, &forks));
             VGA_CHECK_CUDA(cudaMemcpyAsync(&running, A.any_running, sizeof(int), cudaMemcpyDeviceToHost, stream));
             VGA_CHECK_CUDA(cudaStreamSynchronize(stream));
         }

@@ -8,8 +8,9 @@
 
 namespace vga {
 
-constexpr int kEngineWarps = 16;
-constexpr uint32_t kEngineBlock = 64;  // work items per union block of the queue
+constexpr int kEngineWarps = 8;
+constexpr int kEngineGroupNodes = 4;  // nodes per group of the grouped union in the engine
+constexpr uint32_t kEngineBlock = 16;  // work units (hub chunks, node groups) per union block of the queue
 constexpr int kGroups = 14;  // union kernels: (per neighbour | per run) x slice width 16..1024
 
 // One analysis as the batched kernels see it (device memory).
@@ -30,7 +31,13 @@ struct JobDev {
     uint64_t seed;
     uint32_t n;
     int p, S, slices, d, conv;
-    uint32_t units;         // union items per slice: work-list entries (mode 2) or nodes (mode 1)
+    uint32_t units;         // pass-1 scatter units: work-list entries (mode 2) or nodes (mode 1)
+    // mode 2: the grouped union (groups of kGroupAutoNodes consecutive nodes)
+    const GroupItem *groups;
+    const uint32_t *grows;
+    const uint2 *gcls;
+    uint32_t hub_units;     // mode 2: split-hub chunks, the first work-list entries, unioned per node
+    uint32_t uunits;        // union units per slice: hub chunks then groups (mode 2), or nodes (mode 1)
     int mode;               // 1 one gather per neighbour, 2 per run (sparse tables)
     int tblocks;            // table items per slice (mode 2), TableShape<S>::B rows each
     int scheme;             // table scheme of the lookups (mode 2)
@@ -92,10 +99,22 @@ uint64_t engine_arrays_bytes(int cap);
 EngineArrays engine_arrays_at(uint8_t *base, int cap);
 int engine_upload(const EngineArrays &A, const std::vector<JobDev> &jobs, EngineSet *E, cudaStream_t stream);
 int engine_start(const EngineArrays &A, const std::vector<JobDev> &jobs, const EngineSet &E, cudaStream_t stream);
+// Auxiliary streams and events with which engine_pass runs the union kernels
+// of different slice widths concurrently (fork from the pass's stream, join
+// before the estimate): created on first use, destroyed with the object.
+struct EngineForks {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;  // [0]: the fork; [1 + k]: stream k's join
+    EngineForks() = default;
+    EngineForks(const EngineForks &) = delete;
+    EngineForks &operator=(const EngineForks &) = delete;
+    ~EngineForks();
+    int ensure(int n);  // at least n auxiliary streams
+};
 // One pass of every uploaded job.  grid_pct < 100 runs the union kernels on
 // that share of their usual grid (the server's solo-lane priority).
 int engine_pass(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, cudaGraphConditionalHandle cond,
-                int use_cond, int grid_pct = 100);
-int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t stream);
+                int use_cond, int grid_pct = 100, EngineForks *forks = nullptr);
+int engine_run_graph(const EngineArrays &A, const EngineSet &E, cudaStream_t stream, EngineForks *forks = nullptr);
 
 }  // namespace vga

@@ -586,6 +586,115 @@ struct StageStream {
     }
 };
 
+// Run-aware Eq. hll-union of one work item (a whole node, or one chunk of a
+// split hub) for one register slice whose table region `tab` has been built:
+// the item's range lookups stream through the warp's TMA stage `st` (barrier
+// phases in `phase`) and each lookup's table row is gathered (lean_fold);
+// then next[v] = max(gathered, cur[v]) (lean_store).
+template <int S, bool NIB>
+__device__ __forceinline__ void union_item(const RunItem &it, const uint32_t *__restrict__ lk,
+                                           const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab,
+                                           uint8_t *__restrict__ nxt, LkStage &st, uint32_t &phase, int lane,
+                                           uint32_t *flag, int *err, uint8_t *chg) {
+    using Sh = LeanShape<S>;
+    const uint32_t v = it.v & ~kHubChunk;
+    const bool hub = (it.v & kHubChunk) != 0;
+    typename RegFmt<NIB>::Acc acc[4 * Sh::V4] = {};
+    const int g = lane / Sh::G;
+    const uint8_t *base = tab + (lane % Sh::G) * Sh::CH;
+    const StageStream ss(lk, it.b, it.b + it.cnt);
+    const uint32_t off_b = (uint32_t)(it.b - ss.a0), off_e = off_b + it.cnt;
+    ss.start(st, lane);
+    for (uint32_t c = 0; c < ss.chunks; c++) {
+        const uint32_t *buf = ss.acquire(st, c, phase, err, lane);
+        const uint32_t s0 = c * kLkChunk;
+        const uint32_t lo = max(off_b, s0), hi = min(off_e, s0 + (uint32_t)kLkChunk);
+        if (hi > lo) lean_fold<S, NIB>(base, buf, (int)(lo - s0), (int)(hi - s0), g, acc);
+        ss.release(st, c, lane);
+    }
+    uint4 nb[Sh::V4];
+    lean_finish<S, NIB>(acc, nb);
+    lean_store<S, NIB>(nb, cur, nxt, v, lane, hub, flag, err, chg);
+}
+
+// Grouped run-aware Eq. hll-union of one group of NODES consecutive nodes
+// (GroupItem, runs.cu) for one register slice: the group's distinct rows
+// stream through the warp's TMA stage class by class; each class's rows are
+// gathered and folded into one accumulator, which at the class's end is
+// reduced over the warp and max-merged into the partial rows `part` (NODES x S
+// bytes of this warp's shared memory) of the class's nodes.  Finally every
+// node's partial is maxed with its own registers and stored (lean_store).  The
+// maximum over each node's rows is that over its own lookup list, so the
+// registers equal those of union_item bit for bit.
+template <int S, bool NIB, int NODES>
+__device__ __forceinline__ void union_group(const GroupItem &gi, const uint32_t *__restrict__ rows,
+                                            const uint2 *__restrict__ cls, const uint8_t *__restrict__ cur,
+                                            const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt, uint4 *part,
+                                            LkStage &st, uint32_t &phase, int lane, uint32_t *flag, int *err,
+                                            uint8_t *chg) {
+    using Sh = LeanShape<S>;
+    using F = RegFmt<NIB>;
+    constexpr int W16 = S / 16;  // uint4 words of a slice row
+    const uint32_t cnt = gi.cnt, nc = gi.nc;
+    const uint64_t cls0 = gi.cls;
+    for (int q = lane; q < NODES * W16; q += 32) part[q] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    typename F::Acc acc[4 * Sh::V4] = {};
+    const int g = lane / Sh::G, sub = lane % Sh::G;
+    const uint8_t *base = tab + sub * Sh::CH;
+    if (cnt > 0) {
+        uint32_t ci = 0;
+        uint2 cd = cls[cls0];  // {node mask, rows} of the current class
+        uint32_t cend = cd.y;  // group entry where the current class ends
+        const StageStream ss(rows, gi.b, gi.b + cnt);  // gi.b is a multiple of 4
+        ss.start(st, lane);
+        for (uint32_t c = 0; c < ss.chunks; c++) {
+            const uint32_t *buf = ss.acquire(st, c, phase, err, lane);
+            const uint32_t s0 = c * kLkChunk;
+            uint32_t lo = s0;
+            const uint32_t hi = min(cnt, s0 + (uint32_t)kLkChunk);
+            while (lo < hi) {  // warp-uniform: split the chunk at class ends
+                const uint32_t seg = min(hi, cend);
+                if (seg > lo) lean_fold<S, NIB>(base, buf, (int)(lo - s0), (int)(seg - s0), g, acc);
+                lo = seg;
+                if (lo == cend) {  // the class is complete
+                    uint4 w[Sh::V4];
+                    lean_finish<S, NIB>(acc, w);
+                    if (g == 0) {
+#pragma unroll
+                        for (int j = 0; j < NODES; j++)
+                            if ((cd.x >> j) & 1u)
+#pragma unroll
+                                for (int q = 0; q < Sh::V4; q++) {
+                                    uint4 &pp = part[j * W16 + sub * Sh::V4 + q];
+                                    pp = F::max4(pp, w[q]);
+                                }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = typename F::Acc{};
+                    if (++ci < nc) {
+                        cd = cls[cls0 + ci];
+                        cend += cd.y;
+                    } else {
+                        cend = 0xffffffffu;  // past the last entry: no further class end
+                    }
+                }
+            }
+            ss.release(st, c, lane);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NODES; j++) {
+        const uint32_t v = gi.node[j];  // read again here, not held in registers through the loop
+        if (v == 0xffffffffu) break;
+        uint4 nb[Sh::V4];
+#pragma unroll
+        for (int q = 0; q < Sh::V4; q++) nb[q] = part[j * W16 + sub * Sh::V4 + q];
+        lean_store<S, NIB>(nb, cur, nxt, v, lane, false, flag, err, chg);
+    }
+}
+
 // Keys of the first pass's scatter: node_key repacked as j << KeyFmt<K>::RHO_BITS
 // | rho.  16-bit keys (p <= 10: j < 2^10, rho <= 61 < 2^6) halve the bytes the
 // scatter reads; wider precisions keep the 32-bit form.
@@ -864,17 +973,15 @@ __device__ __forceinline__ void harmonic_partial(const uint8_t *__restrict__ reg
         const uint32_t s = rel / (uint32_t)S, o = rel % (uint32_t)S;
         const uint4 x = *reinterpret_cast<const uint4 *>(regs + ((uint64_t)s * n + v) * (uint64_t)S + o);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+        // A lane adds at most m / 32 terms of at most 2^(K-1) = 2^(64-p) each in
+        // this loop, so its sum stays below 2^59: no carry into hi here.
 #pragma unroll
         for (int i = 0; i < 4; i++)
+#pragma unroll
             for (int b = 0; b < fields; b++) {
                 const uint32_t M = (wv[i] >> (width * b)) & fmask;
-                if (M == 0) {
-                    zeros++;
-                } else {
-                    const uint64_t term = 1ull << (K - (int)M);
-                    lo += term;
-                    hi += (lo < term);
-                }
+                zeros += M == 0u ? 1u : 0u;
+                lo += M == 0u ? 0ull : 1ull << (K - (int)M);
             }
     }
 #pragma unroll

@@ -145,7 +145,6 @@ __global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_runs_kernel(
     const RunItem *__restrict__ items, uint64_t n_items, const uint32_t *__restrict__ lk,
     const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab, uint8_t *__restrict__ nxt, uint32_t n,
     uint32_t *__restrict__ flags, const uint32_t *__restrict__ need, int s, uint8_t *__restrict__ chg) {
-    using Sh = LeanShape<S>;
     extern __shared__ __align__(128) unsigned char s_dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -162,22 +161,7 @@ __global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_runs_kernel(
     LkStage &st = reinterpret_cast<LkStage *>(s_dyn)[wib];
     lk_stage_init(st, lane);
     uint32_t phase = 0;
-    typename RegFmt<NIB>::Acc acc[4 * Sh::V4] = {};
-    const int g = lane / Sh::G;
-    const uint8_t *base = tab + (lane % Sh::G) * Sh::CH;
-    const StageStream ss(lk, it.b, it.b + it.cnt);
-    const uint32_t off_b = (uint32_t)(it.b - ss.a0), off_e = off_b + it.cnt;
-    ss.start(st, lane);
-    for (uint32_t c = 0; c < ss.chunks; c++) {
-        const uint32_t *buf = ss.acquire(st, c, phase, err, lane);
-        const uint32_t s0 = c * kLkChunk;
-        const uint32_t lo = max(off_b, s0), hi = min(off_e, s0 + (uint32_t)kLkChunk);
-        if (hi > lo) lean_fold<S, NIB>(base, buf, (int)(lo - s0), (int)(hi - s0), g, acc);
-        ss.release(st, c, lane);
-    }
-    uint4 nb[Sh::V4];
-    lean_finish<S, NIB>(acc, nb);
-    lean_store<S, NIB>(nb, cur, nxt, v, lane, hub, flags, err, chg);
+    union_item<S, NIB>(it, lk, cur, tab, nxt, st, phase, lane, flags, err, chg);
 }
 
 // Grouped run-aware Eq. hll-union for one register slice, one warp per group
@@ -198,8 +182,6 @@ __global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_groups_kernel(
     const uint2 *__restrict__ cls, const uint8_t *__restrict__ cur, const uint8_t *__restrict__ tab,
     uint8_t *__restrict__ nxt, uint32_t *__restrict__ flags, const uint32_t *__restrict__ need, int s,
     uint8_t *__restrict__ chg) {
-    using Sh = LeanShape<S>;
-    using F = RegFmt<NIB>;
     constexpr int W16 = S / 16;  // uint4 words of a slice row
     extern __shared__ __align__(128) unsigned char s_dyn[];
     const int nw = blockDim.x >> 5;
@@ -210,8 +192,6 @@ __global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_groups_kernel(
     const uint64_t warp = (uint64_t)blockIdx.x * nw + wib;
     if (warp >= n_items) return;
     const GroupItem &gi = items[warp];  // node ids are read again where needed, not held in registers
-    const uint32_t cnt = gi.cnt, nc = gi.nc;
-    const uint64_t cls0 = gi.cls;
     int *err = reinterpret_cast<int *>(flags + 2);
     if (need) {
         bool any = false;
@@ -229,64 +209,9 @@ __global__ void __maxnreg__(VGA_UNION_MAXNREG) hb_union_groups_kernel(
             return;
         }
     }
-    for (int q = lane; q < NODES * W16; q += 32) part[q] = make_uint4(0, 0, 0, 0);
-    __syncwarp();
     lk_stage_init(st, lane);
     uint32_t phase = 0;
-    typename F::Acc acc[4 * Sh::V4] = {};
-    const int g = lane / Sh::G, sub = lane % Sh::G;
-    const uint8_t *base = tab + sub * Sh::CH;
-    if (cnt > 0) {
-        uint32_t ci = 0;
-        uint2 cd = cls[cls0];  // {node mask, rows} of the current class
-        uint32_t cend = cd.y;  // group entry where the current class ends
-        const StageStream ss(rows, gi.b, gi.b + cnt);  // gi.b is a multiple of 4
-        ss.start(st, lane);
-        for (uint32_t c = 0; c < ss.chunks; c++) {
-            const uint32_t *buf = ss.acquire(st, c, phase, err, lane);
-            const uint32_t s0 = c * kLkChunk;
-            uint32_t lo = s0;
-            const uint32_t hi = min(cnt, s0 + (uint32_t)kLkChunk);
-            while (lo < hi) {  // warp-uniform: split the chunk at class ends
-                const uint32_t seg = min(hi, cend);
-                if (seg > lo) lean_fold<S, NIB>(base, buf, (int)(lo - s0), (int)(seg - s0), g, acc);
-                lo = seg;
-                if (lo == cend) {  // the class is complete
-                    uint4 w[Sh::V4];
-                    lean_finish<S, NIB>(acc, w);
-                    if (g == 0) {
-#pragma unroll
-                        for (int j = 0; j < NODES; j++)
-                            if ((cd.x >> j) & 1u)
-#pragma unroll
-                                for (int q = 0; q < Sh::V4; q++) {
-                                    uint4 &pp = part[j * W16 + sub * Sh::V4 + q];
-                                    pp = F::max4(pp, w[q]);
-                                }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4 * Sh::V4; q++) acc[q] = typename F::Acc{};
-                    if (++ci < nc) {
-                        cd = cls[cls0 + ci];
-                        cend += cd.y;
-                    } else {
-                        cend = 0xffffffffu;  // past the last entry: no further class end
-                    }
-                }
-            }
-            ss.release(st, c, lane);
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < NODES; j++) {
-        const uint32_t v = gi.node[j];
-        if (v == 0xffffffffu) break;
-        uint4 nb[Sh::V4];
-#pragma unroll
-        for (int q = 0; q < Sh::V4; q++) nb[q] = part[j * W16 + sub * Sh::V4 + q];
-        lean_store<S, NIB>(nb, cur, nxt, v, lane, false, flags, err, chg);
-    }
+    union_group<S, NIB, NODES>(gi, rows, cls, cur, tab, nxt, part, st, phase, lane, flags, err, chg);
 }
 
 // Change-tracked passes.  The union of pass t records, per slice s, which nodes

@@ -65,45 +65,105 @@ __device__ __forceinline__ uint64_t lookup_key(uint32_t r, uint32_t n) {
     return ((uint64_t)(r - slot * n) << 3) | slot;
 }
 
-// One thread per group of up to NODES nodes: merge the group's lookup lists by
+// First index of list[0 .. len) whose key is >= k (the list is sorted by key).
+__device__ __forceinline__ uint32_t key_lower_bound(const uint32_t *__restrict__ list, uint32_t len, uint64_t k,
+                                                    uint32_t n) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (lookup_key(list[mid], n) < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One warp per group of up to NODES nodes: merge the group's lookup lists by
 // key; equal keys (the same row) become one entry whose class is the set of
-// lists holding it.  Without WRITE: count the entries of every class into
-// cc[group << NODES | class].  With WRITE: from those counts, write the
-// group's class descriptors (classes in increasing mask order, empty ones
-// left out) and its rows, sorted by class, at rows[b ...].  Each thread keeps
-// 2^NODES counters or write cursors in shared memory.
+// lists holding it.  The key space is split among the lanes at 31 keys
+// sampled evenly from the group's longest list, and every lane merges its own
+// key range serially.  Without WRITE: count the group's entries of every class
+// into cc[group << NODES | class].  With WRITE: from those counts, write the
+// group's class descriptors (classes in increasing mask order, empty ones left
+// out) and its rows, sorted by class (within a class by key), at rows[b ...].
+// Shared memory: 2^NODES counters or write cursors per lane.
 template <int NODES, bool WRITE>
 __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t n_groups,
                                    const uint64_t *__restrict__ lk_off, const uint32_t *__restrict__ lk, uint32_t n,
                                    uint32_t *__restrict__ cc, uint32_t *__restrict__ rows, uint2 *__restrict__ cls) {
     extern __shared__ uint32_t s_cnt[];
     constexpr uint32_t C = 1u << NODES;
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gid >= n_groups) return;
-    uint32_t *c = s_cnt + threadIdx.x * C;
+    uint32_t *c = s_cnt + (threadIdx.x >> 5) * (C * 32) + lane;  // c[k * 32]: this lane's counter of class k
     const GroupItem &it = items[gid];
-    uint64_t p[NODES], e[NODES], hk[NODES];
+    const uint32_t *list[NODES];
+    uint32_t len[NODES];
+    uint32_t longest = 0;
 #pragma unroll
     for (int j = 0; j < NODES; j++) {
         const uint32_t v = it.node[j];
-        p[j] = v == 0xffffffffu ? 0 : lk_off[v];
-        e[j] = v == 0xffffffffu ? 0 : lk_off[v + 1];
-        hk[j] = p[j] < e[j] ? lookup_key(lk[p[j]], n) : ~0ull;
+        const uint64_t o = v == 0xffffffffu ? 0 : lk_off[v];
+        list[j] = lk + o;
+        len[j] = v == 0xffffffffu ? 0u : (uint32_t)(lk_off[v + 1] - o);
+        if (len[j] > len[longest]) longest = j;
+    }
+    // this lane's key range [k0, k1)
+    const uint32_t L = len[longest];
+    uint64_t k0 = lane == 0 || L == 0 ? 0ull : lookup_key(list[longest][(uint32_t)((uint64_t)L * lane / 32)], n);
+    uint64_t k1 = __shfl_down_sync(0xffffffffu, k0, 1);
+    if (lane == 31) k1 = ~0ull;
+    uint32_t p[NODES], e[NODES];
+    uint64_t hk[NODES];
+#pragma unroll
+    for (int j = 0; j < NODES; j++) {
+        p[j] = k0 == 0 ? 0u : key_lower_bound(list[j], len[j], k0, n);
+        e[j] = k1 == ~0ull ? len[j] : key_lower_bound(list[j], len[j], k1, n);
+        hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
     }
     uint32_t *mine = cc + (gid << NODES);
+    for (uint32_t k = 0; k < C; k++) c[k * 32] = 0;
     if (WRITE) {
-        uint32_t o = 0;
+        // this lane's cursor in class k: the class's base (classes in mask
+        // order) plus the counts of the lower lanes, found by a second merge
+        // pass that only counts
+        for (;;) {
+            uint64_t best = ~0ull;
+#pragma unroll
+            for (int j = 0; j < NODES; j++) best = hk[j] < best ? hk[j] : best;
+            if (best == ~0ull) break;
+            uint32_t mask = 0;
+#pragma unroll
+            for (int j = 0; j < NODES; j++)
+                if (hk[j] == best) {
+                    mask |= 1u << j;
+                    p[j]++;
+                    hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
+                }
+            c[mask * 32]++;
+        }
+        uint32_t base = 0;
         uint64_t ci = it.cls;
         for (uint32_t k = 1; k < C; k++) {
-            const uint32_t cnt = mine[k];
-            c[k] = o;
-            if (cnt) {
-                cls[ci++] = make_uint2(k, cnt);
-                o += cnt;
+            const uint32_t total = mine[k];
+            if (total == 0) continue;  // warp-uniform
+            uint32_t mycount = c[k * 32], excl = mycount;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, excl, o);
+                if (lane >= o) excl += y;
             }
+            c[k * 32] = base + excl - mycount;
+            if (lane == 0) cls[ci] = make_uint2(k, total);
+            ci++;
+            base += total;
         }
-    } else {
-        for (uint32_t k = 0; k < C; k++) c[k] = 0;
+        // merge again, writing
+#pragma unroll
+        for (int j = 0; j < NODES; j++) {
+            p[j] = k0 == 0 ? 0u : key_lower_bound(list[j], len[j], k0, n);
+            hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
+        }
     }
     for (;;) {
         uint64_t best = ~0ull;
@@ -115,17 +175,22 @@ __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t
         for (int j = 0; j < NODES; j++)
             if (hk[j] == best) {
                 mask |= 1u << j;
-                r = lk[p[j]];
+                r = list[j][p[j]];
                 p[j]++;
-                hk[j] = p[j] < e[j] ? lookup_key(lk[p[j]], n) : ~0ull;
+                hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
             }
         if (WRITE)
-            rows[it.b + c[mask]++] = r;
+            rows[it.b + c[mask * 32]++] = r;
         else
-            c[mask]++;
+            c[mask * 32]++;
     }
-    if (!WRITE)
-        for (uint32_t k = 0; k < C; k++) mine[k] = c[k];
+    if (!WRITE) {
+        __syncwarp();
+        for (uint32_t k = 0; k < C; k++) {
+            const uint32_t t = __reduce_add_sync(0xffffffffu, c[k * 32]);
+            if (lane == 0) mine[k] = t;
+        }
+    }
 }
 
 }  // namespace
@@ -311,8 +376,8 @@ int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int 
     }
     if (k) close();
     const uint64_t ng = items.size();
-    const int threads = nodes >= 8 ? 64 : 128;
-    const size_t smem = (size_t)threads * (4u << nodes);
+    const int warps = nodes >= 8 ? 1 : 4;  // one warp per group; 32 lanes x 2^nodes counters each
+    const size_t smem = (size_t)warps * 32 * (4u << nodes);
     DeviceBuffer d_items, d_cc;
     VGA_TRY(d_items.alloc(sizeof(GroupItem) * std::max<uint64_t>(ng, 1)));
     VGA_TRY(d_cc.alloc((4ull << nodes) * std::max<uint64_t>(ng, 1)));
@@ -320,7 +385,8 @@ int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int 
         if (!ng) return VGA_OK;
         VGA_CHECK_CUDA(cudaMemcpyAsync(d_items.ptr, items.data(), sizeof(GroupItem) * ng, cudaMemcpyHostToDevice,
                                        stream));
-        const unsigned blocks = (unsigned)((ng + threads - 1) / threads);
+        const unsigned blocks = (unsigned)((ng + warps - 1) / warps);
+        const int threads = warps * 32;
 #define VGA_GM(NN)                                                                                                   \
     if (write)                                                                                                       \
         group_merge_kernel<NN, true><<<blocks, threads, smem, stream>>>(d_items.as<GroupItem>(), ng, L.d_off,       \
@@ -335,10 +401,10 @@ int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int 
             static cudaError_t attr = cudaSuccess;
             std::call_once(once, [] {
                 attr = cudaFuncSetAttribute(group_merge_kernel<8, false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 4);
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * 256 * 4);
                 if (attr == cudaSuccess)
                     attr = cudaFuncSetAttribute(group_merge_kernel<8, true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 4);
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * 256 * 4);
             });
             VGA_CHECK_CUDA(attr);
             VGA_GM(8);

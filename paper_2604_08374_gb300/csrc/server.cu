@@ -130,6 +130,7 @@ void batched_lane(vga_server *S) {
     const double *lc_base = reinterpret_cast<const double *>(S->arrays + 2 * align256(engine_arrays_bytes(cap)));
     std::vector<std::shared_ptr<Request>> active;
     std::vector<JobDev> host;  // device state of `active`, refreshed after every pass
+    EngineForks forks;         // the pass's union kernels of different slice widths run side by side
     for (;;) {
         std::vector<std::shared_ptr<Request>> fresh;
         {
@@ -204,7 +205,7 @@ void batched_lane(vga_server *S) {
         EngineSet E;
         int rc = engine_upload(A_run, host, &E, stream);
         const int share = S->solo_active.load() ? S->cfg.batched_share : 100;
-        if (rc == VGA_OK) rc = engine_pass(A_run, E, stream, 0, 0, share);
+        if (rc == VGA_OK) rc = engine_pass(A_run, E, stream, 0, 0, share, &forks);
         cudaError_t e = cudaSuccess;
         int err = 0;
         if (rc == VGA_OK) {
