@@ -609,7 +609,10 @@ typedef struct vga_tune_entry {
     int p;               /* precision the entry was tuned at                                 */
     double geu_per_s;    /* winner's union throughput on the tuning graph, 1e9 edges/s       */
     uint64_t tuned_edges;/* E of the tuning graph                                            */
-    int reserved[2];
+    int group_nodes;     /* mode 2 grouped union: nodes per group (0 = automatic, 1 = one node
+                            per warp, 2, 4 or 8); the batched engine honours 1 and otherwise
+                            groups 4 nodes                                                   */
+    int reserved;
 } vga_tune_entry;
 
 /*
@@ -626,7 +629,8 @@ typedef struct vga_tune_entry {
  * Search per bucket: every union variant and power-of-two slice width that fits
  * the L2 at 8 warps per CTA with the automatic hub threshold; then CTA sizes 4
  * and 16 for the best pair; then, in mode 2, hub thresholds of 1/2 and 1/4 of
- * the automatic one.  Each candidate runs two union passes (d = 2) twice and
+ * the automatic one, then group sizes 1, 2 and 8 against the automatic 4.
+ * Each candidate runs two union passes (d = 2) twice and
  * keeps its faster run; a run of each variant first builds any lookup list.
  * Every candidate computes the same registers (they differ only in launch shape).
  */

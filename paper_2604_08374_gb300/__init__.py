@@ -64,11 +64,11 @@ class VgaProfile(C.Structure):
 class VgaTuneEntry(C.Structure):
     _fields_ = [("degree_log2", C.c_int), ("union_mode", C.c_int), ("slice_bytes", C.c_int),
                 ("warps_per_cta", C.c_int), ("hub_lookups", C.c_int), ("p", C.c_int), ("geu_per_s", C.c_double),
-                ("tuned_edges", C.c_uint64), ("reserved", C.c_int * 2)]
+                ("tuned_edges", C.c_uint64), ("group_nodes", C.c_int), ("reserved", C.c_int)]
 
 
 TUNE_FIELDS = ("degree_log2", "union_mode", "slice_bytes", "warps_per_cta", "hub_lookups", "p", "geu_per_s",
-               "tuned_edges")
+               "tuned_edges", "group_nodes")
 
 
 SIGNATURES = {

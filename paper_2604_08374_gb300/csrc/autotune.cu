@@ -30,7 +30,9 @@ int degree_bucket(const vga_graph *g) {
 bool entry_ok(const vga_tune_entry &e) {
     return (e.union_mode == 1 || e.union_mode == 2) && e.slice_bytes >= 16 && e.slice_bytes <= 1024 &&
            !(e.slice_bytes & (e.slice_bytes - 1)) && e.warps_per_cta >= 0 && e.warps_per_cta <= 16 &&
-           e.hub_lookups >= 0;
+           e.hub_lookups >= 0 &&
+           (e.group_nodes == 0 || e.group_nodes == 1 || e.group_nodes == 2 || e.group_nodes == 4 ||
+            e.group_nodes == 8);
 }
 
 // Union time of two passes (d = 2), the faster of two runs; < 0 on failure.
@@ -96,7 +98,18 @@ int tune_graph(const vga_graph *g, int p, cudaStream_t stream, vga_tune_entry *e
             VGA_TRY(consider(t));
         }
     }
+    // 4. group size of the grouped union (mode 2): one node per warp, 2 and 8
+    //    against the automatic 4
+    if (best.union_mode == 2) {
+        const vga_tuning base3 = best;
+        for (int gn : {1, 2, 8}) {
+            vga_tuning t = base3;
+            t.group_nodes = gn;
+            VGA_TRY(consider(t));
+        }
+    }
     e->degree_log2 = degree_bucket(g);
+    e->group_nodes = best.group_nodes;
     e->union_mode = best.union_mode;
     e->slice_bytes = best.slice_bytes;
     e->warps_per_cta = best.warps_per_cta;
@@ -136,9 +149,9 @@ int vga_tune_table_set(const vga_tune_entry *entries, int n) {
     for (int i = 0; i < n; i++)
         if (!entry_ok(entries[i])) {
             set_error("vga_tune_table_set: entry %d has union_mode %d, slice_bytes %d, warps_per_cta %d, "
-                      "hub_lookups %d",
+                      "hub_lookups %d, group_nodes %d",
                       i, entries[i].union_mode, entries[i].slice_bytes, entries[i].warps_per_cta,
-                      entries[i].hub_lookups);
+                      entries[i].hub_lookups, entries[i].group_nodes);
             return VGA_EINVAL;
         }
     std::lock_guard<std::mutex> lock(g_tab_mu);

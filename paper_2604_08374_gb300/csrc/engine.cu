@@ -297,7 +297,8 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
 }
 
 int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
-                const double *lc, double *md, double *ball, uint32_t hub_lookups, cudaStream_t stream, JobDev *out) {
+                const double *lc, double *md, double *ball, uint32_t hub_lookups, cudaStream_t stream, JobDev *out,
+                int group_nodes) {
     JobDev J{};
     const uint64_t n = g->n, m = 1ull << p;
     uint64_t o = 0;
@@ -312,18 +313,22 @@ int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const
         RunItemList list;
         VGA_TRY(ensure_run_items(g, L.scheme, hub_lookups ? hub_lookups : hub_lookups_auto(g, L.scheme), stream,
                                  &list));
-        const uint32_t hub = hub_lookups ? hub_lookups : hub_lookups_auto(g, L.scheme);
-        GroupList groups;
-        VGA_TRY(ensure_group_list(g, L.scheme, hub, kEngineGroupNodes, stream, &groups));
         J.lk = g->lk[L.scheme].d_lk;
         J.scheme = L.scheme;
         J.items = list.items;
         J.units = (uint32_t)list.count;
-        J.groups = groups.items;
-        J.grows = groups.rows;
-        J.gcls = groups.cls;
-        J.hub_units = (uint32_t)list.hub_items;
-        J.uunits = (uint32_t)(list.hub_items + groups.count);
+        if (group_nodes == 1) {  // every work item per node (union_item)
+            J.hub_units = J.uunits = (uint32_t)list.count;
+        } else {
+            const uint32_t hub = hub_lookups ? hub_lookups : hub_lookups_auto(g, L.scheme);
+            GroupList groups;
+            VGA_TRY(ensure_group_list(g, L.scheme, hub, kEngineGroupNodes, stream, &groups));
+            J.groups = groups.items;
+            J.grows = groups.rows;
+            J.gcls = groups.cls;
+            J.hub_units = (uint32_t)list.hub_items;
+            J.uunits = (uint32_t)(list.hub_items + groups.count);
+        }
     } else {
         J.units = g->n;
         J.uunits = g->n;
@@ -772,10 +777,11 @@ int run_batch(vga_job *jobs, int n_jobs, void *ws_ptr, uint64_t ws_bytes, cudaSt
     for (size_t k = 0; k < B.idx.size(); k++) {
         const vga_job &jb = jobs[B.idx[k]];
         vga_tune_entry te{};
-        const uint32_t hub = tune_table_lookup(jb.graph, &te) ? (uint32_t)te.hub_lookups : 0u;
+        const bool tabled = tune_table_lookup(jb.graph, &te);
+        const uint32_t hub = tabled ? (uint32_t)te.hub_lookups : 0u;
         VGA_TRY(make_jobdev(jb.graph, jb.p, jb.d, jb.seed, jb.conv_mode, B.lay[k], ws + B.job_off[k],
                             reinterpret_cast<const double *>(ws + B.off_lc + lc_offset(jb.p)), jb.mean_depth_dev,
-                            jb.ball_size_dev, hub, stream, &host[k]));
+                            jb.ball_size_dev, hub, stream, &host[k], tabled ? te.group_nodes : 0));
     }
     const EngineArrays A = engine_arrays_at(ws + B.off_arrays, (int)host.size());
     EngineSet E;

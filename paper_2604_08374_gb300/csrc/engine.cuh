@@ -90,8 +90,11 @@ JobLayout job_layout(uint32_t n, int p, int slice_cap, uint64_t budget, int mode
 // Device view of one analysis in workspace ws; in mode 2 it builds (on first
 // use) the graph's lookups and its work list for hub threshold hub_lookups
 // (0 = automatic).
+// group_nodes == 1 (a tuned choice) unions every run-aware node per warp;
+// otherwise the engine groups kEngineGroupNodes nodes.
 int make_jobdev(const vga_graph *g, int p, int d, uint64_t seed, int conv, const JobLayout &L, uint8_t *ws,
-                const double *lc, double *md, double *ball, uint32_t hub_lookups, cudaStream_t stream, JobDev *out);
+                const double *lc, double *md, double *ball, uint32_t hub_lookups, cudaStream_t stream, JobDev *out,
+                int group_nodes = 0);
 uint64_t lc_offset(int p);
 uint64_t lc_all_bytes();
 int upload_lc_tables(uint8_t *dst, const bool *used, cudaStream_t stream);

@@ -616,7 +616,8 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         set_error("group_nodes = %d must be 0 (automatic), 1 (one node per warp), 2, 4 or 8", grp);
         return VGA_EINVAL;
     }
-    P->group = P->mode != kModeRuns || grp == 1 ? 0 : grp == 0 ? kGroupAutoNodes : grp;
+    const int grp_sel = grp ? grp : (tabled && te.group_nodes > 0) ? te.group_nodes : 0;
+    P->group = P->mode != kModeRuns || grp_sel == 1 ? 0 : grp_sel == 0 ? kGroupAutoNodes : grp_sel;
     const uint64_t regs = (uint64_t)P->n * P->node_bytes;
     uint64_t o = 0;
     P->off_cur = o;   o = align256(o + regs);

@@ -65,6 +65,9 @@ __device__ __forceinline__ uint64_t lookup_key(uint32_t r, uint32_t n) {
     return ((uint64_t)(r - slot * n) << 3) | slot;
 }
 
+// Entries of each list a merging lane loads at a time (independent loads).
+constexpr int kMergeWindow = 4;
+
 // First index of list[0 .. len) whose key is >= k (the list is sorted by key).
 __device__ __forceinline__ uint32_t key_lower_bound(const uint32_t *__restrict__ list, uint32_t len, uint64_t k,
                                                     uint32_t n) {
@@ -89,44 +92,61 @@ __device__ __forceinline__ uint32_t key_lower_bound(const uint32_t *__restrict__
 template <int NODES, bool WRITE>
 __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t n_groups,
                                    const uint64_t *__restrict__ lk_off, const uint32_t *__restrict__ lk, uint32_t n,
-                                   uint32_t *__restrict__ cc, uint32_t *__restrict__ rows, uint2 *__restrict__ cls) {
-    extern __shared__ uint32_t s_cnt[];
+                                   uint32_t *__restrict__ cc, uint32_t *__restrict__ lane_cc,
+                                   uint32_t *__restrict__ rows, uint2 *__restrict__ cls) {
+    extern __shared__ __align__(16) uint32_t s_cnt[];
     constexpr uint32_t C = 1u << NODES;
     const int lane = threadIdx.x & 31;
     const uint64_t gid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gid >= n_groups) return;
     uint32_t *c = s_cnt + (threadIdx.x >> 5) * (C * 32) + lane;  // c[k * 32]: this lane's counter of class k
+
     const GroupItem &it = items[gid];
     const uint32_t *list[NODES];
     uint32_t len[NODES];
-    uint32_t longest = 0;
+    const uint32_t *longest = lk;  // the longest list (not indexed by a run-time subscript)
+    uint32_t L = 0;
 #pragma unroll
     for (int j = 0; j < NODES; j++) {
         const uint32_t v = it.node[j];
         const uint64_t o = v == 0xffffffffu ? 0 : lk_off[v];
         list[j] = lk + o;
         len[j] = v == 0xffffffffu ? 0u : (uint32_t)(lk_off[v + 1] - o);
-        if (len[j] > len[longest]) longest = j;
+        if (len[j] > L) {
+            L = len[j];
+            longest = list[j];
+        }
     }
     // this lane's key range [k0, k1)
-    const uint32_t L = len[longest];
-    uint64_t k0 = lane == 0 || L == 0 ? 0ull : lookup_key(list[longest][(uint32_t)((uint64_t)L * lane / 32)], n);
+    uint64_t k0 = lane == 0 || L == 0 ? 0ull : lookup_key(longest[(uint32_t)((uint64_t)L * lane / 32)], n);
     uint64_t k1 = __shfl_down_sync(0xffffffffu, k0, 1);
     if (lane == 31) k1 = ~0ull;
-    uint32_t p[NODES], e[NODES];
+    uint32_t p[NODES], p0[NODES], e[NODES];
     uint64_t hk[NODES];
+    uint32_t win[NODES][kMergeWindow];  // the next entries of each list, loaded together
+    auto load_windows = [&]() {
+#pragma unroll
+        for (int j = 0; j < NODES; j++) {
+            p0[j] = p[j];
+#pragma unroll
+            for (int q = 0; q < kMergeWindow; q++) win[j][q] = p[j] + q < e[j] ? list[j][p[j] + q] : 0u;
+            hk[j] = p[j] < e[j] ? lookup_key(win[j][0], n) : ~0ull;
+        }
+    };
 #pragma unroll
     for (int j = 0; j < NODES; j++) {
         p[j] = k0 == 0 ? 0u : key_lower_bound(list[j], len[j], k0, n);
         e[j] = k1 == ~0ull ? len[j] : key_lower_bound(list[j], len[j], k1, n);
-        hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
     }
+    load_windows();
     uint32_t *mine = cc + (gid << NODES);
     for (uint32_t k = 0; k < C; k++) c[k * 32] = 0;
-    if (WRITE) {
-        // this lane's cursor in class k: the class's base (classes in mask
-        // order) plus the counts of the lower lanes, found by a second merge
-        // pass that only counts
+    uint32_t *my_lane_cc = lane_cc ? lane_cc + (gid << NODES) * 32 + lane : nullptr;  // [group][class][lane]
+    if (WRITE && my_lane_cc) {
+        for (uint32_t k = 0; k < C; k++) c[k * 32] = my_lane_cc[k * 32];
+    } else if (WRITE) {
+        // this lane's count in every class, found by a merge pass that only
+        // counts (when the count pass kept no per-lane counts)
         for (;;) {
             uint64_t best = ~0ull;
 #pragma unroll
@@ -142,6 +162,13 @@ __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t
                 }
             c[mask * 32]++;
         }
+#pragma unroll
+        for (int j = 0; j < NODES; j++) p[j] = k0 == 0 ? 0u : key_lower_bound(list[j], len[j], k0, n);
+        load_windows();
+    }
+    if (WRITE) {
+        // this lane's cursor in class k: the class's base (classes in mask
+        // order) plus the counts of the lower lanes
         uint32_t base = 0;
         uint64_t ci = it.cls;
         for (uint32_t k = 1; k < C; k++) {
@@ -158,13 +185,8 @@ __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t
             ci++;
             base += total;
         }
-        // merge again, writing
-#pragma unroll
-        for (int j = 0; j < NODES; j++) {
-            p[j] = k0 == 0 ? 0u : key_lower_bound(list[j], len[j], k0, n);
-            hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
-        }
     }
+    uint32_t *row_base = WRITE ? rows + it.b : nullptr;
     for (;;) {
         uint64_t best = ~0ull;
 #pragma unroll
@@ -175,12 +197,20 @@ __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t
         for (int j = 0; j < NODES; j++)
             if (hk[j] == best) {
                 mask |= 1u << j;
-                r = list[j][p[j]];
+                r = win[j][0];
                 p[j]++;
-                hk[j] = p[j] < e[j] ? lookup_key(list[j][p[j]], n) : ~0ull;
+                // shift the look-ahead window; refill it with independent loads when empty
+#pragma unroll
+                for (int q = 0; q < kMergeWindow - 1; q++) win[j][q] = win[j][q + 1];
+                if (p[j] < e[j] && ((p[j] - p0[j]) % kMergeWindow) == 0) {
+#pragma unroll
+                    for (int q = 0; q < kMergeWindow; q++)
+                        win[j][q] = p[j] + q < e[j] ? list[j][p[j] + q] : 0u;
+                }
+                hk[j] = p[j] < e[j] ? lookup_key(win[j][0], n) : ~0ull;
             }
         if (WRITE)
-            rows[it.b + c[mask * 32]++] = r;
+            row_base[c[mask * 32]++] = r;
         else
             c[mask * 32]++;
     }
@@ -189,6 +219,7 @@ __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t
         for (uint32_t k = 0; k < C; k++) {
             const uint32_t t = __reduce_add_sync(0xffffffffu, c[k * 32]);
             if (lane == 0) mine[k] = t;
+            if (my_lane_cc) my_lane_cc[k * 32] = c[k * 32];
         }
     }
 }
@@ -378,9 +409,12 @@ int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int 
     const uint64_t ng = items.size();
     const int warps = nodes >= 8 ? 1 : 4;  // one warp per group; 32 lanes x 2^nodes counters each
     const size_t smem = (size_t)warps * 32 * (4u << nodes);
-    DeviceBuffer d_items, d_cc;
+    DeviceBuffer d_items, d_cc, d_lane_cc;
     VGA_TRY(d_items.alloc(sizeof(GroupItem) * std::max<uint64_t>(ng, 1)));
     VGA_TRY(d_cc.alloc((4ull << nodes) * std::max<uint64_t>(ng, 1)));
+    // per-lane class counts of the count pass, which spare the write pass a
+    // recount (groups of up to 4 nodes: 2 KB a group)
+    if (nodes <= 4) VGA_TRY(d_lane_cc.alloc((128ull << nodes) * std::max<uint64_t>(ng, 1)));
     auto merge = [&](bool write, uint32_t *rows, uint2 *cls) -> int {
         if (!ng) return VGA_OK;
         VGA_CHECK_CUDA(cudaMemcpyAsync(d_items.ptr, items.data(), sizeof(GroupItem) * ng, cudaMemcpyHostToDevice,
@@ -390,10 +424,12 @@ int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int 
 #define VGA_GM(NN)                                                                                                   \
     if (write)                                                                                                       \
         group_merge_kernel<NN, true><<<blocks, threads, smem, stream>>>(d_items.as<GroupItem>(), ng, L.d_off,       \
-                                                                        L.d_lk, g->n, d_cc.as<uint32_t>(), rows, cls); \
+                                                                        L.d_lk, g->n, d_cc.as<uint32_t>(),           \
+                                                                        d_lane_cc.as<uint32_t>(), rows, cls);        \
     else                                                                                                             \
         group_merge_kernel<NN, false><<<blocks, threads, smem, stream>>>(d_items.as<GroupItem>(), ng, L.d_off,      \
-                                                                         L.d_lk, g->n, d_cc.as<uint32_t>(), rows, cls)
+                                                                         L.d_lk, g->n, d_cc.as<uint32_t>(),          \
+                                                                         d_lane_cc.as<uint32_t>(), rows, cls)
         if (nodes == 2) VGA_GM(2);
         else if (nodes == 4) VGA_GM(4);
         else {

@@ -167,9 +167,10 @@ void batched_lane(vga_server *S) {
             double *md = reinterpret_cast<double *>(r->ws + r->L.bytes);
             JobDev J{};
             vga_tune_entry te{};
-            const uint32_t hub = tune_table_lookup(r->g, &te) ? (uint32_t)te.hub_lookups : 0u;
+            const bool tabled = tune_table_lookup(r->g, &te);
+            const uint32_t hub = tabled ? (uint32_t)te.hub_lookups : 0u;
             const int rc = make_jobdev(r->g, r->p, r->d, r->seed, r->conv, r->L, r->ws, lc_base + lc_offset(r->p) / 8,
-                                       md, md + r->g->n, hub, stream, &J);
+                                       md, md + r->g->n, hub, stream, &J, tabled ? te.group_nodes : 0);
             if (rc != VGA_OK) {
                 fail(S, r, rc, vga_last_error(), stream);
                 continue;

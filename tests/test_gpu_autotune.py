@@ -50,6 +50,7 @@ def test_autotune_entries_and_steering(vga, graphs):
     for e in entries:
         assert e["union_mode"] in (1, 2) and e["warps_per_cta"] in (4, 8, 16) and e["p"] == 8
         assert 16 <= e["slice_bytes"] <= 256 and e["geu_per_s"] > 0
+        assert e["group_nodes"] in (0, 1, 2, 8)
     assert vga.vga_tune_table_get() == entries
     # every graph runs with its bucket's variant and width, and stays exact
     by_bucket = {e["degree_log2"]: e for e in entries}
@@ -91,8 +92,41 @@ def test_tuned_table_in_batch(vga, graphs):
     assert vga.vga_tune_table_get() == []
 
 
+@pytest.mark.parametrize("group_nodes", [1, 2, 8])
+def test_tuned_group_size_single_and_batch(vga, graphs, group_nodes):
+    # a tuned group size steers single runs (any of 1, 2, 8) and batched jobs
+    # (the engine honours 1 and groups 4 nodes otherwise); results stay exact
+    torch = pytest.importorskip("torch")
+    gs = [g for g, _, _ in graphs]
+    table = {}
+    for g in gs:
+        table.setdefault(_bucket(g), {"degree_log2": _bucket(g), "union_mode": 2, "slice_bytes": 64,
+                                      "warps_per_cta": 4, "group_nodes": group_nodes})
+    vga.vga_tune_table_set(list(table.values()))
+    try:
+        jobs = []
+        for g, off, b in graphs:
+            ref = oracle.hyperball(off, b, 8, 0, seed=21, trace=10)
+            got = vga.hyperball_run_trace(g, 8, 0, seed=21, max_trace=10)
+            assert got["iterations"] == ref["iterations"]
+            for t in range(ref["iterations"] + 1):
+                assert np.array_equal(got["regs"][t], ref["regs"][t])
+            n = g.n_nodes
+            jobs.append(dict(graph=g, p=8, d=0, seed=21,
+                             mean_depth=torch.empty(n, dtype=torch.float64, device="cuda"),
+                             ball=torch.empty(n, dtype=torch.float64, device="cuda")))
+        its = vga.hyperball_run_batch(jobs, use_graph=False)
+        for j, (g, off, b), it in zip(jobs, graphs, its):
+            ref = oracle.hyperball(off, b, 8, 0, seed=21)
+            assert it == ref["iterations"]
+            assert np.array_equal(j["mean_depth"].cpu().numpy(), ref["mean_depth"], equal_nan=True)
+    finally:
+        vga.vga_tune_table_set([])
+
+
 def test_tune_table_rejects_bad_entries(vga):
     for bad in ({"degree_log2": 3, "union_mode": 3, "slice_bytes": 64},
+                {"degree_log2": 3, "union_mode": 2, "slice_bytes": 64, "group_nodes": 3},
                 {"degree_log2": 3, "union_mode": 1, "slice_bytes": 48},
                 {"degree_log2": 3, "union_mode": 2, "slice_bytes": 64, "warps_per_cta": 17},
                 {"degree_log2": 3, "union_mode": 2, "slice_bytes": 64, "hub_lookups": -1}):
