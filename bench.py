@@ -356,8 +356,9 @@ def run_reference(args, dist: Dist):
 
 def kernel_source_sha() -> str:
     """Hash of the union kernels' source: their device code (hb_device.cuh), the
-    lookup and work-item declarations in vga_common.cuh, and their definitions
-    in hyperball.cu (host code there does not count)."""
+    lookup and work-item declarations in vga_common.cuh, their definitions in
+    hyperball.cu (host code there does not count), and the group-list builder
+    in runs.cu (which decides what a grouped launch gathers)."""
     h = hashlib.sha256()
 
     def region(rel, start, end):
@@ -371,6 +372,8 @@ def kernel_source_sha() -> str:
     region("paper_2604_08374_gb300/csrc/vga_common.cuh", b"constexpr int kRunLevels", b"// Work list of the run-aware")
     region("paper_2604_08374_gb300/csrc/hyperball.cu", b"// Eq. hll-union for one register slice, one warp per node",
            b"// Microbenchmark twin of hb_union_kernel")
+    # how the grouped union's groups and their row lists are formed
+    region("paper_2604_08374_gb300/csrc/runs.cu", b"// Merge key of a range lookup", None)
     return h.hexdigest()[:16]
 
 
@@ -406,7 +409,7 @@ def run_ours(args, dist: Dist):
     dev = torch.device("cuda", dist.local_rank)
     obst = CONFIGS[args.config]["grid"]()
     t0 = time.perf_counter()
-    g = vga.vga_visibility_build(obst, order=args.order)
+    g, cell_of_node = vga.vga_visibility_build(obst, order=args.order, return_cells=True)
     build_s = time.perf_counter() - t0
     N, E, B = g.n_nodes, g.n_edges, g.n_bytes
     tuned = None
@@ -582,8 +585,10 @@ def run_ours(args, dist: Dist):
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record()
         e2e_passes = 0
+        H, W = obst.shape
         for _ in range(args.steps):
             with vga.vga_graph_load(off_np, bytes_np) as g2:
+                g2.set_cells(W, H, cell_of_node)  # the grid positions, as a caller holding the grid passes them
                 _, _, it = vga.hyperball_run(g2, args.p, args.d, args.seed)
             e2e_passes += it
         s1.record()
@@ -594,7 +599,8 @@ def run_ours(args, dist: Dist):
         extras["e2e"] = {"value": e_units / e_sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * (N + 1) + B,
                          "d2h_bytes_per_step": 16 * N, "ms_per_step": 1e3 * e2e_sec / args.steps,
                          "wall_ms_per_step": 1e3 * e2e_wall / args.steps,
-                         "calls": "vga_graph_load (pinned host CSR) + hyperball_run (host outputs) + vga_graph_free"}
+                         "calls": "vga_graph_load (pinned host CSR) + vga_graph_set_cells (the nodes' grid cells, host "
+                                  "side) + hyperball_run (host outputs) + vga_graph_free"}
         del off_pin, bytes_pin
         # ---- unlimited depth, once ----
         f0 = torch.cuda.Event(enable_timing=True)

@@ -127,6 +127,22 @@ int vga_graph_info(const vga_graph *g, uint32_t *n_nodes, uint64_t *n_edges, uin
  * (N).  Any output may be NULL. */
 int vga_graph_copy_csr(const vga_graph *g, uint64_t *offsets, uint8_t *bytes, uint32_t *degrees);
 
+/*
+ * vga_graph_set_cells -- attach the grid position of every node (Sec. 3.1:
+ * node v is the free cell cell_of_node[v] = y * W + x of a W x H grid), as the
+ * visibility builder does for the graphs it builds.  The run-aware union then
+ * groups nodes by 2 x 2 blocks of cells (vga_tuning.group_nodes = 4, the
+ * default), which share more table rows than runs of consecutive ids; the
+ * results are the same bit for bit either way.  The graph keeps a host copy
+ * (4 bytes a node); cached group lists are dropped.  Any v-to-cell map is
+ * accepted as long as every value is below W * H and no two nodes share a
+ * cell.  NULL cell_of_node detaches the geometry.  Call it while no analysis
+ * runs on the graph.
+ *   Errors: VGA_EINVAL for W or H outside 1..16384, a cell out of range or a
+ *   cell used twice.
+ */
+int vga_graph_set_cells(vga_graph *g, int W, int H, const uint64_t *cell_of_node);
+
 /* ---------------------------------------------------------------------- */
 /* Visibility graph builder (Sec. 3.1)                                     */
 /* ---------------------------------------------------------------------- */

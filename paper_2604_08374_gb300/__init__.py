@@ -82,6 +82,7 @@ SIGNATURES = {
     "vga_graph_free": ([vp], None),
     "vga_graph_info": ([vp, C.POINTER(u32), C.POINTER(u64), C.POINTER(u64)], i32),
     "vga_graph_copy_csr": ([vp, vp, vp, vp], i32),
+    "vga_graph_set_cells": ([vp, i32, i32, vp], i32),
     "vga_visibility_build": ([i32, i32, vp, vp, C.POINTER(vp)], i32),
     "vga_visibility_count": ([i32, i32, vp, C.POINTER(u32)], i32),
     "vga_visibility_build_ordered": ([i32, i32, vp, i32, vp, C.POINTER(vp)], i32),
@@ -239,6 +240,17 @@ class Graph:
 
     def save(self, path: str):
         _check(lib().vga_graph_save_file(self.handle, path.encode()))
+
+    def set_cells(self, W: int, H: int, cell_of_node):
+        """Attach every node's grid cell (y * W + x on a W x H grid); the grouped
+        union then groups 2 x 2 blocks of cells.  None detaches it."""
+        if cell_of_node is None:
+            _check(lib().vga_graph_set_cells(self.handle, 0, 0, None))
+            return
+        cells = np.ascontiguousarray(cell_of_node, np.uint64)
+        if len(cells) != self.n_nodes:
+            raise ValueError("need one cell per node")
+        _check(lib().vga_graph_set_cells(self.handle, W, H, _ptr(cells) if self.n_nodes else None))
 
 
 def vga_graph_load(offsets: np.ndarray, bytes_: np.ndarray, comp_size=None) -> Graph:

@@ -394,18 +394,40 @@ int ensure_group_list(const vga_graph *g, int scheme, uint32_t hub_lookups, int 
         k = 0;
         sum = 0;
     };
-    for (uint32_t v = 0; v < g->n; v++) {
+    auto add = [&](uint32_t v) {
         const uint64_t cnt = off[v + 1] - off[v];
         if (cnt > hub_lookups) {  // split hubs stay per node
             hub_rows += cnt;
-            continue;
+            return;
         }
         if (k && sum + cnt >= (1ull << 31)) close();
         cur.node[k++] = v;
         sum += cnt;
-        if (k == nodes) close();
+    };
+    if (!g->cells.empty() && g->cells.size() == g->n) {
+        // with the grid geometry: blocks of cells (2 x 1, 2 x 2 or 4 x 2), in
+        // raster order of blocks, each block's nodes in raster order
+        const int W = g->cells_W, H = g->cells_H;
+        const int bw = nodes == 2 ? 2 : nodes == 4 ? 2 : 4, bh = nodes == 2 ? 1 : 2;
+        std::vector<uint32_t> node_of((size_t)W * H, 0xffffffffu);
+        for (uint32_t v = 0; v < g->n; v++) node_of[g->cells[v]] = v;
+        for (int by = 0; by < H; by += bh)
+            for (int bx = 0; bx < W; bx += bw) {
+                for (int dy = 0; dy < bh && by + dy < H; dy++)
+                    for (int dx = 0; dx < bw && bx + dx < W; dx++) {
+                        const uint32_t v = node_of[(size_t)(by + dy) * W + bx + dx];
+                        if (v != 0xffffffffu) add(v);
+                    }
+                if (k) close();
+            }
+    } else {
+        // consecutive ids
+        for (uint32_t v = 0; v < g->n; v++) {
+            add(v);
+            if (k == nodes) close();
+        }
+        if (k) close();
     }
-    if (k) close();
     const uint64_t ng = items.size();
     const int warps = nodes >= 8 ? 1 : 4;  // one warp per group; 32 lanes x 2^nodes counters each
     const size_t smem = (size_t)warps * 32 * (4u << nodes);

@@ -55,6 +55,12 @@ struct vga_graph {
     mutable std::mutex lk_mu;
     mutable RunLookups lk[2];
     int lk_scheme = 0;  // the table scheme chosen for this graph (counted at load)
+    // Optional geometry (host copy): the grid cell of every node on a W x H
+    // grid, set by the visibility builder or vga_graph_set_cells.  With it the
+    // grouped union forms its groups from 2 x 2 blocks of cells instead of
+    // consecutive ids.  Changing it drops the cached group lists.
+    int cells_W = 0, cells_H = 0;
+    std::vector<uint32_t> cells;
 };
 
 namespace vga {

@@ -312,6 +312,48 @@ void vga_graph_free(vga_graph *g) {
     delete g;
 }
 
+int vga_graph_set_cells(vga_graph *g, int W, int H, const uint64_t *cell_of_node) {
+    clear_error();
+    if (!g) {
+        set_error("vga_graph_set_cells: null graph");
+        return VGA_EINVAL;
+    }
+    std::vector<uint32_t> cells;
+    if (cell_of_node) {
+        if (W < 1 || H < 1 || W > 16384 || H > 16384) {
+            set_error("vga_graph_set_cells: W = %d, H = %d outside 1..16384", W, H);
+            return VGA_EINVAL;
+        }
+        const uint64_t C = (uint64_t)W * H;
+        std::vector<uint8_t> used(C, 0);
+        cells.resize(g->n);
+        for (uint32_t v = 0; v < g->n; v++) {
+            const uint64_t c = cell_of_node[v];
+            if (c >= C || used[c]) {
+                set_error("vga_graph_set_cells: node %u has cell %llu, outside the %d x %d grid or used twice", v,
+                          (unsigned long long)c, W, H);
+                return VGA_EINVAL;
+            }
+            used[c] = 1;
+            cells[v] = (uint32_t)c;
+        }
+    }
+    std::lock_guard<std::mutex> lock(g->lk_mu);
+    g->cells.swap(cells);
+    g->cells_W = cell_of_node ? W : 0;
+    g->cells_H = cell_of_node ? H : 0;
+    // the group lists were formed from the old geometry
+    for (vga_graph::RunLookups &L : g->lk) {
+        for (const vga_graph::RunLookups::GroupSet &gs : L.groups) {
+            cudaFree(gs.d_items);
+            cudaFree(gs.d_rows);
+            cudaFree(gs.d_cls);
+        }
+        L.groups.clear();
+    }
+    return VGA_OK;
+}
+
 int vga_graph_info(const vga_graph *g, uint32_t *n_nodes, uint64_t *n_edges, uint64_t *n_bytes) {
     clear_error();
     if (!g) {

@@ -360,7 +360,12 @@ int vga_visibility_build_ordered(int W, int H, const uint8_t *obst, int order, u
     uint8_t *pb = d_bytes.as<uint8_t>();
     d_off.release();
     d_bytes.release();
-    return finish_graph_load(n, n_bytes, po, pb, nullptr, stream, out);
+    VGA_TRY(finish_graph_load(n, n_bytes, po, pb, nullptr, stream, out));
+    // the builder knows every node's cell: the grouped union groups 2 x 2 blocks
+    (*out)->cells.swap(cells);
+    (*out)->cells_W = W;
+    (*out)->cells_H = H;
+    return VGA_OK;
 }
 
 int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_node, vga_graph **out) {

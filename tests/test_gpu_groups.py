@@ -166,3 +166,59 @@ def test_grouped_union_register_shards(vga, nodes):
     assert it == ref["iterations"]
     assert np.array_equal(md.cpu().numpy(), ref["mean_depth"], equal_nan=True)
     assert np.array_equal(ball.cpu().numpy(), ref["ball"])
+
+
+# ----------------------------------------------------------------------------
+# groups from the grid geometry (2 x 1, 2 x 2, 4 x 2 blocks of cells)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", ["raster", "hilbert"])
+@pytest.mark.parametrize("name", ["tiny3", "rect96", "sparse", "open1x301"])
+def test_groups_from_cell_blocks(vga, name, order):
+    # graphs from the builder carry their cells, so their groups are blocks of
+    # cells; the same CSR loaded without geometry groups consecutive ids, and
+    # with vga_graph_set_cells blocks again: all must equal the oracle
+    if name.startswith("tiny"):
+        obst = workloads.tiny(int(name[4:]))
+    elif name == "rect96":
+        obst = workloads.rectangles_until(96, 96, (2, 12), int(96 * 96 * 0.88), seed=4)
+    elif name == "open1x301":
+        obst = workloads.open_grid(301, 1)
+    else:
+        rng = np.random.default_rng(11)
+        obst = (rng.random((41, 37)) < 0.3).astype(np.uint8)
+    H, W = obst.shape
+    off, b, cells = oracle.build_graph(obst, order=order)
+    ref = oracle.hyperball(off, b, 10, 0, seed=12, trace=16)
+    g_built, gcells = vga.vga_visibility_build(obst, return_cells=True, order=order)
+    with g_built as g1, vga.vga_graph_load(off, b) as g2:
+        assert np.array_equal(gcells.astype(np.int64), cells)
+        for nodes in (2, 4, 8):
+            assert_same_run(vga.hyperball_run_trace(g1, 10, 0, seed=12, max_trace=16, union_mode=2,
+                                                    group_nodes=nodes), ref)
+            assert_same_run(vga.hyperball_run_trace(g2, 10, 0, seed=12, max_trace=16, union_mode=2,
+                                                    group_nodes=nodes), ref)
+        g2.set_cells(W, H, cells)
+        for nodes in (2, 4, 8):
+            assert_same_run(vga.hyperball_run_trace(g2, 10, 0, seed=12, max_trace=16, union_mode=2,
+                                                    group_nodes=nodes, hub_lookups=3 if nodes == 4 else 0), ref)
+        g2.set_cells(W, H, None)
+        assert_same_run(vga.hyperball_run_trace(g2, 10, 0, seed=12, max_trace=16, union_mode=2), ref)
+
+
+def test_set_cells_rejects_bad_maps(vga):
+    obst = workloads.tiny(1)
+    H, W = obst.shape
+    off, b, cells = oracle.build_graph(obst)
+    with vga.vga_graph_load(off, b) as g:
+        bad = cells.copy()
+        bad[5] = bad[4]  # a cell used twice
+        with pytest.raises(vga.VgaError):
+            g.set_cells(W, H, bad)
+        bad = cells.copy()
+        bad[0] = W * H  # outside the grid
+        with pytest.raises(vga.VgaError):
+            g.set_cells(W, H, bad)
+        with pytest.raises(vga.VgaError):
+            g.set_cells(0, H, cells)
+        g.set_cells(W, H, cells)  # a valid map is accepted
