@@ -131,15 +131,6 @@ struct SliceRow {
     __device__ __forceinline__ const uint8_t *operator()(uint32_t id) const { return cur + (uint64_t)id * S; }
 };
 
-// Row of a range lookup: the lookup is the row index r = k * N + i of window
-// T_k[i] in the slice's table region (T_0 = the slice's own rows, then
-// T_1..T_K, N rows each).
-template <int S>
-struct TableRow {
-    const uint8_t *__restrict__ tab;
-    __device__ __forceinline__ const uint8_t *operator()(uint32_t r) const { return tab + (uint64_t)r * S; }
-};
-
 // Convert the split accumulators to register bytes and fold the P lane groups
 // of a warp together (every lane ends with the group maximum).
 template <int S, bool NIB>
@@ -307,51 +298,6 @@ __device__ __forceinline__ bool lk_wait(LkStage &st, int slot, uint32_t parity) 
     return done != 0;
 }
 
-// Run-aware Eq. hll-union for one register slice (runs.cu explains the
-// lookups): fold into acc the table rows of the range lookups lk[b .. e),
-// where the slice's table region tab (T_0 .. T_4, T_k[i] = max(cur[i .. i +
-// 2^k))) has been built.  The
-// lookups stream through the warp's TMA stage (`st`, with its barrier phases
-// in `phase`) and each chunk's rows are gathered like the per-neighbour union.
-template <int S, bool NIB = false>
-__device__ __forceinline__ void union_range_runs(const uint32_t *__restrict__ lk, const uint8_t *__restrict__ tab,
-                                                 uint64_t b, uint64_t e,
-                                                 LkStage &st, uint32_t &phase, int lane,
-                                                 typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4], int *err) {
-    using Sh = GatherShape<S>;
-    const int g = lane / Sh::G, sub = lane % Sh::G;
-    const TableRow<S> row{tab};
-    if (b >= e) return;
-    const uint64_t a0 = b & ~3ull, e4 = (e + 3) & ~3ull;
-    const uint32_t chunks = (uint32_t)((e4 - a0 + kLkChunk - 1) / kLkChunk);
-    if (lane == 0) {
-        for (uint32_t c = 0; c < 2 && c < chunks; c++) {
-            const uint64_t s0 = a0 + (uint64_t)c * kLkChunk;
-            const uint32_t cnt = (uint32_t)((e4 - s0 < (uint64_t)kLkChunk) ? e4 - s0 : kLkChunk);
-            lk_bulk_load(st, (int)c, lk + s0, cnt * 4u);
-        }
-    }
-    for (uint32_t c = 0; c < chunks; c++) {
-        const int slot = (int)(c & 1u);
-        // every lane observes the barrier phase itself (acquire for its reads)
-        if (!__all_sync(0xffffffffu, lk_wait(st, slot, (phase >> slot) & 1u))) {
-            if (lane == 0) atomicExch(err, 1);
-            lk_wait(st, slot, (phase >> slot) & 1u);  // give an in-flight copy a last chance
-        }
-        phase ^= 1u << slot;
-        const uint64_t s0 = a0 + (uint64_t)c * kLkChunk;
-        const uint64_t lo = b > s0 ? b : s0;
-        const uint64_t hi = (e < s0 + kLkChunk) ? e : s0 + kLkChunk;
-        if (hi > lo) gather_fold<S, NIB>(row, st.buf[slot] + (lo - s0), (int)(hi - lo), g, sub, acc);
-        __syncwarp();
-        if (lane == 0 && c + 2 < chunks) {
-            const uint64_t s2 = a0 + (uint64_t)(c + 2) * kLkChunk;
-            const uint32_t cnt = (uint32_t)((e4 - s2 < (uint64_t)kLkChunk) ? e4 - s2 : kLkChunk);
-            lk_bulk_load(st, slot, lk + s2, cnt * 4u);
-        }
-    }
-}
-
 // Word-wise register max into next[v] for the chunks of a split hub:
 // *p = max(*p, val) field by field, by compare-and-swap.  Every successful
 // swap by another chunk only raises fields, so the loop ends after a few
@@ -367,42 +313,6 @@ __device__ __forceinline__ void atomic_max_word(uint32_t *p, uint32_t val, int *
         old = seen;
     }
     atomicExch(err, 1);
-}
-
-// Store of one chunk of a split hub v: next[v] = max(next[v], cur[v], the
-// chunk's maximum), word by word with atomic_max_word.  next[v] must hold
-// registers no larger than the final ones when the pass starts (the run
-// clears it before the first pass; later it holds the counters of two passes
-// back, and counters only grow), so after all chunks it equals the result of
-// union_store.  The changed flag compares the chunk's maximum with cur[v]:
-// some chunk exceeds cur[v] exactly when the merged row does.
-template <int S, bool NIB>
-__device__ __forceinline__ void union_store_hub(const typename RegFmt<NIB>::Acc (&acc)[4 * GatherShape<S>::V4],
-                                                const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, uint32_t v,
-                                                int lane, uint32_t *flag, int *err, uint8_t *chg = nullptr) {
-    using Sh = GatherShape<S>;
-    const int g = lane / Sh::G, sub = lane % Sh::G;
-    uint4 nb[Sh::V4];
-    finish_groups<S, NIB>(acc, nb);
-    bool changed = false;
-    if (g == 0) {
-        const uint4 *own = reinterpret_cast<const uint4 *>(cur + (uint64_t)v * S + sub * Sh::CH);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(nxt + (uint64_t)v * S + sub * Sh::CH);
-#pragma unroll
-        for (int q = 0; q < Sh::V4; q++) {
-            const uint4 o4 = __ldg(own + q);
-            const uint4 res = RegFmt<NIB>::max4(nb[q], o4);
-            atomic_max_word<NIB>(dst + 4 * q + 0, res.x, err);
-            atomic_max_word<NIB>(dst + 4 * q + 1, res.y, err);
-            atomic_max_word<NIB>(dst + 4 * q + 2, res.z, err);
-            atomic_max_word<NIB>(dst + 4 * q + 3, res.w, err);
-            changed |= (res.x != o4.x) | (res.y != o4.y) | (res.z != o4.z) | (res.w != o4.w);
-        }
-    }
-    if (__any_sync(0xffffffffu, changed) && lane == 0) {
-        if (*reinterpret_cast<volatile uint32_t *>(flag) == 0u) atomicOr(flag, 1u);
-        if (chg) chg[v] = 1u;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -505,7 +415,8 @@ __device__ __forceinline__ void lean_finish(const typename RegFmt<NIB>::Acc (&ac
 }
 
 // Store node v's slice row: max(its gathered maximum nb, cur[v]) into next[v]
-// (by word-wise atomic max for a split hub's chunk, see union_store_hub),
+// (by word-wise atomic max for a split hub's chunk: next[v] starts each pass at
+// or below the result, so after all chunks it holds their maximum),
 // setting *flag, and chg[v] when given, if a register changed.  Lanes of
 // group 0 hold the row; every lane takes part in the vote.
 template <int S, bool NIB>

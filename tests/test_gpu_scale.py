@@ -3,9 +3,11 @@ and 236k-cell configurations checked on sampled nodes and by properties that
 hold at any size, in the launch configuration the benchmark times (p = 10,
 automatic slice width and CTA size).
 
-Full check (96 x 96 grid, N ~ 8k, ~2e7 edges, p = 10, unlimited d, slices
-forced narrow so one pass spans several slice launches): registers, estimates
-and mean depth bit-exact against the oracle at every pass.
+Full checks: a 96 x 96 grid (N ~ 8k, ~2e7 edges, p = 10, unlimited d, slices
+forced narrow so one pass spans several slice launches), and the whole
+~42.7k-cell graph in the city's configuration (3-row tables, 128-byte slices,
+groups of 2 x 2 cell blocks, d = 2): registers, estimates and mean depth
+bit-exact against the oracle at every pass.
 
 Sampled checks (medium and city), each expected value computed by the oracle
 from the obstacle grid alone:
@@ -137,3 +139,22 @@ def test_city_variants_agree(vga):
                 assert np.array_equal(ball, ball0)
     finally:
         g.free()
+
+
+def test_medium_full_parity_city_configuration(vga):
+    # The city's automatic configuration (3-row tables, 128-byte slices, the
+    # grouped union over 2 x 2 blocks of cells, pass 1 as the scatter) on the
+    # whole ~42.7k-cell medium graph: every node's registers and estimate
+    # against the oracle after every pass, d = 2 (pass 2 is a grouped union).
+    obst = workloads.medium(3)
+    off, b, cells = oracle.build_graph(obst)
+    ref = oracle.hyperball(off, b, 10, 2, seed=0, trace=2)
+    g = vga.vga_visibility_build(obst)
+    with g:
+        got = vga.hyperball_run_trace(g, 10, 2, seed=0, max_trace=2, slice_bytes=128, table_levels=3)
+    assert got["iterations"] == ref["iterations"] == 2
+    for t in range(3):
+        assert np.array_equal(got["regs"][t], ref["regs"][t]), f"registers differ after pass {t}"
+        assert np.array_equal(got["c"][t], ref["c"][t]), f"estimates differ after pass {t}"
+    assert np.array_equal(got["mean_depth"], ref["mean_depth"], equal_nan=True)
+    assert np.array_equal(got["ball"], ref["ball"])
