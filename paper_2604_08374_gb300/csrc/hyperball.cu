@@ -560,6 +560,14 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         return VGA_EINVAL;
     }
     P->scheme = levels == 5 ? 0 : levels == 3 ? 1 : g->lk_scheme;
+    // grouped union (runs mode): nodes per group, 0 for one node per warp
+    const int grp = tune ? tune->group_nodes : 0;
+    if (grp != 0 && grp != 1 && grp != 2 && grp != 4 && grp != 8) {
+        set_error("group_nodes = %d must be 0 (automatic), 1 (one node per warp), 2, 4 or 8", grp);
+        return VGA_EINVAL;
+    }
+    const int grp_sel = grp ? grp : (tabled && te.group_nodes > 0) ? te.group_nodes : 0;
+    P->group = P->mode != kModeRuns || grp_sel == 1 ? 0 : grp_sel == 0 ? kGroupAutoNodes : grp_sel;
     // rows of counters the union reads per slice: the slice, or in runs mode its table region
     const uint64_t rows_per_node = P->mode == kModeRuns ? (uint64_t)table_rows(P->scheme) : 1;
     int S = tune ? tune->slice_bytes : 0;
@@ -576,6 +584,7 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         const bool tabled_S = tabled && te.slice_bytes > 0 && !(tune && tune->l2_budget_mb > 0);
         uint64_t budget = (tune && tune->l2_budget_mb > 0) ? (uint64_t)tune->l2_budget_mb << 20
                           : tabled_S                       ? l2_bytes
+                          : P->mode == kModeRuns && P->group ? grouped_l2_budget(g->device)
                           : P->mode == kModeRuns           ? union_l2_budget(g->device)
                                                            : l2_bytes * 6 / 10;
         S = (int)std::min<uint32_t>(P->node_bytes, tabled_S ? (uint32_t)std::min(te.slice_bytes, 1024) : 1024u);
@@ -611,13 +620,6 @@ static int make_plan(const vga_graph *g, int p, const vga_tuning *tune, Plan *P)
         return VGA_EINVAL;
     }
     P->first_scatter = scatter_ok && first != 1;
-    const int grp = tune ? tune->group_nodes : 0;
-    if (grp != 0 && grp != 1 && grp != 2 && grp != 4 && grp != 8) {
-        set_error("group_nodes = %d must be 0 (automatic), 1 (one node per warp), 2, 4 or 8", grp);
-        return VGA_EINVAL;
-    }
-    const int grp_sel = grp ? grp : (tabled && te.group_nodes > 0) ? te.group_nodes : 0;
-    P->group = P->mode != kModeRuns || grp_sel == 1 ? 0 : grp_sel == 0 ? kGroupAutoNodes : grp_sel;
     const uint64_t regs = (uint64_t)P->n * P->node_bytes;
     uint64_t o = 0;
     P->off_cur = o;   o = align256(o + regs);

@@ -226,18 +226,22 @@ __global__ void group_merge_kernel(const GroupItem *__restrict__ items, uint64_t
 
 }  // namespace
 
-uint64_t union_l2_budget(int device) {
+static uint64_t l2_size(int device) {
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
-    return (uint64_t)(l2 > 0 ? l2 : (64 << 20)) * 3 / 4;
+    return (uint64_t)(l2 > 0 ? l2 : (64 << 20));
 }
+
+uint64_t union_l2_budget(int device) { return l2_size(device) * 3 / 4; }
+
+uint64_t grouped_l2_budget(int device) { return l2_size(device) * 5 / 4; }
 
 static std::atomic<uint32_t> g_scheme_nodes{0};  // vga_set_table_scheme_nodes (0 = from the L2 size)
 
 int table_scheme_auto(uint32_t n, int device) {
     const uint32_t above = g_scheme_nodes.load();
     if (above) return n > above - 1u ? 1 : 0;
-    return (uint64_t)table_rows(0) * n * 128u > union_l2_budget(device) ? 1 : 0;
+    return (uint64_t)table_rows(0) * n * 128u > grouped_l2_budget(device) ? 1 : 0;
 }
 
 }  // namespace vga

@@ -168,10 +168,17 @@ constexpr int kMaxTableRows = 5;
 constexpr uint64_t kRunMaxNodes = 1ull << 29;
 
 // The table scheme for a graph of n nodes on `device`: 1 when a 5-row region
-// of 128-byte slices would exceed the L2 share the union aims at, else 0.
+// of 128-byte slices would exceed the grouped union's budget, else 0.
 int table_scheme_auto(uint32_t n, int device);
-// L2 share the run-aware union's table region aims at (bytes).
+// L2 share the per-node run-aware union's table region aims at (bytes): 3/4
+// of the L2.
 uint64_t union_l2_budget(int device);
+// The same for the grouped union: 5/4 of the L2.  A group reads the rows its
+// nodes share together and groups go in block order, so the rows in use at a
+// time are a fraction of the region; on the city graph a 151 MB 5-row region
+// of 128-byte rows (1.2x the L2) ran faster than the 91 MB 3-row one, while a
+// 182 MB region of 256-byte rows or 64-byte rows that fit were slower.
+uint64_t grouped_l2_budget(int device);
 
 // One warp's work in the run-aware union: the lookups lk[b .. b + cnt) of node
 // v & ~kHubChunk.  A node with more lookups than the hub threshold is split
