@@ -142,19 +142,24 @@ def test_city_variants_agree(vga):
 
 
 def test_medium_full_parity_city_configuration(vga):
-    # The city's automatic configuration (3-row tables, 128-byte slices, the
-    # grouped union over 2 x 2 blocks of cells, pass 1 as the scatter) on the
-    # whole ~42.7k-cell medium graph: every node's registers and estimate
-    # against the oracle after every pass, d = 2 (pass 2 is a grouped union).
+    # The city's automatic configuration (5-row tables, 128-byte slices, the
+    # grouped union over 2 x 2 blocks of cells, pass 1 as the scatter) and the
+    # 3-row scheme it replaced, on the whole ~42.7k-cell medium graph: every
+    # node's registers and estimate against the oracle after every pass, d = 2
+    # (pass 2 is a grouped union).
     obst = workloads.medium(3)
     off, b, cells = oracle.build_graph(obst)
     ref = oracle.hyperball(off, b, 10, 2, seed=0, trace=2)
     g = vga.vga_visibility_build(obst)
     with g:
-        got = vga.hyperball_run_trace(g, 10, 2, seed=0, max_trace=2, slice_bytes=128, table_levels=3)
-    assert got["iterations"] == ref["iterations"] == 2
-    for t in range(3):
-        assert np.array_equal(got["regs"][t], ref["regs"][t]), f"registers differ after pass {t}"
-        assert np.array_equal(got["c"][t], ref["c"][t]), f"estimates differ after pass {t}"
-    assert np.array_equal(got["mean_depth"], ref["mean_depth"], equal_nan=True)
-    assert np.array_equal(got["ball"], ref["ball"])
+        for levels in (5, 3):
+            got = vga.hyperball_run_trace(g, 10, 2, seed=0, max_trace=2, slice_bytes=128,
+                                          table_levels=levels)
+            assert got["iterations"] == ref["iterations"] == 2
+            for t in range(3):
+                assert np.array_equal(got["regs"][t], ref["regs"][t]), \
+                    f"{levels}-row tables: registers differ after pass {t}"
+                assert np.array_equal(got["c"][t], ref["c"][t]), \
+                    f"{levels}-row tables: estimates differ after pass {t}"
+            assert np.array_equal(got["mean_depth"], ref["mean_depth"], equal_nan=True)
+            assert np.array_equal(got["ball"], ref["ball"])
