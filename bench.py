@@ -676,8 +676,10 @@ def run_ours(args, dist: Dist):
         # the GPU visibility builder (run once before the timed region) beside the oracle's
         extras["builder"] = {"gpu_seconds": build_s, "pair_tests": N * (N - 1) // 2,
                              "pair_tests_per_s": N * (N - 1) / 2 / build_s,
-                             "what": "vga_visibility_build: main component on the host, then every pair of the "
-                                     "upper triangle walked by supercover DDA on the device, mirrored, encoded"}
+                             "what": "vga_visibility_build: main component on the host, then each source's "
+                                     "8 octants swept column by column on the device with exact slope intervals, "
+                                     "lists counted and LEB128-encoded in two passes; pair_tests = the N(N-1)/2 "
+                                     "pairs it decides"}
         if "cpu_baseline" in extras:
             cb = extras["cpu_baseline"]["builder"]
             extras["builder"]["cpu_oracle_pair_tests_per_s"] = cb["pair_tests_per_s"]

@@ -161,9 +161,31 @@ int vga_graph_set_cells(vga_graph *g, int W, int H, const uint64_t *cell_of_node
  *               (size it W*H to be safe, or query N first with
  *               vga_visibility_count).
  *   out         receives the graph handle.
- * Device scratch: an N x ceil(N/32) bit matrix (N = 236k needs 7 GB).
+ * Method: from every source, the 8 octants are swept column by column outwards
+ * while a list of the unblocked slope intervals (exact integer fractions,
+ * each end open or closed) is kept; a target is visible iff its slope lies in
+ * one of them (the diagonal target also needs the cell beside it, whose
+ * corner its segment touches, free).  The result equals the pairwise rule
+ * above for every pair.  Two passes (count, then write) produce the CSR.
+ * Device scratch besides the CSR: obstacle bitmaps (2 x W x H bits with
+ * margins), a W*H node-id table and 12 bytes a node; per CTA a node bitmap
+ * (in shared memory up to ~800k nodes) and, for sources whose interval lists
+ * outgrow shared memory, global lists of max(W, H) + 2 entries per warp.
+ * Errors: VGA_EINVAL for bad sizes; VGA_ECORRUPT if the sweep's own checks
+ * fail (a visible cell off the component, a list overflow past the proven
+ * bound, a count/write mismatch).
  */
 int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_node, vga_graph **out);
+
+/*
+ * vga_set_visibility_sweep_limits -- test hook for the builder's two
+ * fallbacks: smem_list_cap (1..128, 0 = 128) caps the interval lists kept in
+ * shared memory, so that more sources take the global-list retry;
+ * smem_bitmap_nodes > 0 keeps the node bitmap in global memory for graphs
+ * with more nodes than that (0 = whenever shared memory is too small).
+ * Process-wide; both give the same graph as the defaults.
+ */
+int vga_set_visibility_sweep_limits(int smem_list_cap, uint32_t smem_bitmap_nodes);
 
 /*
  * vga_visibility_build_ordered -- as vga_visibility_build, with the node
@@ -207,7 +229,8 @@ typedef struct vga_tuning {
     int table_levels;    /* mode 2: rows per node of a slice's table of range maxima:
                             5 (windows of 1, 2, 4, 8, 16 rows: fewest lookups) or 3 (1, 4,
                             16: lets wider slices fit the L2); 0 = automatic (3 when five
-                            rows of 128-byte slices would exceed 3/4 of the L2).  A
+                            rows of 128-byte slices would exceed 5/4 of the L2, the
+                            grouped union's budget).  A
                             non-automatic choice builds its own lookup list on first use. */
     int l2_window;       /* 1: during the run, mark the union's table region (mode 2) or
                             register slice (mode 1) persisting in L2 through an access-

@@ -112,6 +112,7 @@ SIGNATURES = {
     "vga_shard_finalize": ([vp, vp, vp, vp], i32),
     "vga_shard_free": ([vp], None),
     "vga_set_table_scheme_nodes": ([u32], i32),
+    "vga_set_visibility_sweep_limits": ([i32, u32], i32),
     "vga_autotune": ([C.POINTER(vp), i32, i32, vp, C.POINTER(VgaTuneEntry), i32, C.POINTER(i32), i32], i32),
     "vga_tune_table_set": ([C.POINTER(VgaTuneEntry), i32], i32),
     "vga_tune_table_get": ([C.POINTER(VgaTuneEntry), i32, C.POINTER(i32)], i32),
@@ -598,6 +599,13 @@ def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, sli
                                           group_nodes=group_nodes),
                                   C.byref(h)))
     return Shard(h)
+
+
+def vga_set_visibility_sweep_limits(smem_list_cap: int = 0, smem_bitmap_nodes: int = 0):
+    """Builder test hook: cap the interval lists kept in shared memory
+    (1..128, 0 = 128) and keep the node bitmap in global memory for graphs above
+    `smem_bitmap_nodes` nodes (0 = only when shared memory is too small)."""
+    _check(lib().vga_set_visibility_sweep_limits(smem_list_cap, smem_bitmap_nodes))
 
 
 def vga_set_table_scheme_nodes(nodes: int = 0):

@@ -94,6 +94,59 @@ def test_builder_matches_oracle(vga, grid):
         assert g.n_nodes == vga.vga_visibility_count(obst)
 
 
+def _builder_grid(name):
+    if name == "wall":
+        obst = workloads.open_grid(20, 12)
+        obst[:, 9] = 1
+        obst[5, 9] = 0
+        return obst
+    if name == "maze":
+        return (np.random.default_rng(3).random((37, 41)) < 0.3).astype(np.uint8)
+    if name == "dense":
+        return (np.random.default_rng(8).random((29, 33)) < 0.45).astype(np.uint8)
+    return workloads.random_rectangles(40, 23, 9, (1, 7), seed=11)
+
+
+@pytest.mark.parametrize("limits", [(1, 0), (2, 1), (0, 1)], ids=["global-lists", "both", "global-bitmap"])
+@pytest.mark.parametrize("grid", ["wall", "maze", "dense", "rect40x23"])
+def test_builder_fallbacks_match_oracle(vga, grid, limits):
+    # The sweep's two fallbacks, forced on small grids: interval lists that
+    # outgrow shared memory are redone with global lists (capacity 1 or 2
+    # sends nearly every source there), and the node bitmap in global memory.
+    obst = _builder_grid(grid)
+    off, b, cells = oracle.build_graph(obst)
+    vga.vga_set_visibility_sweep_limits(*limits)
+    try:
+        g = vga.vga_visibility_build(obst)
+    finally:
+        vga.vga_set_visibility_sweep_limits(0, 0)
+    with g:
+        o2, b2, _ = g.copy_csr()
+        assert np.array_equal(o2, off) and np.array_equal(b2, b)
+
+
+def test_builder_comb_overflows_shared_lists(vga):
+    # A column of single-cell pillars two rows apart leaves ~135 open slope
+    # intervals behind it for sources near the corner, more than the 128 the
+    # shared-memory lists hold: those sources take the global-list retry.
+    W = H = 280
+    obst = np.zeros((H, W), np.uint8)
+    obst[0:H:2, 270] = 1
+    g, gcells = vga.vga_visibility_build(obst, return_cells=True)
+    with g:
+        noc, cells = oracle.main_component(obst)
+        assert np.array_equal(gcells.astype(np.int64), cells)
+        n = g.n_nodes
+        corner = [int(noc[y * W + x]) for y in range(4) for x in range(4)]
+        rng = np.random.default_rng(0)
+        sample = np.unique(np.concatenate([corner, rng.choice(n, 12, replace=False), [n - 1]])).astype(np.int64)
+        row_ptr, col = oracle.visibility_csr(obst, cells, nodes=sample)
+        g_off, g_bytes, _ = g.copy_csr()
+        for k, v in enumerate(sample):
+            got = oracle.decode_list(g_bytes, int(g_off[v]), int(g_off[v + 1]), n)
+            assert np.array_equal(got, col[row_ptr[k]:row_ptr[k + 1]]), f"neighbour list of node {v}"
+
+
 # ----------------------------------------------------------------------------
 # HyperBall, bit-exact at every pass
 # ----------------------------------------------------------------------------
