@@ -125,7 +125,7 @@ struct Slope {
 };
 
 __device__ __forceinline__ int slope_cmp(const Slope &a, const Slope &b) {
-    const long long l = (long long)a.n * b.d, r = (long long)b.n * a.d;
+    const int l = a.n * b.d, r = b.n * a.d;   // |numerators|, denominators < 2^15
     return l < r ? -1 : (l > r ? 1 : 0);
 }
 
@@ -184,11 +184,22 @@ __device__ __forceinline__ bool column_obst(const uint32_t *__restrict__ line, i
     return (__ldg(line + (pos >> 5)) >> (pos & 31)) & 1u;
 }
 
-// Pieces of interval [lo, hi] left after the obstacles of column k in rows
-// r0 .. r1; written to out (when not null) and counted.
-__device__ int interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1,
-                               const uint32_t *__restrict__ line, int lw, int c0, bool neg, uint2 *out) {
-    int cnt = 0;
+// Rows a .. b of column k whose slopes r / k lie in [lo, hi] (b < a: none).
+// Numerators are at most 2k + 3 and k < 2^14, so the products fit 32 bits.
+__device__ __forceinline__ void interval_rows(const Slope &lo, const Slope &hi, int k, int &a, int &b) {
+    const uint32_t nl = (uint32_t)lo.n * (uint32_t)k, nh = (uint32_t)hi.n * (uint32_t)k;
+    uint32_t qa = (nl + (uint32_t)lo.d - 1u) / (uint32_t)lo.d;
+    if (lo.open && qa * (uint32_t)lo.d == nl) qa++;
+    const uint32_t qb = nh / (uint32_t)hi.d;
+    a = (int)qa;
+    b = (int)qb - ((hi.open && qb * (uint32_t)hi.d == nh) ? 1 : 0);
+}
+
+// Appends to out (through the warp's counter) the pieces of interval
+// [lo, hi] left after the obstacles of column k in rows r0 .. r1; pieces past
+// cap are counted but not stored.
+__device__ void interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1, const uint32_t *__restrict__ line,
+                                int lw, int c0, bool neg, uint2 *out, int *count, int cap) {
     int y = r0;
     while (y <= r1) {
         const int lim = min(32, r1 - y + 1);
@@ -214,8 +225,8 @@ __device__ int interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1,
         const Slope mn{2 * s - 1, 2 * k + 1, true}, mx{2 * e + 1, 2 * k - 1, true};
         const Slope phi = slope_cmp(hi, mn) < 0 ? hi : mn;
         if (interval_nonempty(lo, phi)) {
-            if (out) out[cnt] = make_uint2(slope_pack(lo), slope_pack(phi));
-            cnt++;
+            const int at = atomicAdd(count, 1);
+            if (at < cap) out[at] = make_uint2(slope_pack(lo), slope_pack(phi));
         }
         const int c2 = slope_cmp(mx, lo);
         if (c2 > 0) lo = mx;
@@ -223,10 +234,9 @@ __device__ int interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1,
         y = e + 1;
     }
     if (interval_nonempty(lo, hi)) {
-        if (out) out[cnt] = make_uint2(slope_pack(lo), slope_pack(hi));
-        cnt++;
+        const int at = atomicAdd(count, 1);
+        if (at < cap) out[at] = make_uint2(slope_pack(lo), slope_pack(hi));
     }
-    return cnt;
 }
 
 __device__ __forceinline__ uint32_t varint_len(uint32_t x) {
@@ -236,7 +246,7 @@ __device__ __forceinline__ uint32_t varint_len(uint32_t x) {
 // One warp sweeps octant `oct` of source (sx, sy), setting the bits of the
 // visible nodes in bm.  Returns false when the interval list outgrew cap.
 __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32_t *bm, uint2 *la, uint2 *lb,
-                             int cap, uint32_t *mask, int &id_lo, int &id_hi) {
+                             int cap, uint32_t *mask, int *count, int &id_lo, int &id_hi) {
     const int lane = threadIdx.x & 31;
     const bool xmajor = (oct >> 2) == 0;
     const int smaj = (oct & 1) ? -1 : 1;
@@ -260,13 +270,16 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
         const uint32_t *line = base + (size_t)maj * lw;
         // 1. the target rows of every interval into the row mask
         int amin = 0x7fffffff, bmax = -1;
+        int a0 = 0, b0 = -1;   // rows of this lane's first interval, kept for step 3
         for (int i = lane; i < na; i += 32) {
             const uint2 iv = la[i];
             const Slope lo = slope_unpack(iv.x), hi = slope_unpack(iv.y);
-            int a = (int)(((long long)lo.n * k + lo.d - 1) / lo.d);
-            if (lo.open && (long long)a * lo.d == (long long)lo.n * k) a++;
-            int b = (int)(((long long)hi.n * k) / hi.d);
-            if (hi.open && (long long)b * hi.d == (long long)hi.n * k) b--;
+            int a, b;
+            interval_rows(lo, hi, k, a, b);
+            if (i == lane) {
+                a0 = a;
+                b0 = b;
+            }
             if (b >= A.mask_words * 32) {   // b <= k < the major extent: never taken
                 atomicOr(A.err, 4);
                 b = A.mask_words * 32 - 1;
@@ -310,36 +323,20 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
             }
         }
         __syncwarp();
-        // 3. the pieces each interval leaves for column k + 1
-        int cnt = 0;
+        // 3. the pieces each interval leaves for column k + 1, appended to
+        //    the other list in any order
+        if (lane == 0) *count = 0;
+        __syncwarp();
         for (int i = lane; i < na; i += 32) {
             const uint2 iv = la[i];
             const Slope lo = slope_unpack(iv.x), hi = slope_unpack(iv.y);
-            int a = (int)(((long long)lo.n * k + lo.d - 1) / lo.d);
-            if (lo.open && (long long)a * lo.d == (long long)lo.n * k) a++;
-            int b = (int)(((long long)hi.n * k) / hi.d);
-            if (hi.open && (long long)b * hi.d == (long long)hi.n * k) b--;
-            cnt += interval_pieces(lo, hi, k, max(a - 1, 0), b + 1, line, lw, c0, neg, nullptr);
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total > cap) return false;
-        int pos = incl - cnt;
-        for (int i = lane; i < na; i += 32) {
-            const uint2 iv = la[i];
-            const Slope lo = slope_unpack(iv.x), hi = slope_unpack(iv.y);
-            int a = (int)(((long long)lo.n * k + lo.d - 1) / lo.d);
-            if (lo.open && (long long)a * lo.d == (long long)lo.n * k) a++;
-            int b = (int)(((long long)hi.n * k) / hi.d);
-            if (hi.open && (long long)b * hi.d == (long long)hi.n * k) b--;
-            pos += interval_pieces(lo, hi, k, max(a - 1, 0), b + 1, line, lw, c0, neg, lb + pos);
+            int a = a0, b = b0;
+            if (i != lane) interval_rows(lo, hi, k, a, b);
+            interval_pieces(lo, hi, k, max(a - 1, 0), b + 1, line, lw, c0, neg, lb, count, cap);
         }
         __syncwarp();
+        const int total = *count;
+        if (total > cap) return false;
         uint2 *t = la;
         la = lb;
         lb = t;
@@ -361,6 +358,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) visibility_sweep_kernel(Swee
     __shared__ int s_overflow, s_lo[kSweepWarps], s_hi[kSweepWarps];
     __shared__ int s_first[kSweepWarps], s_last[kSweepWarps];
     __shared__ uint32_t s_bytes[kSweepWarps];
+    __shared__ int s_count[kSweepWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t *p = smem;
     uint32_t *bm;
@@ -397,7 +395,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) visibility_sweep_kernel(Swee
         const uint32_t cell = A.cells[u];
         const int sx = (int)(cell % (uint32_t)A.W), sy = (int)(cell / (uint32_t)A.W);
         int id_lo = 0x7fffffff, id_hi = -1;
-        if (!sweep_octant(A, warp, sx, sy, bm, la, lb, cap, mask, id_lo, id_hi)) {
+        if (!sweep_octant(A, warp, sx, sy, bm, la, lb, cap, mask, &s_count[warp], id_lo, id_hi)) {
             if (lane == 0) s_overflow = 1;
             for (int w = lane; w < A.mask_words; w += 32) mask[w] = 0u;
         }
