@@ -5,13 +5,15 @@
 // so neighbour lists come out sorted and delta-encode into mostly one-byte
 // LEB128 varints.
 //
-// Pipeline: (host) main component and numbering; (device) one warp per
-// (source, 32 consecutive targets) walks each segment through the grid and
-// ballots the results into an N x ceil(N/32) bit matrix, upper block triangle
-// only, then 32 x 32 bit-block transposes fill the lower one; (device) one warp per
-// source counts the LEB128 bytes of its row; (host) prefix sum into offsets;
-// (device) one warp per source writes the bytes; then the ordinary load path
-// validates the stream and derives degrees.
+// Method: the angular sweep of Sec. 3.1 ("SparkSieve angular sweep": per
+// source, eight octants expand outwards while a list of open gaps in
+// tan-space [0, 1] loses the ranges obstacles cover), with the gaps' ends kept
+// as exact integer fractions so that the result equals the pairwise rule above
+// for every pair.  Pipeline: (host) main component and numbering, obstacle
+// bitmaps; (device) count pass: per source, the octants swept into a node
+// bitmap and the LEB128 bytes of its list counted; (host) prefix sum into
+// offsets; (device) write pass: the same sweep, the bytes written; then the
+// ordinary load path validates the stream and derives degrees.
 #include <algorithm>
 #include <utility>
 #include <vector>
