@@ -162,7 +162,7 @@ struct SweepArgs {
     int glist_cap;
     uint32_t *gbitmap;             // global node bitmaps, words_n per CTA (large graphs)
     uint32_t words_n;              // ceil(n / 32)
-    int mask_words;                // row-mask words per warp
+    int mask_words;                // row-mask (and staged obstacle) words per warp
     int smem_cap;                  // interval-list capacity in shared memory (<= kSweepCap)
     int *err;                      // nonzero: a visible cell off the component, or a list overflow
 };
@@ -197,16 +197,22 @@ __device__ __forceinline__ void interval_rows(const Slope &lo, const Slope &hi, 
     b = (int)qb - ((hi.open && qb * (uint32_t)hi.d == nh) ? 1 : 0);
 }
 
+// Obstacle bits of rows y .. y + 31 of the current column from its words
+// staged in shared memory (obw[w] holds rows 32w .. 32w + 31).
+__device__ __forceinline__ uint32_t staged_bits(const uint32_t *obw, int y) {
+    return __funnelshift_r(obw[y >> 5], obw[(y >> 5) + 1], y & 31);
+}
+
 // Appends to out (through the warp's counter) the pieces of interval
-// [lo, hi] left after the obstacles of column k in rows r0 .. r1; pieces past
-// cap are counted but not stored.
-__device__ void interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1, const uint32_t *__restrict__ line,
-                                int lw, int c0, bool neg, uint2 *out, int *count, int cap) {
+// [lo, hi] left after the obstacles of column k in rows r0 .. r1 (read from
+// the column's staged words); pieces past cap are counted but not stored.
+__device__ void interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1, const uint32_t *obw, uint2 *out,
+                                int *count, int cap) {
     int y = r0;
     while (y <= r1) {
         const int lim = min(32, r1 - y + 1);
         const uint32_t valid = lim == 32 ? 0xffffffffu : ((1u << lim) - 1u);
-        const uint32_t ob = column_bits(line, lw, c0, neg, y) & valid;
+        const uint32_t ob = staged_bits(obw, y) & valid;
         if (!ob) {
             y += lim;
             continue;
@@ -217,7 +223,7 @@ __device__ void interval_pieces(Slope lo, const Slope &hi, int k, int r0, int r1
         for (int z = s; z <= r1;) {
             const int lim2 = min(32, r1 - z + 1);
             const uint32_t valid2 = lim2 == 32 ? 0xffffffffu : ((1u << lim2) - 1u);
-            const uint32_t fr = ~column_bits(line, lw, c0, neg, z) & valid2;
+            const uint32_t fr = ~staged_bits(obw, z) & valid2;
             if (fr) {
                 e = z + __ffs(fr) - 2;
                 break;
@@ -248,7 +254,7 @@ __device__ __forceinline__ uint32_t varint_len(uint32_t x) {
 // One warp sweeps octant `oct` of source (sx, sy), setting the bits of the
 // visible nodes in bm.  Returns false when the interval list outgrew cap.
 __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32_t *bm, uint2 *la, uint2 *lb,
-                             int cap, uint32_t *mask, int *count, int &id_lo, int &id_hi) {
+                             int cap, uint32_t *mask, uint32_t *obw, int *count, int &id_lo, int &id_hi) {
     const int lane = threadIdx.x & 31;
     const bool xmajor = (oct >> 2) == 0;
     const int smaj = (oct & 1) ? -1 : 1;
@@ -271,7 +277,7 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
         if (maj < 0 || maj >= maj_n) break;
         const uint32_t *line = base + (size_t)maj * lw;
         // 1. the target rows of every interval into the row mask
-        int amin = 0x7fffffff, bmax = -1;
+        int amin = 0x7fffffff, bmax = -1, rmax = 0;
         int a0 = 0, b0 = -1;   // rows of this lane's first interval, kept for step 3
         for (int i = lane; i < na; i += 32) {
             const uint2 iv = la[i];
@@ -282,10 +288,11 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
                 a0 = a;
                 b0 = b;
             }
-            if (b >= A.mask_words * 32) {   // b <= k < the major extent: never taken
+            if (b >= A.mask_words * 32 - 33) {   // b <= k < the major extent: never taken
                 atomicOr(A.err, 4);
-                b = A.mask_words * 32 - 1;
+                b = A.mask_words * 32 - 34;
             }
+            rmax = max(rmax, b + 1);
             if (a <= b) {
                 amin = min(amin, a);
                 bmax = max(bmax, b);
@@ -298,6 +305,10 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
         }
         amin = __reduce_min_sync(0xffffffffu, amin);
         bmax = __reduce_max_sync(0xffffffffu, bmax);
+        rmax = __reduce_max_sync(0xffffffffu, rmax);
+        // the column's obstacle words for rows 0 .. rmax + 32, staged once for
+        // steps 2 and 3
+        for (int w = lane; w <= (rmax >> 5) + 1; w += 32) obw[w] = column_bits(line, lw, c0, neg, w * 32);
         __syncwarp();
         // 2. visible targets: masked rows that are free; the diagonal target
         //    also needs (k, k - 1) free
@@ -305,7 +316,7 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
             const bool diag_blocked = column_obst(line, lw, c0, neg, k - 1);
             for (int w = amin >> 5; w <= (bmax >> 5); w++) {
                 const uint32_t m = mask[w];
-                uint32_t vis = m & ~column_bits(line, lw, c0, neg, w * 32);
+                uint32_t vis = m & ~obw[w];
                 if (diag_blocked && k >= w * 32 && k < w * 32 + 32) vis &= ~(1u << (k - w * 32));
                 if ((vis >> lane) & 1u) {
                     const int r = w * 32 + lane;
@@ -334,7 +345,7 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
             const Slope lo = slope_unpack(iv.x), hi = slope_unpack(iv.y);
             int a = a0, b = b0;
             if (i != lane) interval_rows(lo, hi, k, a, b);
-            interval_pieces(lo, hi, k, max(a - 1, 0), b + 1, line, lw, c0, neg, lb, count, cap);
+            interval_pieces(lo, hi, k, max(a - 1, 0), b + 1, obw, lb, count, cap);
         }
         __syncwarp();
         const int total = *count;
@@ -383,6 +394,7 @@ __global__ void __launch_bounds__(kSweepThreads, 5) visibility_sweep_kernel(Swee
         p += (size_t)kSweepWarps * 2 * kSweepCap * sizeof(uint2);
     }
     uint32_t *mask = reinterpret_cast<uint32_t *>(p) + (size_t)warp * A.mask_words;
+    uint32_t *obw = reinterpret_cast<uint32_t *>(p) + (size_t)(kSweepWarps + warp) * A.mask_words;
     for (uint32_t w = threadIdx.x; w < A.words_n; w += blockDim.x) bm[w] = 0u;
     for (int w = lane; w < A.mask_words; w += 32) mask[w] = 0u;
     for (;;) {
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(kSweepThreads, 5) visibility_sweep_kernel(Swee
         const uint32_t cell = A.cells[u];
         const int sx = (int)(cell % (uint32_t)A.W), sy = (int)(cell / (uint32_t)A.W);
         int id_lo = 0x7fffffff, id_hi = -1;
-        if (!sweep_octant(A, warp, sx, sy, bm, la, lb, cap, mask, &s_count[warp], id_lo, id_hi)) {
+        if (!sweep_octant(A, warp, sx, sy, bm, la, lb, cap, mask, obw, &s_count[warp], id_lo, id_hi)) {
             if (lane == 0) s_overflow = 1;
             for (int w = lane; w < A.mask_words; w += 32) mask[w] = 0u;
         }
@@ -603,7 +615,7 @@ int vga_visibility_build_ordered(int W, int H, const uint8_t *obst, int order, u
     VGA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     VGA_CHECK_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const size_t list_smem = (size_t)kSweepWarps * 2 * kSweepCap * sizeof(uint2);
-    const size_t mask_smem = (size_t)kSweepWarps * mask_words * 4;
+    const size_t mask_smem = (size_t)2 * kSweepWarps * mask_words * 4;   // row masks and staged obstacle words
     const size_t bitmap_smem = (size_t)((words_n + 3) & ~3u) * 4;
     // the node bitmap stays in shared memory while two CTAs fit an SM
     const bool smem_bitmap = bitmap_smem + list_smem + mask_smem + 1024 <= (size_t)smem_optin / 2 &&
