@@ -630,13 +630,28 @@ def run_ours(args, dist: Dist):
         sweep = []
         for (sp, sd, sb) in ((8, args.d, 8), (12, args.d, 8), (args.p, 10, 8), (args.p, args.d, 4)):
             step(sd, p=sp, bits=sb)
+            if sb == 4:  # the packed format's union launches against the same L2 ceilings
+                vga.vga_profile_reset()
+                vga.vga_profile_enable(True)
             f0.record(stream)
             s_passes = step(sd, p=sp, bits=sb)
             f1.record(stream)
             torch.cuda.synchronize()
             sec_s = f0.elapsed_time(f1) / 1e3
-            sweep.append({"p": sp, "d": sd, "register_bits": sb, "seconds": sec_s, "passes": s_passes,
-                          "geu_per_s": s_passes * E / sec_s / 1e9})
+            entry = {"p": sp, "d": sd, "register_bits": sb, "seconds": sec_s, "passes": s_passes,
+                     "geu_per_s": s_passes * E / sec_s / 1e9}
+            if sb == 4:
+                vga.vga_profile_enable(False)
+                p4 = vga.vga_profile_read()
+                if p4["union_launches"]:
+                    ms4 = p4["union_ms"] / p4["union_launches"]
+                    ach4 = p4["union_gather_bytes"] / p4["union_launches"] / (ms4 / 1e3) / 1e9
+                    entry["union"] = {"slice_bytes": p4["slice_bytes"], "launches_timed": p4["union_launches"],
+                                      "avg_launch_ms": ms4, "achieved_gbs": ach4,
+                                      "frac_vs_l2_stream": ach4 / l2_stream, "frac_vs_gather_shape": ach4 / l2_peak,
+                                      "what": "distinct table rows x slice bytes per launch over the launch time "
+                                              "(a 128-byte row holds 256 packed registers)"}
+            sweep.append(entry)
         # register shards (the multi-GPU split) run in lockstep on this one GPU: the same
         # union work as one run plus the per-pass partial sums and their estimate, so the
         # time over the unsharded run is the split's compute overhead (no interconnect)
