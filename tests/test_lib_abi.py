@@ -68,6 +68,26 @@ def test_encoder_matches_oracle(built_lib, seed):
     assert bytes(b) == bytes(ref_bytes)
 
 
+@pytest.mark.parametrize("case", ["tiny3", "maze", "ties", "all_obstacles", "one_cell"])
+def test_main_component_count_matches_oracle(built_lib, case):
+    # the builder's host step (largest 4-connected free component, ties to the
+    # lowest raster index) against the oracle's, with no device work
+    vga, _ = built_lib
+    if case == "tiny3":
+        obst = workloads.tiny(3)
+    elif case == "maze":
+        obst = (np.random.default_rng(5).random((23, 31)) < 0.45).astype(np.uint8)
+    elif case == "ties":  # two equal free halves split by a wall
+        obst = np.zeros((6, 9), np.uint8)
+        obst[:, 4] = 1
+    elif case == "all_obstacles":
+        obst = np.ones((4, 5), np.uint8)
+    else:
+        obst = np.zeros((1, 1), np.uint8)
+    _, cells = oracle.main_component(obst)
+    assert vga.vga_visibility_count(obst) == len(cells)
+
+
 def test_encoder_rejects_unsorted_lists(built_lib):
     vga, _ = built_lib
     with pytest.raises(vga.VgaError) as e:
