@@ -179,7 +179,7 @@ int vga_visibility_build(int W, int H, const uint8_t *obst, uint64_t *cell_of_no
 
 /*
  * vga_set_visibility_sweep_limits -- test hook for the builder's two
- * fallbacks: smem_list_cap (1..96, 0 = 96) caps the interval lists kept in
+ * fallbacks: smem_list_cap (1..48, 0 = 48) caps the interval lists kept in
  * shared memory, so that more sources take the global-list retry;
  * smem_bitmap_nodes > 0 keeps the node bitmap in global memory for graphs
  * with more nodes than that (0 = whenever shared memory is too small).

@@ -603,7 +603,7 @@ def vga_shard_create(g: Graph, p: int, seed: int, shard: int, n_shards: int, sli
 
 def vga_set_visibility_sweep_limits(smem_list_cap: int = 0, smem_bitmap_nodes: int = 0):
     """Builder test hook: cap the interval lists kept in shared memory
-    (1..96, 0 = 96) and keep the node bitmap in global memory for graphs above
+    (1..48, 0 = 48) and keep the node bitmap in global memory for graphs above
     `smem_bitmap_nodes` nodes (0 = only when shared memory is too small)."""
     _check(lib().vga_set_visibility_sweep_limits(smem_list_cap, smem_bitmap_nodes))
 

@@ -111,7 +111,7 @@ uint64_t hilbert_position(int k, uint32_t x, uint32_t y) {
 
 constexpr int kSweepWarps = 8;                     // one warp per octant
 constexpr int kSweepThreads = kSweepWarps * 32;
-constexpr int kSweepCap = 96;                      // intervals per list in shared memory
+constexpr int kSweepCap = 48;                      // intervals per list in shared memory
 constexpr int kPad = 64;                           // margin bits (obstacles) on both sides of a line
 constexpr uint32_t kNoSource = 0xffffffffu;
 
@@ -365,7 +365,7 @@ __device__ bool sweep_octant(const SweepArgs &A, int oct, int sx, int sy, uint32
 // proven maximum (retried sources); otherwise kSweepCap entries in shared
 // memory, and a source whose list outgrows them is queued for the retry.
 template <bool WRITE, bool GLOBAL_LISTS, bool SMEM_BITMAP>
-__global__ void __launch_bounds__(kSweepThreads, 5) visibility_sweep_kernel(SweepArgs A) {
+__global__ void __launch_bounds__(kSweepThreads, 6) visibility_sweep_kernel(SweepArgs A) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_src;
     __shared__ int s_overflow, s_lo[kSweepWarps], s_hi[kSweepWarps];

@@ -127,7 +127,7 @@ def test_builder_fallbacks_match_oracle(vga, grid, limits):
 
 def test_builder_comb_overflows_shared_lists(vga):
     # A column of single-cell pillars two rows apart leaves ~135 open slope
-    # intervals behind it for sources near the corner, more than the 96 the
+    # intervals behind it for sources near the corner, more than the 48 the
     # shared-memory lists hold: those sources take the global-list retry.
     W = H = 280
     obst = np.zeros((H, W), np.uint8)
